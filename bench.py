@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of one full self-consistent GW iteration on one GB300.
+
+A step is one GW iteration (density matrix and HF, P~0, screened solve,
+Sigma~, transforms, chemical-potential search and Dyson) over a seeded
+synthetic system resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C2] [--precision fp32]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+  python bench.py --peaks                # fp64 / fp32 / tf32 matmul rates of this GPU
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GW iteration seconds and P/Sigma TFLOP/s, FP64 vs mixed, at stated Sigma error"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# per-SM per-clock flop rates of the SIMT pipes used by the contraction kernel
+FP32_FLOPS_PER_CLK_SM = 128 * 2       # 128 FP32 lanes x FMA
+FP64_FLOPS_PER_CLK_SM = 2 * 2         # 2 FP64 FMA per SM per clock (1.26 TFLOP/s at 2.07 GHz)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gw", choices=["gw", "reference"])
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--fp64-steps", type=int, default=1, help="timed fp64-path iterations for the comparison")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-q", type=int, default=1, help="q-slices in the CPU sample")
+    p.add_argument("--peaks", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- flop accounting
+
+def flops(cfg):
+    nao, naux, ntau = cfg["nao"], cfg["naux"], cfg["ntau"]
+    nk = cfg["kmesh"][0] * cfg["kmesh"][1] * cfg["kmesh"][2]
+    contr = 8.0 * nk * nk * ntau * (naux * naux * nao * nao + 2 * naux * nao ** 3)
+    return dict(P0=contr, Sigma=contr, screened=8.0 * naux ** 3 * nk * ntau,
+                transforms=16.0 * nk * naux * naux * ntau * ntau + 16.0 * nk * nao * nao * ntau * ntau,
+                K=16.0 * nk * nk * naux * nao ** 3)
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- inputs
+
+def make_inputs(workload, seed_offset=0):
+    from synth import CONFIGS, config_seed, make_system, matsubara_indices
+    cfg = dict(CONFIGS[workload])
+    sysd = make_system(cfg["nao"], cfg["naux"], cfg["kmesh"], config_seed(workload, seed_offset))
+    fn, bm = matsubara_indices(cfg["ntau"])
+    sysd.update(beta=cfg["beta"], ntau=cfg["ntau"], fermi_n=fn, bose_m=bm, n_elec=float(cfg["nao"]))
+    return cfg, sysd
+
+
+def traffic_from_profiles(workload, precision):
+    """Per-launch DRAM bytes of the contraction kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2206_07660_gb300", "csrc", "k_gett.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "contraction_%s_%s.md" % (workload, precision))
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m1 = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m1 or not m2 or m1.group(1) != sha:
+        return None
+    return float(m2.group(1))
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+
+def cpu_sample(cfg, sysd, nq_sample=1):
+    """Time the oracle on a bounded slice of one iteration and extrapolate.
+
+    The slice: A2 (P~0), A4 (screened solve, all nw) and A6 (Sigma~
+    contribution) for nq_sample of the nq q-points, from the non-interacting
+    G; the q-independent rest (HF, transforms of Sigma, mu search and Dyson)
+    is timed in full.  Seconds per iteration = nq/nq_sample x slice + rest.
+    """
+    import numpy as np
+    from oracle import gw as ogw
+    st = ogw.State(sysd)
+    st.dyson()
+    G = st.G_tau
+    km, V, grid = st.km, st.V, st.grid
+    nk = km.nk
+    ntau, naux = grid.ntau, V.shape[2]
+    t0 = time.perf_counter()
+    for q in range(nq_sample):
+        P = np.zeros((1, ntau, naux, naux), dtype=np.complex128)
+        for k in range(nk):
+            kq = km.add(k, q)
+            VG = np.einsum("Qda,tab->tQdb", V[k, kq], G[:, kq])
+            Z = np.einsum("tcd,tQdb->tQcb", -G[::-1, k], VG)
+            P[0] += np.einsum("tQcb,Rbc->tQR", Z, V[kq, k], optimize=True)
+        P = ogw.herm(P * 2.0 / nk)
+        Piw = ogw.to_matsubara(grid.TFb, P, 1)
+        Pt = ogw.herm(ogw.to_matsubara(grid.TBb, ogw.screened(Piw), 1))
+        Sig = np.zeros_like(G)
+        for k in range(nk):
+            kmq = km.sub(k, q)
+            X = np.einsum("tQR,Qia->tRia", Pt[0], V[k, kmq], optimize=True)
+            Y = np.einsum("tRia,tab->tRib", X, G[:, kmq])
+            Sig[:, k] += np.einsum("tRib,Rbj->tij", Y, V[kmq, k], optimize=True)
+    t_slice = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    gam = ogw.density_matrix(grid, G)
+    Sinf = ogw.hartree(V, gam) + ogw.exchange(V, gam)
+    Siw = ogw.to_matsubara(grid.TFf, ogw.herm(Sig), 0)
+    st.Sigma_inf, st.Sigma_iw = Sinf, Siw
+    st.dyson()
+    t_rest = time.perf_counter() - t1
+    per_iter = t_slice * nk / nq_sample + t_rest
+    cores = len(os.sched_getaffinity(0))
+    return per_iter, dict(slice_s=t_slice, rest_s=t_rest, cores=cores,
+                          sample="oracle (NumPy complex128) on %d of %d q-slices of A2+A4+A6 plus the "
+                                 "full HF, Sigma transform, mu search and Dyson; seconds per iteration "
+                                 "extrapolated as nq/%d x slice + rest" % (nq_sample, nk, nq_sample))
+
+
+# ---------------------------------------------------------------- peaks
+
+def measure_peaks():
+    import torch
+    out = {"gpu": torch.cuda.get_device_name(0)}
+    for name, dt, n, tf32 in [("fp64", torch.float64, 8192, False), ("fp32_simt", torch.float32, 8192, False),
+                              ("tf32", torch.float32, 8192, True), ("bf16", torch.bfloat16, 8192, False)]:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dt)
+        b = torch.randn(n, n, device="cuda", dtype=dt)
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        best = 1e9
+        for _ in range(5):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(); a @ b; e.record(); torch.cuda.synchronize()
+            best = min(best, s.elapsed_time(e) / 1e3)
+        out[name + "_tflops"] = 2.0 * n ** 3 / best / 1e12
+    out["host_cores"] = len(os.sched_getaffinity(0))
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg, sysd = make_inputs(args.workload)
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        v, info = cpu_sample(cfg, sysd, args.cpu_sample_q)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/iteration",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": workload_config(cfg, args.workload, "fp64-oracle"),
+            "cpu_baseline": {"value": value, "unit": "s/iteration", "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": value, "unit": "s/iteration", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_config(cfg, name, precision):
+    nk = cfg["kmesh"][0] * cfg["kmesh"][1] * cfg["kmesh"][2]
+    return {"workload": "%s: nao=%d naux=%d k-mesh %dx%dx%d (nk=%d) ntau=nw=%d beta=%g, %s contractions, "
+                        "fp64 screened solve/transforms/Dyson/mu" % (name, cfg["nao"], cfg["naux"], *cfg["kmesh"], nk,
+                                                                     cfg["ntau"], cfg["beta"], precision),
+            "nao": cfg["nao"], "naux": cfg["naux"], "nk": nk, "ntau": cfg["ntau"], "beta": cfg["beta"],
+            "contract_precision": precision, "l2": "inputs larger than L2 (V is %.2f GB)" %
+            (nk * nk * cfg["naux"] * cfg["nao"] ** 2 * 16 / 1e9), "parallelism": "single GPU"}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gw(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2206_07660_gb300 import GW
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # replicas: each rank runs its own seeded system of the same workload
+    cfg, sysd = make_inputs(args.workload, seed_offset=rank)
+    fl = flops(cfg)
+    g = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
+           sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision=args.precision)
+    g.dyson()
+    G0 = g.get("G_tau")
+    mu0 = g.get("mu")
+    for _ in range(args.warmup):
+        g.iterate(1)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    l0 = g.kernel_launches()
+    g.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stage = {"ms_polarization": 0.0, "ms_screened": 0.0, "ms_selfenergy": 0.0, "ms_dyson": 0.0}
+    last = None
+    for _ in range(args.steps):
+        last = g.iterate(1)
+        for kk in stage:
+            stage[kk] += last[kk]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    gemm_ms, gemm_flops, gemm_launches = g.profile_read()
+    g.profile(False)
+    launches = g.kernel_launches() - l0
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    s_per_iter = ms / args.steps / 1e3
+    K = args.steps
+    p_tflops = fl["P0"] / (stage["ms_polarization"] / K / 1e3) / 1e12
+    s_tflops = fl["Sigma"] / (stage["ms_selfenergy"] / K / 1e3) / 1e12
+
+    # fp64 path from the same G0: one iteration for the comparison and the Sigma error
+    extra = {}
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        sig_mixed = None
+        g.set("G_tau", G0); g.set("mu", mu0); g.reset_sigma()
+        g.iterate(1)
+        sig_mixed = (g.get("Sigma_inf"), g.get("Sigma_tau"))
+        g64 = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
+                 sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision="fp64")
+        g64.set("G_tau", G0); g64.set("mu", mu0)
+        t64 = []
+        for i in range(args.fp64_steps):
+            st64 = g64.iterate(1)
+            t64.append(st64["ms_total"] / 1e3)
+            if i == 0:
+                err_inf = float(np.abs(sig_mixed[0] - g64.get("Sigma_inf")).max())
+                err_tau = float(np.abs(sig_mixed[1] - g64.get("Sigma_tau")).max())
+                p64 = fl["P0"] / (st64["ms_polarization"] / 1e3) / 1e12
+                s64 = fl["Sigma"] / (st64["ms_selfenergy"] / 1e3) / 1e12
+        g64.close()
+        extra = {"fp64_path": {"s_per_iteration": statistics.median(t64), "P_tflops": p64, "Sigma_tflops": s64,
+                               "steps": args.fp64_steps},
+                 "mixed_speedup_over_fp64": statistics.median(t64) / s_per_iter,
+                 "sigma_err_Ha": {"Sigma_inf": err_inf, "Sigma_tilde_tau": err_tau,
+                                  "against": "fp64 GPU path from the same G (itself matched to the fp64 "
+                                             "oracle to 1e-10 Ha in the parity tests)"}}
+
+    # end to end through the public API: G in from pinned host memory, G and Sigma out
+    e2e_t = []
+    hG = torch.from_numpy(G0).pin_memory()
+    outG = torch.empty_like(hG).pin_memory()
+    outS = torch.empty(g.shape_of("Sigma_iw"), dtype=torch.complex128).pin_memory()
+    g.reset_sigma()
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set("G_tau", hG)
+        g.iterate(1)
+        g.get("G_tau", out=outG)
+        g.get("Sigma_iw", out=outS)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": statistics.median(e2e_t), "unit": "s/iteration",
+           "h2d_bytes_per_step": hG.numel() * 16, "d2h_bytes_per_step": (outG.numel() + outS.numel()) * 16}
+
+    peak = (SM_COUNT * (FP32_FLOPS_PER_CLK_SM if args.precision == "fp32" else FP64_FLOPS_PER_CLK_SM)
+            * SM_MAX_MHZ * 1e6 / 1e12)
+    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
+    traffic = traffic_from_profiles(args.workload, args.precision)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "gett_kernel<%s> (complex contraction, SIMT FMA)" % args.precision,
+            "launches": gemm_launches, "algorithmic_flops_per_launch": gemm_flops / max(1, gemm_launches),
+            "avg_launch_ms": gemm_ms / max(1, gemm_launches),
+            "peak_basis": "152 SMs x %d flop/clk x 2070 MHz (unit counts and max SM clock)" %
+                          (FP32_FLOPS_PER_CLK_SM if args.precision == "fp32" else FP64_FLOPS_PER_CLK_SM)}
+    line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iteration", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64" if args.precision == "fp32" else "c128", "data": "synthetic",
+            "config": workload_config(cfg, args.workload, args.precision),
+            "P_tflops": p_tflops, "Sigma_tflops": s_tflops,
+            "stage_ms_per_iteration": {k: v / K for k, v in stage.items()},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "e2e": e2e}
+    line.update(extra)
+    g.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, info = cpu_sample(cfg, sysd, args.cpu_sample_q)
+        line["cpu_baseline"] = {"value": v, "unit": "s/iteration", "cores": info["cores"], "kind": "oracle",
+                                "sample": info["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.peaks:
+        return measure_peaks()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gw(args)
+
+
+if __name__ == "__main__":
+    main()

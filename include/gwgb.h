@@ -1,0 +1,207 @@
+/*
+ * gwgb.h -- C ABI of a single-GPU (GB300, sm_103a) library for fully
+ * self-consistent finite-temperature GW in Gaussian Bloch orbitals with
+ * density-fitted Coulomb integrals (Yeh, Iskakov, Zgid, Gull, "Fully
+ * Self-Consistent Finite-Temperature GW in Gaussian Bloch Orbitals for
+ * Solids").
+ *
+ * Data conventions
+ *   - Complex arrays are interleaved (re, im) IEEE doubles, row-major.
+ *   - nk = kmesh[0]*kmesh[1]*kmesh[2]; k = (i1*kmesh[1] + i2)*kmesh[2] + i3
+ *     (Gamma-centred mesh); k+q and k-q are taken componentwise modulo the mesh.
+ *   - nw = ntau: the same number of sampled Matsubara points as tau nodes,
+ *     for both fermionic and bosonic functions.
+ *   - Layouts:  H0, S, Sigma_inf, gamma          [nk][nao][nao]
+ *               V^{k k'}_{ij}(Q)                 [nk][nk][naux][nao][nao]
+ *               G, Sigma~ (tau or i w)           [ntau][nk][nao][nao]
+ *               P~0, P~ (tau or i Omega)         [nq = nk][ntau][naux][naux]
+ *   - The tau grid is the first-kind Chebyshev roots on [0, beta]; a function
+ *     of tau is represented by the interpolating polynomial through its node
+ *     values.  The forward transform is the exact Fourier integral of that
+ *     interpolant at the sampled frequencies (Eq. tau_to_iw); the backward
+ *     transform is its exact inverse (stand-in for Eq. iw_to_tau).
+ *
+ * Ownership and errors
+ *   - Inputs are copied during gw_init (device pointers with GW_INPUT_DEVICE;
+ *     with GW_BORROW_V the V tensor is referenced, not copied, and must
+ *     outlive the context).  The caller keeps ownership of its buffers.
+ *   - Device memory comes from cfg->dev_alloc / dev_free when given (for
+ *     instance PyTorch's caching allocator), else from cudaMalloc / cudaFree.
+ *   - All work is enqueued on cfg->stream.  Calls that return a status which
+ *     depends on device results (gw_init's input checks, gw_dyson,
+ *     gw_screened, gw_iterate) synchronise that stream.
+ *   - No call aborts, traps or throws across the ABI.  On failure a call
+ *     returns a non-zero gw_status and gw_last_error() gives a message.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef GWGB_H
+#define GWGB_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gw_ctx gw_ctx;
+
+typedef enum {
+  GW_OK = 0,
+  GW_ERR_ARG = 1,            /* bad size, null pointer, input fails a check     */
+  GW_ERR_CUDA = 2,           /* a CUDA runtime call failed                      */
+  GW_ERR_OOM = 3,            /* device allocation failed                        */
+  GW_ERR_NOT_CONVERGED = 4,  /* chemical-potential search hit its step cap      */
+  GW_ERR_SINGULAR = 5,       /* zero pivot in a Dyson or screened-solve inverse */
+  GW_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                   */
+  GW_ERR_STATE = 7,          /* call out of order (e.g. no G yet)               */
+  GW_ERR_INTERNAL = 8
+} gw_status;
+
+/* Number format of the two dominant contractions (P~0 and Sigma~). */
+typedef enum {
+  GW_FP64 = 0,        /* complex128 throughout                                  */
+  GW_FP32 = 1,        /* complex64 products, fp32 accumulation per k-slab,
+                         fp64 accumulation across slabs                         */
+  GW_SPLIT_BF16 = 2,  /* reserved */
+  GW_SPLIT_TF32 = 3   /* reserved */
+} gw_precision;
+
+enum {
+  GW_INPUT_DEVICE = 1u << 0, /* H0, S, V passed to gw_init are device pointers   */
+  GW_BORROW_V     = 1u << 1, /* with GW_INPUT_DEVICE: use V in place, no copy     */
+  GW_SKIP_CHECKS  = 1u << 2  /* skip the Hermiticity / pairing checks of gw_init  */
+};
+
+typedef void* (*gw_alloc_fn)(void* user, size_t bytes);
+typedef void (*gw_free_fn)(void* user, void* ptr);
+
+typedef struct {
+  int32_t nao;            /* orbitals per cell                                    */
+  int32_t naux;           /* auxiliary (density-fitting) functions, Eq. U_decompose */
+  int32_t kmesh[3];       /* Gamma-centred k-mesh                                 */
+  int32_t ntau;           /* tau nodes = sampled Matsubara points                 */
+  double beta;            /* inverse temperature (1/Ha)                           */
+  double n_elec;          /* electrons per cell (half filling: nao)               */
+  double mu_tol;          /* |N(mu) - n_elec| threshold; the paper uses 1e-9      */
+  int32_t mu_maxit;       /* cap on N(mu) evaluations -> GW_ERR_NOT_CONVERGED     */
+  double damping;         /* alpha of Sigma <- (1-alpha) Sigma_old + alpha Sigma_new */
+  int32_t contract_prec;  /* gw_precision of the P~0 and Sigma~ contractions       */
+  int32_t spin_factor;    /* s = 2 for a spin-restricted closed shell             */
+  const int32_t* fermi_n; /* [ntau] host: sampled fermionic n, w_n = (2n+1) pi/beta */
+  const int32_t* bose_m;  /* [ntau] host: sampled bosonic m, Omega_m = 2 m pi/beta  */
+  void* stream;           /* cudaStream_t; NULL = legacy default stream           */
+  gw_alloc_fn dev_alloc;  /* optional device allocator                            */
+  gw_free_fn dev_free;
+  void* alloc_user;
+  uint64_t flags;         /* GW_INPUT_DEVICE | GW_BORROW_V | GW_SKIP_CHECKS        */
+} gw_config;
+
+/* Quantities readable with gw_get / writable with gw_set.  Sizes in bytes. */
+typedef enum {
+  GW_Q_G_TAU = 0,      /* [ntau][nk][nao][nao] c128  (get, set)                 */
+  GW_Q_G_IW = 1,       /* [nw][nk][nao][nao]   c128  (get)                      */
+  GW_Q_SIGMA_INF = 2,  /* [nk][nao][nao]       c128  (get, set) static part      */
+  GW_Q_SIGMA_TAU = 3,  /* [ntau][nk][nao][nao] c128  (get)                      */
+  GW_Q_SIGMA_IW = 4,   /* [nw][nk][nao][nao]   c128  (get, set) dynamic part     */
+  GW_Q_P0_TAU = 5,     /* [nq][ntau][naux][naux] c128 (get, set)                */
+  GW_Q_P0_IW = 6,      /* [nq][nw][naux][naux]  c128 (get, set); overwritten by
+                          gw_screened, which leaves P~(i Omega) in its place    */
+  GW_Q_P_IW = 7,       /* same buffer as GW_Q_P0_IW after gw_screened (get)     */
+  GW_Q_P_TAU = 8,      /* [nq][ntau][naux][naux] c128 (get, set)                */
+  GW_Q_GAMMA = 9,      /* [nk][nao][nao] c128 density matrix (get)              */
+  GW_Q_MU = 10,        /* double (get, set)                                     */
+  GW_Q_TFF = 11,       /* [nw][ntau] c128 fermionic tau -> i w   (get)          */
+  GW_Q_TBF = 12,       /* [ntau][nw] c128 fermionic i w -> tau   (get)          */
+  GW_Q_TFB = 13,       /* [nw][ntau] c128 bosonic tau -> i Omega (get)          */
+  GW_Q_TBB = 14,       /* [ntau][nw] c128 bosonic i Omega -> tau (get)          */
+  GW_Q_LB = 15,        /* [ntau] double  L_j(beta^-)             (get)          */
+  GW_Q_TAU = 16,       /* [ntau] double  tau nodes               (get)          */
+  GW_Q_N_ELEC = 17,    /* double electron count at the last mu   (get)          */
+  GW_Q_SIGMA_INF_NEW = 18 /* [nk][nao][nao] c128 last HF result before mixing (get) */
+} gw_quantity;
+
+typedef struct {
+  double mu;          /* chemical potential after the iteration               */
+  double n_elec;      /* N(mu) reached                                        */
+  int32_t mu_steps;   /* N(mu) evaluations of the search                      */
+  double max_dG;      /* max |G_new(tau) - G_old(tau)|                        */
+  double max_dSigma;  /* max |Sigma~_new(i w) - Sigma~_old(i w)| before mixing */
+  float ms_total;     /* device time of the iteration                         */
+  float ms_polarization, ms_screened, ms_selfenergy, ms_dyson, ms_hf;
+} gw_iter_stats;
+
+/* Create a context: validates sizes, copies H0, S (Eq. scalar_S) and V (Eq.
+ * U_decompose), builds the tau grid, the transform matrices and the density
+ * weights on the device.  Unless GW_SKIP_CHECKS, rejects with GW_ERR_ARG
+ * inputs where H0 or S is not Hermitian or V^{k'k}(Q) != V^{kk'}(Q)^H beyond
+ * 1e-10 relative.  Synchronises cfg->stream.  *out is NULL on failure. */
+gw_status gw_init(const gw_config* cfg, const double* H0, const double* S, const double* V,
+                  gw_ctx** out);
+
+/* Free every device buffer of the context (borrowed V excepted). */
+gw_status gw_destroy(gw_ctx* ctx);
+
+/* Copy a quantity in (gw_set) or out (gw_get).  `bytes` must equal the size
+ * listed for it in gw_quantity.  on_device != 0: src/dst is a device pointer.
+ * gw_get synchronises the stream when dst is a host pointer. */
+gw_status gw_set(gw_ctx* ctx, gw_quantity which, const void* src, size_t bytes, int on_device);
+gw_status gw_get(gw_ctx* ctx, gw_quantity which, void* dst, size_t bytes, int on_device);
+
+/* Static self-energy (Sec. "Hartree-Fock self-energy"): gamma^k = -G^k(beta^-)
+ * from the current G(tau), then Sigma_inf = J + K (Eqs. HF_J, HF_K), stored as
+ * GW_Q_SIGMA_INF_NEW.  Requires G. */
+gw_status gw_hf(gw_ctx* ctx);
+
+/* P~0^q(tau) for all q (Eq. tilde_P0_tau; P~0 = (s/Nk) sum V G^{k+q}(tau) V
+ * G^k(-tau), G(-tau) = -G(beta - tau)), Hermitian-symmetrised, then its bosonic
+ * transform P~0^q(i Omega_m) (Eq. P0t_to_P0w).  Requires G. */
+gw_status gw_polarization(gw_ctx* ctx);
+
+/* Screened solve P~ = [I - P~0(i Omega)]^{-1} P~0(i Omega) for every (q, m)
+ * (Eq. tilde_P_omega), then P~^q(tau) (Eq. Piw_to_Pt), Hermitian-symmetrised.
+ * Returns GW_ERR_SINGULAR on a zero pivot.  Synchronises. */
+gw_status gw_screened(gw_ctx* ctx);
+
+/* Sigma~^k(tau) = -(1/Nk) sum_q sum V^{k,k-q} G^{k-q}(tau) P~^q(tau) V^{k-q,k}
+ * (Eq. tilde_sigma2), symmetrised, its fermionic transform Sigma~(i w), and the
+ * static part of gw_hf.  The self-energy used by the next gw_dyson becomes
+ * (1-damping) Sigma_old + damping Sigma_new when an earlier self-energy exists
+ * (else Sigma_new).  Requires G and P~(tau). */
+gw_status gw_selfenergy(gw_ctx* ctx);
+
+/* Dyson equation (Eq. Dyson) with chemical-potential search: bisection on
+ * N(mu) = (s/Nk) sum_k tr[gamma^k S^k] until |N - n_elec| <= mu_tol and the
+ * bracket is below 1e-13, then G(i w) = [(i w + mu) S - H0 - Sigma_inf -
+ * Sigma~(i w)]^{-1} and G(tau) (symmetrised).  With no self-energy set this is
+ * the non-interacting G0.  Synchronises.  mu_out may be NULL. */
+gw_status gw_dyson(gw_ctx* ctx, double* mu_out);
+
+/* n_iter full GW iterations from the current G (computing G0 first when no G
+ * exists): gw_hf, gw_polarization, gw_screened, gw_selfenergy, gw_dyson.
+ * stats_out (may be NULL) receives the record of the last iteration. */
+gw_status gw_iterate(gw_ctx* ctx, int32_t n_iter, gw_iter_stats* stats_out);
+
+/* Drop the stored self-energy so that the next gw_selfenergy is not mixed. */
+gw_status gw_reset_sigma(gw_ctx* ctx);
+
+/* Message of the last failure of this context (or of gw_init when ctx is NULL). */
+const char* gw_last_error(const gw_ctx* ctx);
+
+/* Number of kernels the library has launched so far (all contexts). */
+int64_t gw_kernel_launches(const gw_ctx* ctx);
+
+/* Per-launch timing of the contraction kernel that carries Eqs. tilde_P0_tau,
+ * tilde_sigma2 and HF_K: with enable != 0 every launch is bracketed by CUDA
+ * events on cfg->stream (a few microseconds of overhead per launch).
+ * Synchronises and resets the accumulators. */
+gw_status gw_profile(gw_ctx* ctx, int enable);
+
+/* Reads and resets the accumulators of gw_profile: out3[0] = summed device
+ * milliseconds of the timed launches, out3[1] = their complex-MAC flops
+ * (8 M N K per launch), out3[2] = number of launches.  Synchronises. */
+gw_status gw_profile_read(gw_ctx* ctx, double* out3);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GWGB_H */

@@ -14,10 +14,15 @@ and iw_to_tau; Sec. "Representation on the imaginary axes"):
   The Lagrange basis L_j is written through its Chebyshev series,
   L_j(x) = sum_k C[k, j] T_k(x), C[k, j] = (2 - delta_k0)/ntau * T_k(x_j).
 * The forward transform is Eq. tau_to_iw applied to that interpolant:
-  TF[n, j] = int_0^beta L_j(tau) exp(i nu_n tau) dtau, evaluated by
-  Gauss-Legendre quadrature with enough points to be exact to roundoff for
-  the polynomial-times-exponential integrand.  nu_n = (2n+1) pi / beta for
-  fermions and 2 n pi / beta for bosons; the sampled integers n are inputs.
+  TF[n, j] = int_0^beta L_j(tau) exp(i nu_n tau) dtau.  With tau = (beta/2)(1+x)
+  and a = nu beta / 2 this is (beta/2) e^{i a} sum_k C[k, j] I_k(a), where the
+  Chebyshev moments I_k(a) = int_{-1}^{1} T_k(x) e^{i a x} dx are summed from
+  the Jacobi-Anger expansion e^{i a x} = sum_m eps_m i^m J_m(a) T_m(x) and the
+  exact integrals int T_k T_m dx (Bessel values from scipy.special.jv).  This
+  keeps full double accuracy at large a, where a quadrature's node rounding
+  is amplified by a.  a = (2n+1) pi/2 for fermions and m pi for bosons, so the
+  matrices depend on beta only through the prefactor beta/2; the sampled
+  integers n, m are inputs.  A Gauss-Legendre version is kept for checks.
 * The backward transform is the exact inverse on the sampled frequencies,
   TB = TF^{-1}: the unique interpolant whose Fourier integrals reproduce the
   sampled values (the discrete stand-in for the Matsubara sum of
@@ -57,8 +62,45 @@ def lagrange_eval(x, ntau):
     return T @ C
 
 
+def cheb_moments(a, nmom):
+    """I[f, k] = int_{-1}^{1} T_k(x) e^{i a_f x} dx, k < nmom (Jacobi-Anger series)."""
+    from scipy.special import jv
+    a = np.asarray(a, dtype=np.float64)
+    out = np.zeros((len(a), nmom), dtype=np.complex128)
+    k = np.arange(nmom)
+    for f, af in enumerate(a):
+        mmax = int(abs(af) + 20 * abs(af) ** (1.0 / 3.0) + 40) + nmom
+        m = np.arange(mmax + 1)
+        eps = np.where(m == 0, 1.0, 2.0)
+        c = eps * (1j ** (m % 4)) * jv(m, af)            # e^{iax} = sum_m c_m T_m(x)
+        kk, mm = k[:, None], m[None, :]
+        even = ((kk + mm) % 2 == 0)
+        with np.errstate(divide="ignore"):
+            W = np.where(even, 1.0 / (1.0 - (kk + mm) ** 2.0) + 1.0 / (1.0 - (kk - mm) ** 2.0), 0.0)
+        out[f] = W @ c
+    return out
+
+
+def fourier_matrix_ja(beta, ntau, a):
+    """TF[n, j] from the half-angle arguments a_n (exact e^{i a} for a = integer * pi/2)."""
+    a = np.asarray(a, dtype=np.float64)
+    I = cheb_moments(a, ntau)                               # [n, k]
+    C = lagrange_cheb_coeffs(ntau)                          # [k, j]
+    return (beta / 2.0) * np.exp(1j * a)[:, None] * (I @ C)
+
+
+def fermionic_a(n):
+    """a = w_n beta / 2 = (2n+1) pi / 2."""
+    return (2 * np.asarray(n, dtype=np.float64) + 1) * (np.pi / 2)
+
+
+def bosonic_a(m):
+    """a = Omega_m beta / 2 = m pi."""
+    return np.asarray(m, dtype=np.float64) * np.pi
+
+
 def fourier_matrix(beta, ntau, nu, npts=None):
-    """TF[n, j] = int_0^beta L_j(tau) exp(i nu_n tau) dtau (Eq. tau_to_iw).
+    """Gauss-Legendre evaluation of TF[n, j] = int_0^beta L_j(tau) exp(i nu_n tau) dtau.
 
     With tau = (beta/2)(1+x):  TF = (beta/2) e^{i a} int_{-1}^{1} L_j(x) e^{i a x} dx,
     a = nu beta / 2.  Gauss-Legendre with npts points; the default is large
@@ -94,8 +136,8 @@ class Grid:
         self.tau = tau_nodes(beta, ntau)
         self.wf = fermionic_freqs(beta, self.fermi_n)
         self.wb = bosonic_freqs(beta, self.bose_m)
-        self.TFf = fourier_matrix(beta, ntau, self.wf)
-        self.TFb = fourier_matrix(beta, ntau, self.wb)
+        self.TFf = fourier_matrix_ja(beta, ntau, fermionic_a(self.fermi_n))
+        self.TFb = fourier_matrix_ja(beta, ntau, bosonic_a(self.bose_m))
         self.TBf = np.linalg.inv(self.TFf)
         self.TBb = np.linalg.inv(self.TFb)
         ends = lagrange_eval(np.array([-1.0, 1.0]), ntau)

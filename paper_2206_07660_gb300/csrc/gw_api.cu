@@ -1,0 +1,681 @@
+// C ABI of the library (declared in include/gwgb.h): context, buffers and
+// the stage drivers of one self-consistent GW iteration.  Every arithmetic
+// step runs in the kernels of this directory; the host only sequences
+// launches on the caller's stream.
+#include <stdio.h>
+#include <string.h>
+#include <math.h>
+#include <new>
+#include <string>
+#include <vector>
+#include <atomic>
+#include "gw_internal.cuh"
+
+using namespace gwk;
+
+namespace gwk { std::atomic<long long> g_launches{0}; }
+
+struct gw_ctx {
+  gw_config cfg{};
+  int nao = 0, naux = 0, nk = 0, ntau = 0, nw = 0;
+  int64_t n2 = 0, na2 = 0;
+  double spin = 2.0;
+  cudaStream_t st = nullptr;
+  std::string err;
+  std::vector<int> kplus, kminus;  // [q * nk + k]
+  std::vector<void*> owned;
+  // inputs
+  double2 *H0 = nullptr, *S = nullptr, *V = nullptr;
+  float2* V32 = nullptr;
+  // grid
+  double *tau = nullptr, *lb = nullptr, *l0 = nullptr, *wn = nullptr;
+  double2 *TFf = nullptr, *TBf = nullptr, *TFb = nullptr, *TBb = nullptr, *r = nullptr;
+  int *d_fn = nullptr, *d_bm = nullptr;
+  // state
+  double2 *G_tau = nullptr, *G_iw = nullptr, *G_prev = nullptr, *gamma = nullptr, *tQ = nullptr;
+  double2 *Sinf = nullptr, *Sinf_new = nullptr, *Siw = nullptr, *Siw_new = nullptr, *Stau = nullptr;
+  double2 *P0_tau = nullptr, *P_iw = nullptr, *P_tau = nullptr;
+  // chain intermediates and workspaces
+  void *chA = nullptr, *chB = nullptr;
+  size_t ch_bytes = 0;
+  float2 *G32 = nullptr, *P32 = nullptr, *gam32 = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* partial = nullptr;
+  MuState* mus = nullptr;
+  MuState* h_mus = nullptr;  // pinned
+  int* info = nullptr;
+  double* dscr = nullptr;    // small device scratch (max reductions)
+  double* h_scr = nullptr;   // pinned
+  double mu = 0.0, n_at_mu = 0.0;
+  int mu_steps = 0;
+  bool have_G = false, have_mu = false, have_sigma = false, have_P0 = false, have_P = false;
+  cudaEvent_t ev[8]{};
+  // optional per-launch timing of the contraction kernel (gw_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> pev;
+  size_t pused = 0;
+  double pflops = 0.0;
+  int64_t plaunch = 0;
+};
+
+static thread_local std::string g_init_err;
+
+#define CK(x)                                                                        \
+  do {                                                                               \
+    cudaError_t e_ = (x);                                                            \
+    if (e_ != cudaSuccess) return fail(c, GW_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static gw_status fail(gw_ctx* c, gw_status s, const std::string& m) {
+  if (c) c->err = m; else g_init_err = m;
+  return s;
+}
+
+static void* dalloc(gw_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (c->cfg.dev_alloc) p = c->cfg.dev_alloc(c->cfg.alloc_user, bytes);
+  else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+  if (p) c->owned.push_back(p);
+  return p;
+}
+
+static void free_all(gw_ctx* c) {
+  if (c->st) cudaStreamSynchronize(c->st); else cudaDeviceSynchronize();
+  for (void* p : c->owned) {
+    if (c->cfg.dev_free) c->cfg.dev_free(c->cfg.alloc_user, p); else cudaFree(p);
+  }
+  c->owned.clear();
+  if (c->h_mus) cudaFreeHost(c->h_mus);
+  if (c->h_scr) cudaFreeHost(c->h_scr);
+  c->h_mus = nullptr; c->h_scr = nullptr;
+  for (auto& e : c->ev) if (e) { cudaEventDestroy(e); e = nullptr; }
+  for (auto& e : c->pev) cudaEventDestroy(e);
+  c->pev.clear();
+}
+
+static inline void count(int n) { g_launches += n; }
+
+static cudaError_t run_gett(const GettDesc& d, const void* A, Ty ta, const void* B, Ty tb, void* C, Ty tc, Ty acc,
+                            gw_ctx* c) {
+  count(d.ksplit > 1 ? 2 : 1);
+  if (!c->prof) return gett(d, A, ta, B, tb, C, tc, acc, c->ws, c->ws_bytes, c->st);
+  while (c->pev.size() < c->pused + 2) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    c->pev.push_back(e);
+  }
+  cudaEventRecord(c->pev[c->pused], c->st);
+  cudaError_t r = gett(d, A, ta, B, tb, C, tc, acc, c->ws, c->ws_bytes, c->st);
+  cudaEventRecord(c->pev[c->pused + 1], c->st);
+  c->pused += 2;
+  c->pflops += 8.0 * (double)d.M * (double)d.N * (double)d.K * (double)d.Z;
+  c->plaunch += 1;
+  return r;
+}
+
+static GettDesc base_desc(int64_t M, int64_t N, int64_t K, int64_t Z) {
+  GettDesc d{};
+  d.M = M; d.N = N; d.K = K; d.Z = Z;
+  d.az = d.bz = d.cz = I1(0);
+  d.alpha = make_double2(1, 0); d.beta = make_double2(0, 0);
+  d.ksplit = 1;
+  return d;
+}
+
+// Y[z] = T (nrow x ntau) * X[z] (ntau x ncol): transforms along the tau axis.
+static cudaError_t transform(gw_ctx* c, const double2* T, const double2* X, double2* Y, int64_t nrow, int64_t ncol,
+                             int64_t batch, int64_t xstride, int64_t ystride) {
+  GettDesc d = base_desc(nrow, ncol, c->ntau, batch);
+  d.am = I1(c->ntau); d.ak = I1(1);
+  d.bk = I1(ncol); d.bn = I1(1); d.bz = I1(xstride);
+  d.cm = I1(ncol); d.cn = I1(1); d.cz = I1(ystride);
+  return run_gett(d, T, Ty::C128, X, Ty::C128, Y, Ty::C128, Ty::C128, c);
+}
+
+static int kidx(const int* m, int a, int b, int cc) {
+  return ((a % m[0] + m[0]) % m[0] * m[1] + (b % m[1] + m[1]) % m[1]) * m[2] + (cc % m[2] + m[2]) % m[2];
+}
+
+// ------------------------------------------------------------------ init / destroy
+
+extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const double* S, const double* V,
+                             gw_ctx** out) {
+  if (!out) return fail(nullptr, GW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !H0 || !S || !V) return fail(nullptr, GW_ERR_ARG, "null config or input pointer");
+  if (cfg->nao <= 0 || cfg->naux <= 0 || cfg->ntau <= 0 || cfg->kmesh[0] <= 0 || cfg->kmesh[1] <= 0 ||
+      cfg->kmesh[2] <= 0)
+    return fail(nullptr, GW_ERR_ARG, "sizes must be positive");
+  if (cfg->nao > 96) return fail(nullptr, GW_ERR_ARG, "nao > 96 is not supported by the Dyson kernel");
+  if (!(cfg->beta > 0) || !cfg->fermi_n || !cfg->bose_m) return fail(nullptr, GW_ERR_ARG, "bad beta or index sets");
+  if (cfg->contract_prec != GW_FP64 && cfg->contract_prec != GW_FP32)
+    return fail(nullptr, GW_ERR_ARG, "contract_prec not available");
+  if ((cfg->flags & GW_BORROW_V) && !(cfg->flags & GW_INPUT_DEVICE))
+    return fail(nullptr, GW_ERR_ARG, "GW_BORROW_V needs GW_INPUT_DEVICE");
+  for (int i = 0; i < cfg->ntau; ++i)
+    for (int j = i + 1; j < cfg->ntau; ++j)
+      if (cfg->fermi_n[i] == cfg->fermi_n[j] || cfg->bose_m[i] == cfg->bose_m[j])
+        return fail(nullptr, GW_ERR_ARG, "repeated Matsubara index");
+  gw_ctx* c = new (std::nothrow) gw_ctx();
+  if (!c) return fail(nullptr, GW_ERR_OOM, "host allocation failed");
+  c->cfg = *cfg;
+  c->nao = cfg->nao; c->naux = cfg->naux; c->ntau = cfg->ntau; c->nw = cfg->ntau;
+  c->nk = cfg->kmesh[0] * cfg->kmesh[1] * cfg->kmesh[2];
+  c->n2 = (int64_t)c->nao * c->nao; c->na2 = (int64_t)c->naux * c->naux;
+  c->spin = cfg->spin_factor > 0 ? cfg->spin_factor : 2;
+  c->st = (cudaStream_t)cfg->stream;
+  if (c->cfg.mu_tol <= 0) c->cfg.mu_tol = 1e-9;
+  if (c->cfg.mu_maxit <= 0) c->cfg.mu_maxit = 400;
+  const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
+  const int64_t n2 = c->n2, na2 = c->na2;
+  // k-mesh tables: k + q and k - q componentwise modulo the mesh
+  c->kplus.resize((size_t)nk * nk); c->kminus.resize((size_t)nk * nk);
+  const int* m = cfg->kmesh;
+  for (int q = 0; q < nk; ++q) {
+    int q1 = q / (m[1] * m[2]), q2 = (q / m[2]) % m[1], q3 = q % m[2];
+    for (int k = 0; k < nk; ++k) {
+      int k1 = k / (m[1] * m[2]), k2 = (k / m[2]) % m[1], k3 = k % m[2];
+      c->kplus[(size_t)q * nk + k] = kidx(m, k1 + q1, k2 + q2, k3 + q3);
+      c->kminus[(size_t)q * nk + k] = kidx(m, k1 - q1, k2 - q2, k3 - q3);
+    }
+  }
+  auto A = [&](size_t bytes) { return dalloc(c, bytes); };
+  const size_t cb = sizeof(double2);
+  const size_t vbytes = (size_t)nk * nk * naux * n2 * cb;
+  bool ok = true;
+  auto need = [&](void* p) { ok = ok && p != nullptr; return p; };
+  c->H0 = (double2*)need(A(nk * n2 * cb));
+  c->S = (double2*)need(A(nk * n2 * cb));
+  if (cfg->flags & GW_BORROW_V) c->V = (double2*)V;
+  else c->V = (double2*)need(A(vbytes));
+  if (cfg->contract_prec == GW_FP32) c->V32 = (float2*)need(A(vbytes / 2));
+  c->tau = (double*)need(A(ntau * 8)); c->lb = (double*)need(A(ntau * 8)); c->l0 = (double*)need(A(ntau * 8));
+  c->wn = (double*)need(A(ntau * 8));
+  c->TFf = (double2*)need(A((size_t)ntau * ntau * cb)); c->TBf = (double2*)need(A((size_t)ntau * ntau * cb));
+  c->TFb = (double2*)need(A((size_t)ntau * ntau * cb)); c->TBb = (double2*)need(A((size_t)ntau * ntau * cb));
+  c->r = (double2*)need(A(ntau * cb));
+  c->d_fn = (int*)need(A(ntau * 4)); c->d_bm = (int*)need(A(ntau * 4));
+  const size_t gsz = (size_t)ntau * nk * n2 * cb;
+  c->G_tau = (double2*)need(A(gsz)); c->G_iw = (double2*)need(A(gsz)); c->G_prev = (double2*)need(A(gsz));
+  c->Stau = (double2*)need(A(gsz)); c->Siw = (double2*)need(A(gsz)); c->Siw_new = (double2*)need(A(gsz));
+  c->gamma = (double2*)need(A(nk * n2 * cb)); c->tQ = (double2*)need(A(naux * cb));
+  c->Sinf = (double2*)need(A(nk * n2 * cb)); c->Sinf_new = (double2*)need(A(nk * n2 * cb));
+  const size_t psz = (size_t)nk * ntau * na2 * cb;
+  c->P0_tau = (double2*)need(A(psz)); c->P_iw = (double2*)need(A(psz)); c->P_tau = (double2*)need(A(psz));
+  // chain intermediates: max(ntau * naux * n2, nk * naux * n2) complex of the contraction type
+  size_t chn = (size_t)(ntau > nk ? ntau : nk) * naux * n2;
+  c->ch_bytes = chn * (cfg->contract_prec == GW_FP32 ? 8 : 16);
+  c->chA = need(A(c->ch_bytes)); c->chB = need(A(c->ch_bytes));
+  if (cfg->contract_prec == GW_FP32) {
+    c->G32 = (float2*)need(A(gsz / 2)); c->P32 = (float2*)need(A(psz / 2));
+    c->gam32 = (float2*)need(A(nk * n2 * 8));
+  }
+  // workspace: split-K partials and the screened-solve panels
+  size_t ws = screened_work_bytes(naux, (int64_t)nk * ntau);
+  const size_t ws_cap = (size_t)4 << 30;
+  size_t ws_min = screened_work_bytes(naux, 1) * 8;
+  if (ws > ws_cap) ws = ws_cap;
+  if (ws < ws_min) ws = ws_min;
+  size_t splitk = (size_t)64 * ntau * n2 * cb;          // Sigma last contraction, ksplit <= 64
+  size_t splitk2 = (size_t)64 * nk * n2 * cb;           // exchange
+  if (ws < splitk) ws = splitk;
+  if (ws < splitk2) ws = splitk2;
+  int ld = 0;
+  size_t gws = grid_ws_bytes(ntau, cfg->fermi_n, cfg->bose_m, &ld);
+  if (ws < gws) ws = gws;
+  c->ws_bytes = ws;
+  c->ws = need(A(ws));
+  c->partial = (double*)need(A((size_t)ntau * nk * 8));
+  c->mus = (MuState*)need(A(sizeof(MuState)));
+  c->info = (int*)need(A(64));
+  c->dscr = (double*)need(A(64 * 8));
+  if (!ok) { free_all(c); delete c; return fail(nullptr, GW_ERR_OOM, "device allocation failed"); }
+  if (cudaMallocHost(&c->h_mus, sizeof(MuState)) != cudaSuccess ||
+      cudaMallocHost(&c->h_scr, 64 * 8) != cudaSuccess) {
+    free_all(c); delete c; return fail(nullptr, GW_ERR_OOM, "pinned allocation failed");
+  }
+  for (auto& e : c->ev) cudaEventCreate(&e);
+  cudaStream_t st = c->st;
+  cudaMemcpyKind kind = (cfg->flags & GW_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  gw_status s = GW_OK;
+  auto chk = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && s == GW_OK) { s = GW_ERR_CUDA; c->err = std::string(what) + ": " + cudaGetErrorString(e); }
+  };
+  chk(cudaMemcpyAsync(c->H0, H0, nk * n2 * cb, kind, st), "H0 copy");
+  chk(cudaMemcpyAsync(c->S, S, nk * n2 * cb, kind, st), "S copy");
+  if (!(cfg->flags & GW_BORROW_V)) chk(cudaMemcpyAsync(c->V, V, vbytes, kind, st), "V copy");
+  chk(cudaMemcpyAsync(c->d_fn, cfg->fermi_n, ntau * 4, cudaMemcpyHostToDevice, st), "index copy");
+  chk(cudaMemcpyAsync(c->d_bm, cfg->bose_m, ntau * 4, cudaMemcpyHostToDevice, st), "index copy");
+  chk(cudaMemsetAsync(c->info, 0, 64, st), "memset");
+  chk(cudaMemsetAsync(c->Sinf, 0, nk * n2 * cb, st), "memset");
+  chk(cudaMemsetAsync(c->Siw, 0, gsz, st), "memset");
+  // grid and transforms
+  chk(grid_build_ws(ntau, cfg->beta, c->d_fn, c->d_bm, ld, c->ws, c->tau, c->TFf, c->TFb, c->lb, c->l0, st), "grid");
+  count(4);
+  chk(cudaMemcpyAsync(c->TBf, c->TFf, (size_t)ntau * ntau * cb, cudaMemcpyDeviceToDevice, st), "copy");
+  chk(cudaMemcpyAsync(c->TBb, c->TFb, (size_t)ntau * ntau * cb, cudaMemcpyDeviceToDevice, st), "copy");
+  chk(invert_small_gj(c->TBf, ntau, c->info, st), "TBf");
+  chk(invert_small_gj(c->TBb, ntau, c->info, st), "TBb");
+  chk(density_weights(ntau, c->lb, c->TBf, c->r, st), "weights");
+  chk(fermi_freqs(ntau, cfg->beta, c->d_fn, c->wn, st), "freqs");
+  count(4);
+  if (cfg->contract_prec == GW_FP32) { chk(to_c64(c->V, c->V32, vbytes / cb, st), "V32"); count(1); }
+  // input checks
+  chk(cudaMemsetAsync(c->dscr, 0, 64 * 8, st), "memset");
+  if (!(cfg->flags & GW_SKIP_CHECKS)) {
+    chk(check_herm(c->H0, nao, nk, c->dscr, st), "check");
+    chk(check_herm(c->S, nao, nk, c->dscr + 2, st), "check");
+    chk(check_v_pairing(c->V, nk, naux, nao, c->dscr + 4, st), "check");
+    count(3);
+  }
+  chk(cudaMemcpyAsync(c->h_scr, c->dscr, 64 * 8, cudaMemcpyDeviceToHost, st), "copy");
+  int h_info = 0;
+  chk(cudaMemcpyAsync(&h_info, c->info, 4, cudaMemcpyDeviceToHost, st), "copy");
+  chk(cudaStreamSynchronize(st), "sync");
+  if (s == GW_OK && h_info) { s = GW_ERR_SINGULAR; c->err = "transform matrix is singular"; }
+  if (s == GW_OK && !(cfg->flags & GW_SKIP_CHECKS)) {
+    const double* h = c->h_scr;
+    if (h[0] > 1e-10 * (h[1] > 1 ? h[1] : 1)) { s = GW_ERR_ARG; c->err = "H0 is not Hermitian"; }
+    else if (h[2] > 1e-10 * (h[3] > 1 ? h[3] : 1)) { s = GW_ERR_ARG; c->err = "S is not Hermitian"; }
+    else if (h[4] > 1e-10 * (h[5] > 1e-300 ? h[5] : 1)) { s = GW_ERR_ARG; c->err = "V^{k'k}(Q) != V^{kk'}(Q)^H"; }
+  }
+  if (s != GW_OK) { g_init_err = c->err; free_all(c); delete c; return s; }
+  *out = c;
+  return GW_OK;
+}
+
+extern "C" gw_status gw_destroy(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  free_all(c);
+  delete c;
+  return GW_OK;
+}
+
+extern "C" const char* gw_last_error(const gw_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
+extern "C" int64_t gw_kernel_launches(const gw_ctx*) { return (int64_t)g_launches.load(); }
+
+// ------------------------------------------------------------------ get / set
+
+static bool qinfo(gw_ctx* c, gw_quantity q, void** p, size_t* bytes, bool* settable) {
+  const size_t cb = 16;
+  const size_t gsz = (size_t)c->ntau * c->nk * c->n2 * cb, ksz = (size_t)c->nk * c->n2 * cb;
+  const size_t psz = (size_t)c->nk * c->ntau * c->na2 * cb, tsz = (size_t)c->ntau * c->ntau * cb;
+  *settable = false;
+  switch (q) {
+    case GW_Q_G_TAU: *p = c->G_tau; *bytes = gsz; *settable = true; return true;
+    case GW_Q_G_IW: *p = c->G_iw; *bytes = gsz; return true;
+    case GW_Q_SIGMA_INF: *p = c->Sinf; *bytes = ksz; *settable = true; return true;
+    case GW_Q_SIGMA_INF_NEW: *p = c->Sinf_new; *bytes = ksz; return true;
+    case GW_Q_SIGMA_TAU: *p = c->Stau; *bytes = gsz; return true;
+    case GW_Q_SIGMA_IW: *p = c->Siw; *bytes = gsz; *settable = true; return true;
+    case GW_Q_P0_TAU: *p = c->P0_tau; *bytes = psz; *settable = true; return true;
+    case GW_Q_P0_IW: *p = c->P_iw; *bytes = psz; *settable = true; return true;
+    case GW_Q_P_IW: *p = c->P_iw; *bytes = psz; return true;
+    case GW_Q_P_TAU: *p = c->P_tau; *bytes = psz; *settable = true; return true;
+    case GW_Q_GAMMA: *p = c->gamma; *bytes = ksz; return true;
+    case GW_Q_TFF: *p = c->TFf; *bytes = tsz; return true;
+    case GW_Q_TBF: *p = c->TBf; *bytes = tsz; return true;
+    case GW_Q_TFB: *p = c->TFb; *bytes = tsz; return true;
+    case GW_Q_TBB: *p = c->TBb; *bytes = tsz; return true;
+    case GW_Q_LB: *p = c->lb; *bytes = (size_t)c->ntau * 8; return true;
+    case GW_Q_TAU: *p = c->tau; *bytes = (size_t)c->ntau * 8; return true;
+    default: return false;
+  }
+}
+
+extern "C" gw_status gw_set(gw_ctx* c, gw_quantity q, const void* src, size_t bytes, int on_device) {
+  if (!c || !src) return fail(c, GW_ERR_ARG, "null argument");
+  if (q == GW_Q_MU) {
+    if (bytes != 8 || on_device) return fail(c, GW_ERR_ARG, "mu is one host double");
+    c->mu = *(const double*)src; c->have_mu = true;
+    return GW_OK;
+  }
+  void* p; size_t nb; bool settable;
+  if (!qinfo(c, q, &p, &nb, &settable) || !settable) return fail(c, GW_ERR_ARG, "quantity is not settable");
+  if (bytes != nb) return fail(c, GW_ERR_ARG, "byte count does not match the quantity");
+  CK(cudaMemcpyAsync(p, src, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  if (!on_device) CK(cudaStreamSynchronize(c->st));
+  if (q == GW_Q_G_TAU) c->have_G = true;
+  if (q == GW_Q_P0_IW) c->have_P0 = true;
+  if (q == GW_Q_P_TAU) c->have_P = true;
+  if (q == GW_Q_SIGMA_INF || q == GW_Q_SIGMA_IW) c->have_sigma = true;
+  return GW_OK;
+}
+
+extern "C" gw_status gw_get(gw_ctx* c, gw_quantity q, void* dst, size_t bytes, int on_device) {
+  if (!c || !dst) return fail(c, GW_ERR_ARG, "null argument");
+  if (q == GW_Q_MU || q == GW_Q_N_ELEC) {
+    if (bytes != 8 || on_device) return fail(c, GW_ERR_ARG, "scalar is one host double");
+    *(double*)dst = q == GW_Q_MU ? c->mu : c->n_at_mu;
+    return GW_OK;
+  }
+  void* p; size_t nb; bool settable;
+  if (!qinfo(c, q, &p, &nb, &settable)) return fail(c, GW_ERR_ARG, "unknown quantity");
+  if (bytes != nb) return fail(c, GW_ERR_ARG, "byte count does not match the quantity");
+  CK(cudaMemcpyAsync(dst, p, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  if (!on_device) CK(cudaStreamSynchronize(c->st));
+  return GW_OK;
+}
+
+extern "C" gw_status gw_reset_sigma(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  c->have_sigma = false;
+  CK(cudaMemsetAsync(c->Sinf, 0, (size_t)c->nk * c->n2 * 16, c->st));
+  CK(cudaMemsetAsync(c->Siw, 0, (size_t)c->ntau * c->nk * c->n2 * 16, c->st));
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ A1: gamma, J, K
+
+static gw_status exchange(gw_ctx* c) {
+  // K^k_ij = -(1/Nk) sum_{k',Q,a,b} V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q)    (Eq. HF_K)
+  const int nk = c->nk, nao = c->nao, naux = c->naux;
+  const int64_t n2 = c->n2, slab = (int64_t)naux * n2;
+  const bool f32 = c->cfg.contract_prec == GW_FP32;
+  const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = f32 ? Ty::C64 : Ty::C128;
+  const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
+  const void* gp = c->gamma;
+  Ty tg = Ty::C128;
+  if (f32) { CK(to_c64(c->gamma, c->gam32, nk * n2, c->st)); count(1); gp = c->gam32; tg = Ty::C64; }
+  const size_t es = f32 ? 8 : 16;
+  for (int kp = 0; kp < nk; ++kp) {
+    // Y[k][i][Q][b] = sum_a V^{k k'}[Q][i][a] gamma^{k'}[a][b]    (batch over k)
+    GettDesc d = base_desc((int64_t)naux * nao, nao, nao, nk);
+    d.am = I1(nao); d.ak = I1(1); d.az = I1((int64_t)nk * slab);
+    d.bk = I1(nao); d.bn = I1(1); d.bz = I1(0);
+    d.cm = I2(nao, nao, (int64_t)naux * nao); d.cn = I1(1); d.cz = I1(slab);
+    const char* Vb = (const char*)Vp + (size_t)kp * slab * es;
+    const char* gb = (const char*)gp + (size_t)kp * n2 * es;
+    CK(run_gett(d, Vb, tv, gb, tg, c->chA, tv, acc, c));
+    // K[k][i][j] += -(1/Nk) sum_{(Q,b)} Y[k][i][(Q,b)] V^{k' k}[Q][b][j]
+    GettDesc e = base_desc(nao, nao, (int64_t)naux * nao, nk);
+    e.am = I1((int64_t)naux * nao); e.ak = I1(1); e.az = I1(slab);
+    e.bk = I1(nao); e.bn = I1(1); e.bz = I1(slab);
+    e.cm = I1(nao); e.cn = I1(1); e.cz = I1(n2);
+    e.alpha = make_double2(-1.0 / nk, 0); e.beta = make_double2(1, 0);
+    e.ksplit = 16;
+    const char* Vk = (const char*)Vp + (size_t)kp * nk * slab * es;
+    CK(run_gett(e, c->chA, tv, Vk, tv, c->Sinf_new, Ty::C128, acc, c));
+  }
+  return GW_OK;
+}
+
+extern "C" gw_status gw_hf(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  const int nk = c->nk, nao = c->nao, naux = c->naux;
+  CK(density_gamma(c->G_tau, c->lb, c->gamma, c->ntau, (int64_t)nk * c->n2, c->st));
+  CK(hartree_t(c->V, c->gamma, c->tQ, nk, naux, nao, c->st));
+  CK(hartree_j(c->V, c->tQ, c->Sinf_new, nk, naux, nao, c->spin / nk, c->st));   // Eq. HF_J
+  count(3);
+  return exchange(c);
+}
+
+// ------------------------------------------------------------------ A2/A3: polarization
+
+extern "C" gw_status gw_polarization(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
+  const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
+  const bool f32 = c->cfg.contract_prec == GW_FP32;
+  const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = tv;
+  const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
+  const void* Gp = c->G_tau;
+  const size_t es = f32 ? 8 : 16;
+  if (f32) { CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st)); count(1); Gp = c->G32; }
+  for (int q = 0; q < nk; ++q) {
+    double2* Pq = c->P0_tau + (size_t)q * ntau * na2;
+    for (int k = 0; k < nk; ++k) {
+      const int kq = c->kplus[(size_t)q * nk + k];
+      const char* Vkq = (const char*)Vp + ((size_t)k * nk + kq) * slab * es;
+      // Y[t][(Q,d)][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b]
+      GettDesc d1 = base_desc((int64_t)naux * nao, nao, nao, ntau);
+      d1.am = I1(nao); d1.ak = I1(1); d1.az = I1(0);
+      d1.bk = I1(nao); d1.bn = I1(1); d1.bz = I1(gstep);
+      d1.cm = I1(nao); d1.cn = I1(1); d1.cz = I1(slab);
+      CK(run_gett(d1, Vkq, tv, (const char*)Gp + (size_t)kq * n2 * es, tv, c->chA, tv, acc, c));
+      // Z[t][Q][c][b] = sum_d G^k_cd(-t) Y[t][Q][d][b],  G(-t_j) = -G(t_{ntau-1-j})
+      GettDesc d2 = base_desc(nao, (int64_t)naux * nao, nao, ntau);
+      d2.am = I1(nao); d2.ak = I1(1); d2.az = I1(-gstep);
+      d2.bk = I1(nao); d2.bn = I2(nao, n2, 1); d2.bz = I1(slab);
+      d2.cm = I1(nao); d2.cn = I2(nao, n2, 1); d2.cz = I1(slab);
+      d2.alpha = make_double2(-1, 0);
+      const char* Gm = (const char*)Gp + ((size_t)(ntau - 1) * gstep + (size_t)k * n2) * es;
+      CK(run_gett(d2, Gm, tv, c->chA, tv, c->chB, tv, acc, c));
+      // P[t][Q][Q'] += (s/Nk) sum_{(c,b)} Z[t][Q][(c,b)] V^{k+q,k}_{bc}(Q'),
+      // with V^{k+q,k}_{bc}(Q') = conj V^{k,k+q}_{cb}(Q') (pairing checked at init)
+      GettDesc d3 = base_desc((int64_t)ntau * naux, naux, n2, 1);
+      d3.am = I1(n2); d3.ak = I1(1);
+      d3.bk = I1(1); d3.bn = I1(n2); d3.conjB = true;
+      d3.cm = I1(naux); d3.cn = I1(1);
+      d3.alpha = make_double2(c->spin / nk, 0);
+      d3.beta = make_double2(k == 0 ? 0.0 : 1.0, 0);
+      CK(run_gett(d3, c->chB, tv, Vkq, tv, Pq, Ty::C128, acc, c));
+    }
+  }
+  CK(herm_batched(c->P0_tau, naux, (int64_t)nk * ntau, na2, c->st));
+  count(1);
+  // P~0(i Omega_m) = sum_j TFb[m][j] P~0(tau_j)   (Eq. P0t_to_P0w)
+  CK(transform(c, c->TFb, c->P0_tau, c->P_iw, c->nw, na2, nk, (int64_t)ntau * na2, (int64_t)c->nw * na2));
+  c->have_P0 = true;
+  c->have_P = false;
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ A4/A5: screened solve
+
+extern "C" gw_status gw_screened(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  if (!c->have_P0) return fail(c, GW_ERR_STATE, "no polarization yet");
+  const int nk = c->nk, naux = c->naux, ntau = c->ntau;
+  const int64_t na2 = c->na2;
+  CK(cudaMemsetAsync(c->info, 0, 4, c->st));
+  CK(screened_inplace(c->P_iw, naux, (int64_t)nk * c->nw, (double2*)c->ws, c->ws_bytes, c->info, c->st));
+  {
+    int64_t nbk = (naux + 63) / 64;
+    count((int)(2 + nbk * 6));
+  }
+  // P~(tau_j) = sum_m TBb[j][m] P~(i Omega_m)   (Eq. Piw_to_Pt), symmetrised
+  CK(transform(c, c->TBb, c->P_iw, c->P_tau, ntau, na2, nk, (int64_t)c->nw * na2, (int64_t)ntau * na2));
+  CK(herm_batched(c->P_tau, naux, (int64_t)nk * ntau, na2, c->st));
+  count(1);
+  int h = 0;
+  CK(cudaMemcpyAsync(c->h_scr, c->info, 4, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  memcpy(&h, c->h_scr, 4);
+  c->have_P0 = false;   // P~0(i Omega) was overwritten
+  if (h) return fail(c, GW_ERR_SINGULAR, "zero pivot in the screened solve");
+  c->have_P = true;
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ A6: self-energy
+
+static gw_status sigma_dynamic(gw_ctx* c) {
+  const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
+  const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
+  const bool f32 = c->cfg.contract_prec == GW_FP32;
+  const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = tv;
+  const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
+  const void* Gp = c->G_tau;
+  const void* Pp = c->P_tau;
+  const size_t es = f32 ? 8 : 16;
+  if (f32) {
+    CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st));
+    CK(to_c64(c->P_tau, c->P32, (int64_t)nk * ntau * na2, c->st));
+    count(2);
+    Gp = c->G32; Pp = c->P32;
+  }
+  for (int q = 0; q < nk; ++q) {
+    const char* Pq = (const char*)Pp + (size_t)q * ntau * na2 * es;
+    for (int k = 0; k < nk; ++k) {
+      const int kmq = c->kminus[(size_t)q * nk + k];
+      // X[t][Q'][(i,a)] = sum_Q P~^q[t][Q][Q'] V^{k,k-q}[Q][(i,a)]
+      GettDesc d1 = base_desc(naux, n2, naux, ntau);
+      d1.am = I1(1); d1.ak = I1(naux); d1.az = I1(na2);
+      d1.bk = I1(n2); d1.bn = I1(1); d1.bz = I1(0);
+      d1.cm = I1(n2); d1.cn = I1(1); d1.cz = I1(slab);
+      const char* Vkk = (const char*)Vp + ((size_t)k * nk + kmq) * slab * es;
+      CK(run_gett(d1, Pq, tv, Vkk, tv, c->chA, tv, acc, c));
+      // Y[t][i][Q'][b] = sum_a X[t][Q'][i][a] G^{k-q}[t][a][b]
+      GettDesc d2 = base_desc((int64_t)naux * nao, nao, nao, ntau);
+      d2.am = I1(nao); d2.ak = I1(1); d2.az = I1(slab);
+      d2.bk = I1(nao); d2.bn = I1(1); d2.bz = I1(gstep);
+      d2.cm = I2(nao, nao, (int64_t)naux * nao); d2.cn = I1(1); d2.cz = I1(slab);
+      CK(run_gett(d2, c->chA, tv, (const char*)Gp + (size_t)kmq * n2 * es, tv, c->chB, tv, acc, c));
+      // Sigma~[t][k][i][j] += -(1/Nk) sum_{(Q',b)} Y[t][i][(Q',b)] V^{k-q,k}[Q'][b][j]
+      GettDesc d3 = base_desc(nao, nao, (int64_t)naux * nao, ntau);
+      d3.am = I1((int64_t)naux * nao); d3.ak = I1(1); d3.az = I1(slab);
+      d3.bk = I1(nao); d3.bn = I1(1); d3.bz = I1(0);
+      d3.cm = I1(nao); d3.cn = I1(1); d3.cz = I1(gstep);
+      d3.alpha = make_double2(-1.0 / nk, 0);
+      d3.beta = make_double2(q == 0 ? 0.0 : 1.0, 0);
+      d3.ksplit = 8;
+      const char* Vk2 = (const char*)Vp + ((size_t)kmq * nk + k) * slab * es;
+      CK(run_gett(d3, c->chB, tv, Vk2, tv, c->Stau + (size_t)k * n2, Ty::C128, acc, c));
+    }
+  }
+  CK(herm_batched(c->Stau, nao, (int64_t)ntau * nk, n2, c->st));
+  count(1);
+  // Sigma~(i w_n) = sum_j TFf[n][j] Sigma~(tau_j)
+  CK(transform(c, c->TFf, c->Stau, c->Siw_new, c->nw, gstep, 1, 0, 0));
+  return GW_OK;
+}
+
+extern "C" gw_status gw_selfenergy(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  if (!c->have_P) return fail(c, GW_ERR_STATE, "no screened interaction yet");
+  gw_status s = gw_hf(c);
+  if (s != GW_OK) return s;
+  s = sigma_dynamic(c);
+  if (s != GW_OK) return s;
+  const int64_t ksz = (int64_t)c->nk * c->n2, gsz = (int64_t)c->ntau * ksz;
+  CK(cudaMemsetAsync(c->dscr + 8, 0, 8, c->st));
+  CK(maxabs_diff(c->Siw_new, c->Siw, gsz, c->dscr + 8, c->st));
+  count(1);
+  const double a = c->have_sigma ? c->cfg.damping : 1.0;
+  CK(axpby(c->Sinf, c->Sinf_new, a, 1.0 - a, ksz, c->st));
+  CK(axpby(c->Siw, c->Siw_new, a, 1.0 - a, gsz, c->st));
+  count(2);
+  c->have_sigma = true;
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ A7: Dyson + mu
+
+static DysonArgs dyson_args(gw_ctx* c) {
+  DysonArgs a{};
+  a.nao = c->nao; a.nk = c->nk; a.nw = c->nw;
+  a.H0 = c->H0; a.S = c->S; a.Sinf = c->Sinf; a.Siw = c->Siw;
+  a.wn = c->wn; a.r = c->r; a.spin = c->spin;
+  return a;
+}
+
+extern "C" gw_status gw_dyson(gw_ctx* c, double* mu_out) {
+  if (!c) return GW_ERR_ARG;
+  DysonArgs a = dyson_args(c);
+  const int64_t nsys = (int64_t)c->nw * c->nk;
+  const double scale = -c->spin / c->nk;
+  MuState* h = c->h_mus;
+  memset(h, 0, sizeof(MuState));
+  const double center = c->have_mu ? c->mu : 0.0;
+  h->lo = center - 1.0; h->hi = center + 1.0; h->x = h->lo;
+  h->target = c->cfg.n_elec; h->tol = c->cfg.mu_tol; h->width = 1e-13; h->maxit = c->cfg.mu_maxit;
+  CK(cudaMemcpyAsync(c->mus, h, sizeof(MuState), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->info, 0, 4, c->st));
+  const int chunk = 8;
+  for (int it = 0; it < c->cfg.mu_maxit + chunk; it += chunk) {
+    for (int j = 0; j < chunk; ++j) {
+      CK(dyson_eval(a, &c->mus->x, nullptr, c->partial, &c->mus->done, c->info, c->st));
+      CK(mu_step(c->mus, c->partial, nsys, scale, c->st));
+      count(2);
+    }
+    CK(cudaMemcpyAsync(h, c->mus, sizeof(MuState), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (h->done) break;
+  }
+  c->mu_steps = h->iter;
+  if (!h->done || h->status != 0) return fail(c, GW_ERR_NOT_CONVERGED, "chemical-potential search hit its cap");
+  c->mu = h->x; c->have_mu = true; c->n_at_mu = h->Nx;
+  // G(i w) at the final mu, then G(tau) = TBf G(i w), symmetrised
+  CK(dyson_eval(a, &c->mus->x, c->G_iw, nullptr, nullptr, c->info, c->st));
+  count(1);
+  const int64_t gstep = (int64_t)c->nk * c->n2;
+  CK(transform(c, c->TBf, c->G_iw, c->G_tau, c->ntau, gstep, 1, 0, 0));
+  CK(herm_batched(c->G_tau, c->nao, (int64_t)c->ntau * c->nk, c->n2, c->st));
+  count(1);
+  int bad = 0;
+  CK(cudaMemcpyAsync(c->h_scr, c->info, 4, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  memcpy(&bad, c->h_scr, 4);
+  if (bad) return fail(c, GW_ERR_SINGULAR, "zero pivot in the Dyson inversion");
+  c->have_G = true;
+  if (mu_out) *mu_out = c->mu;
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ iteration
+
+extern "C" gw_status gw_iterate(gw_ctx* c, int32_t n_iter, gw_iter_stats* stats) {
+  if (!c || n_iter < 0) return GW_ERR_ARG;
+  gw_status s;
+  if (!c->have_G) { if ((s = gw_dyson(c, nullptr)) != GW_OK) return s; }
+  const int64_t gsz = (int64_t)c->ntau * c->nk * c->n2;
+  for (int it = 0; it < n_iter; ++it) {
+    CK(cudaEventRecord(c->ev[0], c->st));
+    CK(cudaMemcpyAsync(c->G_prev, c->G_tau, gsz * 16, cudaMemcpyDeviceToDevice, c->st));
+    if ((s = gw_polarization(c)) != GW_OK) return s;
+    CK(cudaEventRecord(c->ev[1], c->st));
+    if ((s = gw_screened(c)) != GW_OK) return s;
+    CK(cudaEventRecord(c->ev[2], c->st));
+    if ((s = gw_selfenergy(c)) != GW_OK) return s;
+    CK(cudaEventRecord(c->ev[3], c->st));
+    if ((s = gw_dyson(c, nullptr)) != GW_OK) return s;
+    CK(cudaEventRecord(c->ev[4], c->st));
+    CK(cudaMemsetAsync(c->dscr + 9, 0, 8, c->st));
+    CK(maxabs_diff(c->G_tau, c->G_prev, gsz, c->dscr + 9, c->st));
+    count(1);
+    CK(cudaMemcpyAsync(c->h_scr, c->dscr, 16 * 8, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      stats->mu = c->mu; stats->n_elec = c->n_at_mu; stats->mu_steps = c->mu_steps;
+      stats->max_dSigma = c->h_scr[8]; stats->max_dG = c->h_scr[9];
+      cudaEventElapsedTime(&stats->ms_total, c->ev[0], c->ev[4]);
+      cudaEventElapsedTime(&stats->ms_polarization, c->ev[0], c->ev[1]);
+      cudaEventElapsedTime(&stats->ms_screened, c->ev[1], c->ev[2]);
+      cudaEventElapsedTime(&stats->ms_selfenergy, c->ev[2], c->ev[3]);
+      cudaEventElapsedTime(&stats->ms_dyson, c->ev[3], c->ev[4]);
+    }
+  }
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ profiling
+
+extern "C" gw_status gw_profile(gw_ctx* c, int enable) {
+  if (!c) return GW_ERR_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  c->prof = enable != 0;
+  c->pused = 0; c->pflops = 0.0; c->plaunch = 0;
+  return GW_OK;
+}
+
+extern "C" gw_status gw_profile_read(gw_ctx* c, double* out3) {
+  if (!c || !out3) return GW_ERR_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < c->pused; i += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->pev[i], c->pev[i + 1]));
+    ms += t;
+  }
+  out3[0] = ms; out3[1] = c->pflops; out3[2] = (double)c->plaunch;
+  c->pused = 0; c->pflops = 0.0; c->plaunch = 0;
+  return GW_OK;
+}

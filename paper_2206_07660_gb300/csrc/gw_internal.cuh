@@ -1,0 +1,95 @@
+// Internal declarations shared by the library's translation units.
+// Complex numbers are interleaved (re, im) pairs: double2 / float2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+#include "../../include/gwgb.h"
+
+namespace gwk {
+
+// ------------------------------------------------------------------ complex helpers
+template <typename T> struct cplx;
+template <> struct cplx<double> { using t = double2; };
+template <> struct cplx<float>  { using t = float2; };
+
+__host__ __device__ inline double2 mk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ inline float2  mkf(float r, float i) { return make_float2(r, i); }
+
+// ------------------------------------------------------------------ generic strided contraction
+// C(m,n) = alpha * sum_k opA(A(m,k)) * opB(B(k,n)) + beta * C(m,n), batched.
+// Each of m, n, k (and the batch index z) is split into an outer and an inner
+// part, idx = outer * inner_extent + inner, and the address of an element is
+// outer * stride1 + inner * stride0.  This lets one kernel read every tensor
+// slice of the method (transposed blocks, (Q,i) row pairs, ...) in place.
+struct Idx2 {
+  int64_t inner;   // inner extent (>= 1)
+  int64_t s1, s0;  // strides of outer and inner part, in complex elements
+};
+struct GettDesc {
+  int64_t M, N, K, Z;       // Z = batch count
+  Idx2 am, ak, az;          // A(m, k) in batch z
+  Idx2 bk, bn, bz;          // B(k, n)
+  Idx2 cm, cn, cz;          // C(m, n)
+  bool conjA, conjB;
+  double2 alpha, beta;      // beta == 0 -> C is not read
+  int ksplit;               // > 1: deterministic split-K through a workspace
+};
+
+// element type tags for the contraction kernels
+enum class Ty : int { C64 = 0, C128 = 1 };
+
+// Launch a contraction.  ta/tb/tc: storage types of A, B, C.  acc: accumulate
+// in double (C128) or float (C64).  ws: workspace for split-K (may be null
+// when ksplit == 1); returns cudaError_t.
+cudaError_t gett(const GettDesc& d, const void* A, Ty ta, const void* B, Ty tb, void* C, Ty tc,
+                 Ty acc, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t gett_ws_bytes(const GettDesc& d, Ty acc);
+
+inline Idx2 I1(int64_t s0) { return Idx2{INT64_MAX / 4, 0, s0}; }          // plain index
+inline Idx2 I2(int64_t inner, int64_t s1, int64_t s0) { return Idx2{inner, s1, s0}; }
+
+// ------------------------------------------------------------------ other kernels
+cudaError_t herm_batched(double2* X, int64_t n, int64_t count, int64_t stride, cudaStream_t st);
+size_t grid_ws_bytes(int ntau, const int* fn_host, const int* bm_host, int* ld_out);
+cudaError_t grid_build_ws(int ntau, double beta, const int* d_fn, const int* d_bm, int ld, void* ws,
+                          double* tau, double2* TFf, double2* TFb, double* lb, double* l0, cudaStream_t st);
+cudaError_t density_weights(int ntau, const double* lb, const double2* TBf, double2* r, cudaStream_t st);
+cudaError_t fermi_freqs(int ntau, double beta, const int* fn, double* wn, cudaStream_t st);
+cudaError_t invert_small_gj(double2* A, int n, int* d_info, cudaStream_t st);
+cudaError_t screened_inplace(double2* P, int64_t n, int64_t count, double2* work, size_t work_bytes,
+                             int* d_info, cudaStream_t st);
+size_t screened_work_bytes(int64_t n, int64_t count);
+
+struct DysonArgs {
+  int nao, nk, nw;
+  const double2* H0; const double2* S; const double2* Sinf; const double2* Siw; // Siw [nw][nk][nao2]
+  const double* wn;      // fermionic frequencies [nw]
+  const double2* r;      // density weights [nw] (complex)
+  double spin;
+};
+cudaError_t dyson_eval(const DysonArgs& a, const double* mu_ptr, double2* G_out, double* partial,
+                       const int* done_flag, int* d_info, cudaStream_t st);
+struct MuState {
+  double lo, hi, Nlo, Nhi, x, Nx, target, tol, width;
+  int phase, iter, maxit, done, status;
+};
+cudaError_t mu_step(MuState* s, const double* partial, int64_t count, double scale, cudaStream_t st);
+size_t dyson_smem(int nao, int nt);
+
+cudaError_t density_gamma(const double2* G_tau, const double* lb, double2* gamma, int ntau, int64_t nelem,
+                          cudaStream_t st);
+cudaError_t hartree_t(const double2* V, const double2* gamma, double2* t, int nk, int naux, int nao,
+                      cudaStream_t st);
+cudaError_t hartree_j(const double2* V, const double2* t, double2* J, int nk, int naux, int nao, double fac,
+                      cudaStream_t st);
+cudaError_t axpby(double2* y, const double2* x, double a, double b, int64_t n, cudaStream_t st);
+cudaError_t identity_minus(double2* X, int64_t n, int64_t count, double sign, cudaStream_t st);
+cudaError_t check_v_pairing(const double2* V, int nk, int naux, int nao, double* d_maxdev, cudaStream_t st);
+cudaError_t check_herm(const double2* X, int64_t n, int64_t count, double* d_maxdev, cudaStream_t st);
+cudaError_t maxabs_diff(const double2* a, const double2* b, int64_t n, double* d_out, cudaStream_t st);
+cudaError_t to_c64(const double2* x, float2* y, int64_t n, cudaStream_t st);
+
+}  // namespace gwk

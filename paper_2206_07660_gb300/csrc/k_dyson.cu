@@ -1,0 +1,141 @@
+// Dyson equation on the sampled Matsubara points and the chemical-potential
+// search (Eq. Dyson; Sec. "scGW workflow": mu adjusted to charge neutrality).
+//
+// One thread block per (n, k): A = (i w_n + mu) S - H0 - Sigma_inf - Sigma~(i w_n)
+// is built in shared memory and inverted in place (Gauss-Jordan, partial
+// pivoting).  For the electron count the block returns Re[r_n tr(A^{-1} S)];
+// a single-block kernel reduces those in a fixed order (deterministic) and
+// advances a bracketing/bisection state machine held in device memory, so the
+// whole search runs without host round trips except a periodic "done" read.
+#include "gw_internal.cuh"
+#include "gj.cuh"
+
+namespace gwk {
+
+__global__ void __launch_bounds__(256) dyson_kernel(DysonArgs a, const double* mu_ptr, double2* G_out,
+                                                    double* partial, const int* done_flag, int* info) {
+  if (done_flag && *(volatile const int*)done_flag) return;
+  extern __shared__ unsigned char smem[];
+  const int n = a.nao, lda = n;
+  double2* A = (double2*)smem;
+  double2* f = A + n * lda;
+  int* perm = (int*)(f + n);
+  double* rv = (double*)(perm + n + (n & 1));
+  int* ri = (int*)(rv + blockDim.x);
+  const double mu = *mu_ptr;
+  const int64_t n2 = (int64_t)n * n;
+  const int64_t nsys = (int64_t)a.nw * a.nk;
+  for (int64_t sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
+    const int w = (int)(sys / a.nk), k = (int)(sys - (int64_t)w * a.nk);
+    const double wn = a.wn[w];
+    const double2* S = a.S + k * n2;
+    const double2* H = a.H0 + k * n2;
+    const double2* Si = a.Sinf + k * n2;
+    const double2* Sw = a.Siw + sys * n2;
+    for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+      double2 s = S[e], h = H[e], x = Si[e], y = Sw[e];
+      // (i wn + mu) s
+      double re = mu * s.x - wn * s.y, im = mu * s.y + wn * s.x;
+      A[e] = make_double2(re - h.x - x.x - y.x, im - h.y - x.y - y.y);
+    }
+    __syncthreads();
+    int bad = gj_invert_smem(A, n, lda, f, perm, rv, ri);
+    if (bad && threadIdx.x == 0) atomicOr(info, 1);
+    if (G_out) {
+      double2* Gd = G_out + sys * n2;
+      for (int e = threadIdx.x; e < n2; e += blockDim.x) Gd[e] = A[e];
+    }
+    if (partial) {
+      // tr(A^{-1} S) = sum_ij Ainv_ij S_ji
+      double tr = 0, ti = 0;
+      for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+        int i = e / n, j = e - i * n;
+        double2 g = A[e], s = S[(int64_t)j * n + i];
+        tr += g.x * s.x - g.y * s.y;
+        ti += g.x * s.y + g.y * s.x;
+      }
+      rv[threadIdx.x] = tr;
+      __syncthreads();
+      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) rv[threadIdx.x] += rv[threadIdx.x + s];
+        __syncthreads();
+      }
+      double trr = rv[0];
+      __syncthreads();
+      rv[threadIdx.x] = ti;
+      __syncthreads();
+      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) rv[threadIdx.x] += rv[threadIdx.x + s];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        double2 r = a.r[w];
+        partial[sys] = r.x * trr - r.y * rv[0];   // Re(r_n tr)
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t dyson_smem(int nao, int nt) {
+  return (size_t)nao * nao * sizeof(double2) + (size_t)nao * sizeof(double2) + (size_t)(nao + 1) * sizeof(int) + 8 +
+         (size_t)nt * (sizeof(double) + sizeof(int));
+}
+
+cudaError_t dyson_eval(const DysonArgs& a, const double* mu_ptr, double2* G_out, double* partial,
+                       const int* done_flag, int* info, cudaStream_t st) {
+  const int nt = 256;
+  size_t sm = dyson_smem(a.nao, nt);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(dyson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  int64_t nsys = (int64_t)a.nw * a.nk;
+  int blocks = (int)(nsys < 152 * 8 ? nsys : 152 * 8);
+  dyson_kernel<<<blocks, nt, sm, st>>>(a, mu_ptr, G_out, partial, done_flag, info);
+  return cudaGetLastError();
+}
+
+// One step of the bracketing bisection.  state->x is the point evaluated by
+// the preceding dyson_kernel; `scale` turns the summed partials into N(x).
+__global__ void __launch_bounds__(1024) mu_step_kernel(MuState* s, const double* partial, int64_t count,
+                                                       double scale) {
+  if (*(volatile int*)&s->done) return;
+  __shared__ double red[1024];
+  double acc = 0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) acc += partial[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int t = blockDim.x / 2; t > 0; t >>= 1) {
+    if (threadIdx.x < t) red[threadIdx.x] += red[threadIdx.x + t];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double N = scale * red[0];
+  s->iter += 1;
+  if (s->phase == 0) {            // N at lo: must be <= target
+    s->Nlo = N;
+    if (N > s->target) { double w = s->hi - s->lo; s->lo -= 2.0 * w; s->x = s->lo; }
+    else { s->phase = 1; s->x = s->hi; }
+  } else if (s->phase == 1) {     // N at hi: must be >= target
+    s->Nhi = N;
+    if (N < s->target) { double w = s->hi - s->lo; s->hi += 2.0 * w; s->x = s->hi; }
+    else { s->phase = 2; s->x = 0.5 * (s->lo + s->hi); }
+  } else {                        // bisection
+    s->Nx = N;
+    if (fabs(N - s->target) <= s->tol && (s->hi - s->lo) <= s->width) {
+      s->done = 1; s->status = 0;
+    } else {
+      if (N < s->target) s->lo = s->x; else s->hi = s->x;
+      s->x = 0.5 * (s->lo + s->hi);
+    }
+  }
+  if (!s->done && s->iter >= s->maxit) { s->done = 1; s->status = 1; }
+}
+
+cudaError_t mu_step(MuState* s, const double* partial, int64_t count, double scale, cudaStream_t st) {
+  mu_step_kernel<<<1, 1024, 0, st>>>(s, partial, count, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace gwk

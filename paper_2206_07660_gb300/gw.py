@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libgwgb.so (argument marshalling only).
+
+Every step of the method runs in the library's CUDA kernels; this module
+converts Python/NumPy/torch arguments into the C ABI of include/gwgb.h and
+back.  Device memory for the library comes from PyTorch's caching allocator
+and work is enqueued on PyTorch's current CUDA stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgwgb.so")
+
+GW_OK, GW_ERR_ARG, GW_ERR_CUDA, GW_ERR_OOM, GW_ERR_NOT_CONVERGED, GW_ERR_SINGULAR, GW_ERR_TIMEOUT, \
+    GW_ERR_STATE, GW_ERR_INTERNAL = range(9)
+PRECISIONS = {"fp64": 0, "fp32": 1, "split_bf16": 2, "split_tf32": 3}
+GW_INPUT_DEVICE, GW_BORROW_V, GW_SKIP_CHECKS = 1, 2, 4
+
+QUANTITIES = {
+    "G_tau": 0, "G_iw": 1, "Sigma_inf": 2, "Sigma_tau": 3, "Sigma_iw": 4, "P0_tau": 5, "P0_iw": 6,
+    "P_iw": 7, "P_tau": 8, "gamma": 9, "mu": 10, "TFf": 11, "TBf": 12, "TFb": 13, "TBb": 14,
+    "lb": 15, "tau": 16, "n_elec": 17, "Sigma_inf_new": 18,
+}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class GwConfig(ctypes.Structure):
+    _fields_ = [
+        ("nao", ctypes.c_int32), ("naux", ctypes.c_int32), ("kmesh", ctypes.c_int32 * 3),
+        ("ntau", ctypes.c_int32), ("beta", ctypes.c_double), ("n_elec", ctypes.c_double),
+        ("mu_tol", ctypes.c_double), ("mu_maxit", ctypes.c_int32), ("damping", ctypes.c_double),
+        ("contract_prec", ctypes.c_int32), ("spin_factor", ctypes.c_int32),
+        ("fermi_n", ctypes.POINTER(ctypes.c_int32)), ("bose_m", ctypes.POINTER(ctypes.c_int32)),
+        ("stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+        ("alloc_user", ctypes.c_void_p), ("flags", ctypes.c_uint64),
+    ]
+
+
+class GwIterStats(ctypes.Structure):
+    _fields_ = [
+        ("mu", ctypes.c_double), ("n_elec", ctypes.c_double), ("mu_steps", ctypes.c_int32),
+        ("max_dG", ctypes.c_double), ("max_dSigma", ctypes.c_double), ("ms_total", ctypes.c_float),
+        ("ms_polarization", ctypes.c_float), ("ms_screened", ctypes.c_float),
+        ("ms_selfenergy", ctypes.c_float), ("ms_dyson", ctypes.c_float), ("ms_hf", ctypes.c_float),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libgwgb.so; raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libgwgb.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_2206_07660_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    lib.gw_init.argtypes = [ctypes.POINTER(GwConfig), P, P, P, ctypes.POINTER(P)]
+    lib.gw_destroy.argtypes = [P]
+    lib.gw_set.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int]
+    lib.gw_get.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int]
+    for name in ("gw_hf", "gw_polarization", "gw_screened", "gw_selfenergy", "gw_reset_sigma"):
+        getattr(lib, name).argtypes = [P]
+    lib.gw_dyson.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.gw_iterate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(GwIterStats)]
+    lib.gw_last_error.argtypes = [P]
+    lib.gw_last_error.restype = ctypes.c_char_p
+    lib.gw_profile.argtypes = [P, ctypes.c_int]
+    lib.gw_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.gw_kernel_launches.argtypes = [P]
+    lib.gw_kernel_launches.restype = ctypes.c_int64
+    for name in ("gw_init", "gw_destroy", "gw_set", "gw_get", "gw_hf", "gw_polarization", "gw_screened",
+                 "gw_selfenergy", "gw_dyson", "gw_iterate", "gw_reset_sigma", "gw_profile", "gw_profile_read"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class GWError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("gw status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _ptr(x):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data, False
+    assert x.is_contiguous()
+    return x.data_ptr(), x.is_cuda
+
+
+class GW:
+    """One self-consistent GW problem resident on the GPU.
+
+    H0, S: [nk, nao, nao] complex128; V: [nk, nk, naux, nao, nao] complex128
+    (numpy arrays, or CUDA torch tensors with device_inputs=True).
+    fermi_n, bose_m: sampled Matsubara integers (length ntau).
+    """
+
+    def __init__(self, H0, S, V, kmesh, ntau, beta, fermi_n, bose_m, n_elec=None, damping=0.5,
+                 mu_tol=1e-9, mu_maxit=400, precision="fp64", spin=2, borrow_V=False,
+                 skip_checks=False, torch_alloc=True):
+        import torch
+        self.lib = load()
+        self.torch = torch
+        nk, nao = H0.shape[0], H0.shape[1]
+        naux = V.shape[2]
+        self.nk, self.nao, self.naux, self.ntau = int(nk), int(nao), int(naux), int(ntau)
+        self._fn = np.ascontiguousarray(fermi_n, dtype=np.int32)
+        self._bm = np.ascontiguousarray(bose_m, dtype=np.int32)
+        cfg = GwConfig()
+        cfg.nao, cfg.naux, cfg.ntau = self.nao, self.naux, self.ntau
+        for i in range(3):
+            cfg.kmesh[i] = int(kmesh[i])
+        cfg.beta = float(beta)
+        cfg.n_elec = float(nao if n_elec is None else n_elec)
+        cfg.mu_tol, cfg.mu_maxit, cfg.damping = float(mu_tol), int(mu_maxit), float(damping)
+        cfg.contract_prec = PRECISIONS[precision]
+        cfg.spin_factor = int(spin)
+        cfg.fermi_n = self._fn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        cfg.bose_m = self._bm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        self.stream = torch.cuda.current_stream()
+        cfg.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self.device = torch.cuda.current_device()
+        if torch_alloc:
+            dev, strm = self.device, self.stream
+
+            def _alloc(user, nbytes):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm)
+                except Exception:
+                    return None
+
+            def _free(user, p):
+                torch.cuda.caching_allocator_delete(int(p))
+            self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
+            cfg.dev_alloc, cfg.dev_free = self._alloc_cb, self._free_cb
+        flags = 0
+        hp, hdev = _ptr(H0)
+        sp, _ = _ptr(S)
+        vp, vdev = _ptr(V)
+        if hdev:
+            flags |= GW_INPUT_DEVICE
+        if borrow_V:
+            flags |= GW_BORROW_V
+            self._V_ref = V
+        if skip_checks:
+            flags |= GW_SKIP_CHECKS
+        cfg.flags = flags
+        self._cfg = cfg
+        ctx = ctypes.c_void_p()
+        st = self.lib.gw_init(ctypes.byref(cfg), hp, sp, vp, ctypes.byref(ctx))
+        if st != GW_OK:
+            raise GWError(st, self.lib.gw_last_error(None).decode())
+        self.ctx = ctx
+
+    # -- plumbing
+    def _check(self, st):
+        if st != GW_OK:
+            raise GWError(st, self.lib.gw_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.gw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape_of(self, name):
+        nk, nao, naux, nt = self.nk, self.nao, self.naux, self.ntau
+        return {
+            "G_tau": (nt, nk, nao, nao), "G_iw": (nt, nk, nao, nao), "Sigma_inf": (nk, nao, nao),
+            "Sigma_inf_new": (nk, nao, nao), "Sigma_tau": (nt, nk, nao, nao), "Sigma_iw": (nt, nk, nao, nao),
+            "P0_tau": (nk, nt, naux, naux), "P0_iw": (nk, nt, naux, naux), "P_iw": (nk, nt, naux, naux),
+            "P_tau": (nk, nt, naux, naux), "gamma": (nk, nao, nao), "TFf": (nt, nt), "TBf": (nt, nt),
+            "TFb": (nt, nt), "TBb": (nt, nt),
+        }[name]
+
+    def get(self, name, out=None):
+        q = QUANTITIES[name]
+        if name in ("mu", "n_elec"):
+            v = ctypes.c_double()
+            self._check(self.lib.gw_get(self.ctx, q, ctypes.byref(v), 8, 0))
+            return v.value
+        if name in ("lb", "tau"):
+            arr = np.empty(self.ntau, dtype=np.float64)
+        else:
+            arr = np.empty(self.shape_of(name), dtype=np.complex128) if out is None else out
+        p, dev = _ptr(arr)
+        self._check(self.lib.gw_get(self.ctx, q, p, arr.nbytes if isinstance(arr, np.ndarray)
+                                    else arr.numel() * arr.element_size(), int(dev)))
+        return arr
+
+    def set(self, name, value):
+        q = QUANTITIES[name]
+        if name == "mu":
+            v = ctypes.c_double(float(value))
+            self._check(self.lib.gw_set(self.ctx, q, ctypes.byref(v), 8, 0))
+            return
+        if isinstance(value, np.ndarray):
+            value = np.ascontiguousarray(value, dtype=np.complex128)
+            nbytes = value.nbytes
+        else:
+            nbytes = value.numel() * value.element_size()
+        p, dev = _ptr(value)
+        self._check(self.lib.gw_set(self.ctx, q, p, nbytes, int(dev)))
+
+    # -- stages (Eqs. HF_J/HF_K, tilde_P0_tau, tilde_P_omega, tilde_sigma2, Dyson)
+    def hf(self):
+        self._check(self.lib.gw_hf(self.ctx))
+
+    def polarization(self):
+        self._check(self.lib.gw_polarization(self.ctx))
+
+    def screened(self):
+        self._check(self.lib.gw_screened(self.ctx))
+
+    def selfenergy(self):
+        self._check(self.lib.gw_selfenergy(self.ctx))
+
+    def dyson(self):
+        mu = ctypes.c_double()
+        self._check(self.lib.gw_dyson(self.ctx, ctypes.byref(mu)))
+        return mu.value
+
+    def reset_sigma(self):
+        self._check(self.lib.gw_reset_sigma(self.ctx))
+
+    def iterate(self, n=1):
+        s = GwIterStats()
+        self._check(self.lib.gw_iterate(self.ctx, int(n), ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in GwIterStats._fields_}
+
+    def profile(self, enable=True):
+        self._check(self.lib.gw_profile(self.ctx, int(bool(enable))))
+
+    def profile_read(self):
+        """(ms, flops, launches) of the contraction kernel since the last read."""
+        out = (ctypes.c_double * 3)()
+        self._check(self.lib.gw_profile_read(self.ctx, out))
+        return float(out[0]), float(out[1]), int(out[2])
+
+    def kernel_launches(self):
+        return int(self.lib.gw_kernel_launches(self.ctx))

@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, stage by
+stage and for full iterations, on seeded inputs whose sizes span several
+64-wide tiles and ragged tails.
+
+Tolerances (fp64 path): the two sides evaluate the same discrete definition
+with different summation orders, so they agree to roundoff amplified by the
+conditioning of each step: ~1e-13 relative for the contractions, cond(TF) x
+1e-15 for the transforms, and 1e-10 Ha absolute for Sigma and G after a full
+iteration (the target accuracy for the fp64 path).
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import gpu, hermitian_noise, oracle_state, rel, system
+from oracle import gw as ogw
+from oracle.grids import Grid
+from synth import make_config_system, matsubara_indices
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("ntau,beta", [(8, 20.0), (32, 100.0), (92, 1000.0), (100, 1000.0)])
+def test_transform_matrices(ntau, beta):
+    sysd = system(2, 3, (1, 1, 1), ntau, beta, 1)
+    g = gpu(sysd)
+    fn, bm = matsubara_indices(ntau)
+    o = Grid(beta, ntau, fn, bm)
+    assert rel(g.get("TFf"), o.TFf) < 1e-13
+    assert rel(g.get("TFb"), o.TFb) < 1e-13
+    assert rel(g.get("TBf"), o.TBf) < 1e-15 * np.linalg.cond(o.TFf) * 20
+    assert rel(g.get("TBb"), o.TBb) < 1e-15 * np.linalg.cond(o.TFb) * 20
+    assert np.abs(g.get("lb") - o.lb).max() < 1e-12 * np.abs(o.lb).max()
+    assert np.abs(g.get("tau") - o.tau).max() < 1e-12 * beta
+
+
+@pytest.mark.parametrize("nao,naux,kmesh,ntau,beta", [(3, 5, (1, 1, 1), 8, 10.0), (8, 32, (2, 2, 2), 32, 100.0),
+                                                      (13, 20, (3, 1, 1), 24, 200.0)])
+def test_dyson_noninteracting(nao, naux, kmesh, ntau, beta):
+    sysd = system(nao, naux, kmesh, ntau, beta, 7)
+    g = gpu(sysd)
+    mu = g.dyson()
+    st = oracle_state(sysd)
+    st.dyson()
+    assert abs(g.get("n_elec") - nao) <= 1e-9
+    assert abs(mu - st.mu) < 1e-8
+    assert np.abs(g.get("G_tau") - st.G_tau).max() < 1e-10
+    # G(i w) ~ 1/w near the lowest frequency, so it carries the bisection's
+    # last-digit freedom in mu amplified by |G|^2: compare it relatively
+    assert rel(g.get("G_iw"), st.G_iw) < 1e-11
+
+
+def _perturbed_green(sysd, seed):
+    st = oracle_state(sysd)
+    st.dyson()
+    G = st.G_tau + hermitian_noise(st.G_tau.shape, 0.02, seed)
+    return st, G
+
+
+@pytest.mark.parametrize("nao,naux,kmesh,ntau", [(5, 70, (3, 1, 1), 12), (8, 32, (2, 2, 2), 32),
+                                                 (17, 9, (1, 2, 1), 10), (1, 1, (1, 1, 1), 8)])
+def test_polarization(nao, naux, kmesh, ntau):
+    sysd = system(nao, naux, kmesh, ntau, 60.0, 11)
+    st, G = _perturbed_green(sysd, 3)
+    g = gpu(sysd)
+    g.set("G_tau", G)
+    g.polarization()
+    P0 = ogw.polarization_tau(st.V, G, st.km)
+    P0iw = ogw.to_matsubara(st.grid.TFb, P0, 1)
+    assert rel(g.get("P0_tau"), P0) < 1e-13
+    assert rel(g.get("P0_iw"), P0iw) < 1e-12
+
+
+@pytest.mark.parametrize("naux,nq,ntau", [(130, 2, 6), (64, 3, 5), (7, 1, 9)])
+def test_screened(naux, nq, ntau):
+    # seeded P~0(i Omega) with a negative-definite Hermitian part (as the
+    # polarization has), so that I - P~0 is well conditioned
+    sysd = system(2, naux, (nq, 1, 1), ntau, 30.0, 5)
+    rng = np.random.default_rng(9)
+    A = (rng.standard_normal((nq, ntau, naux, naux)) + 1j * rng.standard_normal((nq, ntau, naux, naux))) / np.sqrt(naux)
+    P0 = -0.5 * (A @ np.conj(np.swapaxes(A, -1, -2))) + 0.3 * (A - np.conj(np.swapaxes(A, -1, -2)))
+    g = gpu(sysd)
+    g.set("P0_iw", P0)
+    g.screened()
+    P = ogw.screened(P0)
+    o = Grid(30.0, ntau, *matsubara_indices(ntau))
+    Pt = ogw.herm(ogw.to_matsubara(o.TBb, P, 1))
+    assert rel(g.get("P_iw"), P) < 1e-12
+    assert rel(g.get("P_tau"), Pt) < 1e-12
+
+
+@pytest.mark.parametrize("nao,naux,kmesh,ntau", [(5, 70, (3, 1, 1), 12), (8, 32, (2, 2, 2), 32),
+                                                 (17, 9, (1, 2, 1), 10)])
+def test_selfenergy(nao, naux, kmesh, ntau):
+    sysd = system(nao, naux, kmesh, ntau, 60.0, 13)
+    st, G = _perturbed_green(sysd, 4)
+    nk = st.km.nk
+    P = hermitian_noise((nk, ntau, naux, naux), 0.1, 8)
+    g = gpu(sysd)
+    g.set("G_tau", G)
+    g.set("P_tau", P)
+    g.selfenergy()
+    S = ogw.selfenergy_tau(st.V, G, P, st.km)
+    Siw = ogw.to_matsubara(st.grid.TFf, S, 0)
+    gam = ogw.density_matrix(st.grid, G)
+    Sinf = ogw.hartree(st.V, gam) + ogw.exchange(st.V, gam)
+    assert rel(g.get("Sigma_tau"), S) < 1e-13
+    assert rel(g.get("Sigma_iw"), Siw) < 1e-12
+    assert rel(g.get("Sigma_inf_new"), Sinf) < 1e-13
+    assert rel(g.get("gamma"), gam) < 1e-13
+
+
+@pytest.mark.parametrize("trs", [False, True])
+def test_full_iterations_c1(trs):
+    sysd = make_config_system("C1", trs=trs)
+    g = gpu(sysd, damping=0.5)
+    st = oracle_state(sysd, damping=0.5)
+    for it in range(2):
+        stats = g.iterate(1)
+        st.iterate()
+        assert abs(stats["n_elec"] - st.n_elec) <= 1e-9
+        assert np.abs(g.get("Sigma_inf") - st.Sigma_inf).max() < 1e-10
+        assert np.abs(g.get("Sigma_iw") - st.Sigma_iw).max() < 1e-10
+        assert np.abs(g.get("Sigma_tau") - st.Sigma_tau).max() < 1e-10
+        assert np.abs(g.get("G_tau") - st.G_tau).max() < 1e-10
+        assert abs(g.get("mu") - st.mu) < 1e-8
+
+
+def test_single_orbital_closed_form():
+    # nao = naux = nk = 1 with the exact G at the nodes: P~0 is the constant
+    # -s v^2 f (1-f) and Sigma~ has a closed form (see oracle.closed_forms)
+    from oracle import closed_forms as cf
+    ntau, beta, eps, v, mu = 16, 10.0, 0.3, 0.7, 0.05
+    fn, bm = matsubara_indices(ntau)
+    sysd = dict(H0=np.full((1, 1, 1), eps, dtype=np.complex128), S=np.ones((1, 1, 1), dtype=np.complex128),
+                V=np.full((1, 1, 1, 1, 1), v, dtype=np.complex128), kmesh=(1, 1, 1), ntau=ntau, beta=beta,
+                fermi_n=fn, bose_m=bm, n_elec=1.0)
+    o = Grid(beta, ntau, fn, bm)
+    cl = cf.single_orbital(beta, eps, v, mu, o.tau)
+    g = gpu(sysd)
+    g.set("G_tau", cl["G"].reshape(ntau, 1, 1, 1).astype(np.complex128))
+    g.polarization()
+    assert np.abs(g.get("P0_tau") - cl["c"]).max() < 1e-14
+    g.screened()
+    tol = 50 * np.linalg.cond(o.TFb) * np.finfo(float).eps * (1 + abs(beta * cl["c"]))
+    assert np.abs(g.get("P_tau") - cl["P_tau"]).max() < tol * abs(cl["P_tau"])
+    g.selfenergy()
+    assert np.abs(g.get("Sigma_tau")[:, 0, 0, 0] - cl["Sigma_tau"]).max() < tol * np.abs(cl["Sigma_tau"]).max()
+    assert abs(g.get("Sigma_inf_new")[0, 0, 0] - (cl["J"] + cl["K"])) < 1e-13
+
+
+def test_fp32_contractions_c1():
+    sysd = make_config_system("C1")
+    g = gpu(sysd, precision="fp32")
+    st = oracle_state(sysd)
+    g.iterate(1)
+    st.iterate()
+    err = np.abs(g.get("Sigma_tau") - st.Sigma_tau).max()
+    assert err < 1e-5, err
+    assert np.abs(g.get("Sigma_inf") - st.Sigma_inf).max() < 1e-5
+
+
+def test_rejects_bad_inputs():
+    from paper_2206_07660_gb300 import GWError
+    sysd = system(3, 4, (2, 1, 1), 8, 10.0, 2)
+    V = sysd["V"].copy()
+    V[0, 1] += 0.1
+    bad = dict(sysd, V=V)
+    with pytest.raises(GWError):
+        gpu(bad)
+    H = sysd["H0"].copy()
+    H[0, 0, 1] += 0.1
+    with pytest.raises(GWError):
+        gpu(dict(sysd, H0=H))
+    g = gpu(sysd)
+    with pytest.raises(GWError):
+        g.polarization()     # no G yet

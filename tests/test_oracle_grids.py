@@ -126,3 +126,14 @@ def test_matsubara_index_sets():
         assert 0 in bm
         if ntau % 2 == 0:
             assert set(fn) == set(-fn - 1)        # symmetric fermionic set
+
+
+def test_jacobi_anger_matches_quadrature_low_frequencies():
+    # two independent evaluations of the same integrals agree where the
+    # quadrature is accurate (moderate a)
+    from oracle.grids import fourier_matrix_ja, fermionic_a
+    ntau = 24
+    n = np.arange(-12, 12)
+    A = fourier_matrix_ja(30.0, ntau, fermionic_a(n))
+    B = fourier_matrix(30.0, ntau, (2 * n + 1) * np.pi / 30.0)
+    assert np.abs(A - B).max() < 1e-13 * np.abs(B).max()
