@@ -63,7 +63,9 @@ typedef enum {
   GW_FP32 = 1,        /* complex64 products, fp32 accumulation per k-slab,
                          fp64 accumulation across slabs                         */
   GW_SPLIT_BF16 = 2,  /* reserved */
-  GW_SPLIT_TF32 = 3   /* reserved */
+  GW_SPLIT_TF32 = 3   /* the dominant GEMM of each contraction on tcgen05 tensor cores with
+                         x = hi + lo TF32 splits (hi*hi + hi*lo + lo*hi, fp32 accumulation,
+                         fp64 accumulation across (q, k) slabs); other steps as GW_FP32 */
 } gw_precision;
 
 enum {
@@ -190,16 +192,18 @@ const char* gw_last_error(const gw_ctx* ctx);
 /* Number of kernels the library has launched so far (all contexts). */
 int64_t gw_kernel_launches(const gw_ctx* ctx);
 
-/* Per-launch timing of the contraction kernel that carries Eqs. tilde_P0_tau,
- * tilde_sigma2 and HF_K: with enable != 0 every launch is bracketed by CUDA
- * events on cfg->stream (a few microseconds of overhead per launch).
+/* Per-launch timing of the two contraction kernels that carry Eqs.
+ * tilde_P0_tau, tilde_sigma2 and HF_K (the SIMT strided contraction and the
+ * tensor-core split-TF32 GEMM): with enable != 0 every launch is bracketed by
+ * CUDA events on cfg->stream (a few microseconds of overhead per launch).
  * Synchronises and resets the accumulators. */
 gw_status gw_profile(gw_ctx* ctx, int enable);
 
-/* Reads and resets the accumulators of gw_profile: out3[0] = summed device
- * milliseconds of the timed launches, out3[1] = their complex-MAC flops
- * (8 M N K per launch), out3[2] = number of launches.  Synchronises. */
-gw_status gw_profile_read(gw_ctx* ctx, double* out3);
+/* Reads and resets the accumulators of gw_profile.  out6[0..2]: SIMT
+ * contraction kernel -- summed device milliseconds, useful flops (8 per
+ * complex multiply-add), launches; out6[3..5]: the same for the tensor-core
+ * kernel.  Synchronises. */
+gw_status gw_profile_read(gw_ctx* ctx, double* out6);
 
 #ifdef __cplusplus
 }

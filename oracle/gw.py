@@ -78,34 +78,40 @@ def exchange(V, gamma):
     """Eq. HF_K: K^k_ij = -(1/Nk) sum_{k',Q,ab} V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q)."""
     nk = gamma.shape[0]
     K = np.zeros_like(gamma)
+    naux, nao = V.shape[2], V.shape[3]
     for k in range(nk):
         for kp in range(nk):
-            A = V[k, kp] @ gamma[kp]                          # [Q, i, b]
-            K[k] -= np.einsum("Qib,Qbj->ij", A, V[kp, k])
+            A = np.matmul(V[k, kp], gamma[kp])                # [Q, i, b]
+            At = A.transpose(1, 0, 2).reshape(nao, naux * nao)  # [i, (Q, b)]
+            K[k] -= At @ V[kp, k].reshape(naux * nao, nao)
     return K / nk
 
 
 # ---------------------------------------------------------------- A2: P~0(tau)
 
-def polarization_tau(V, G_tau, km, s=2.0, symmetrize=True):
+def polarization_tau(V, G_tau, km, s=2.0, symmetrize=True, qs=None):
     """Eq. tilde_P0_tau (sign/orientation as in the module docstring).
 
     P~0^q_{QQ'}(tau) = (s/Nk) sum_k sum_abcd V^{k,k+q}_da(Q) G^{k+q}_ab(tau)
                                           V^{k+q,k}_bc(Q') G^k_cd(-tau)
-    Returns [nq, ntau, naux, naux].
+    Returns [nq, ntau, naux, naux] (only the q in `qs` are filled when given).
     """
-    ntau, nk = G_tau.shape[0], G_tau.shape[1]
+    ntau, nk, nao = G_tau.shape[0], G_tau.shape[1], G_tau.shape[2]
     naux = V.shape[2]
     Gm = g_minus_tau(G_tau)
     P = np.zeros((nk, ntau, naux, naux), dtype=np.complex128)
-    for q in range(nk):
+    for q in (range(nk) if qs is None else qs):
         for k in range(nk):
             kq = km.add(k, q)
-            # Z[t, Q, c, b] = sum_{d,a} G^k_cd(-t) V^{k,kq}_da(Q) G^{kq}_ab(t)
-            VG = np.einsum("Qda,tab->tQdb", V[k, kq], G_tau[:, kq])
-            Z = np.einsum("tcd,tQdb->tQcb", Gm[:, k], VG)
-            # P[t, Q, Q'] += sum_{c,b} Z[t, Q, c, b] V^{kq,k}_bc(Q')
-            P[q] += np.einsum("tQcb,Rbc->tQR", Z, V[kq, k], optimize=True)
+            # VG[t, Q, d, b] = sum_a V^{k,k+q}_da(Q) G^{k+q}_ab(t)
+            VG = np.matmul(V[k, kq].reshape(naux * nao, nao)[None], G_tau[:, kq])
+            VG = VG.reshape(ntau, naux, nao, nao)
+            # Z[t, Q, c, b] = sum_d G^k_cd(-t) VG[t, Q, d, b]
+            VGt = VG.transpose(0, 2, 1, 3).reshape(ntau, nao, naux * nao)
+            Z = np.matmul(Gm[:, k], VGt).reshape(ntau, nao, naux, nao).transpose(0, 2, 1, 3)
+            # P[t, Q, R] += sum_{c,b} Z[t, Q, c, b] V^{k+q,k}_bc(R)
+            B = V[kq, k].transpose(2, 1, 0).reshape(nao * nao, naux)
+            P[q] += (np.ascontiguousarray(Z).reshape(ntau * naux, nao * nao) @ B).reshape(ntau, naux, naux)
     P *= s / nk
     return herm(P) if symmetrize else P
 
@@ -128,21 +134,27 @@ def screened(P0_iw):
 
 # ---------------------------------------------------------------- A6: Sigma~(tau)
 
-def selfenergy_tau(V, G_tau, P_tau, km, symmetrize=True):
+def selfenergy_tau(V, G_tau, P_tau, km, symmetrize=True, qs=None):
     """Eq. tilde_sigma2:
     Sigma~^k_ij(tau) = -(1/Nk) sum_q sum_ab sum_QQ' G^{k-q}_ab(tau) V^{k,k-q}_ia(Q)
                                                    P~^q_QQ'(tau) V^{k-q,k}_bj(Q')
-    P_tau: [nq, ntau, naux, naux].  Returns [ntau, nk, nao, nao].
+    P_tau: [nq, ntau, naux, naux].  Returns [ntau, nk, nao, nao] (the sum runs
+    over the q in `qs` only when given).
     """
     ntau, nk, nao = G_tau.shape[0], G_tau.shape[1], G_tau.shape[2]
+    naux = V.shape[2]
     Sig = np.zeros((ntau, nk, nao, nao), dtype=np.complex128)
-    for q in range(nk):
+    for q in (range(nk) if qs is None else qs):
+        PT = np.ascontiguousarray(P_tau[q].transpose(0, 2, 1))           # [t, Q', Q]
         for k in range(nk):
             kmq = km.sub(k, q)
-            # X[t, Q', i, a] = sum_Q P[t, Q, Q'] V^{k,kmq}_ia(Q)
-            X = np.einsum("tQR,Qia->tRia", P_tau[q], V[k, kmq], optimize=True)
-            Y = np.einsum("tRia,tab->tRib", X, G_tau[:, kmq])
-            Sig[:, k] += np.einsum("tRib,Rbj->tij", Y, V[kmq, k], optimize=True)
+            # X[t, Q', i, a] = sum_Q P~^q_QQ'(t) V^{k,k-q}_ia(Q)
+            X = np.matmul(PT, V[k, kmq].reshape(naux, nao * nao)[None])
+            # Y[t, Q', i, b] = sum_a X[t, Q', i, a] G^{k-q}_ab(t)
+            Y = np.matmul(X.reshape(ntau, naux * nao, nao), G_tau[:, kmq]).reshape(ntau, naux, nao, nao)
+            # Sigma[t, i, j] += sum_{Q', b} Y[t, Q', i, b] V^{k-q,k}_bj(Q')
+            Yt = Y.transpose(0, 2, 1, 3).reshape(ntau, nao, naux * nao)
+            Sig[:, k] += np.matmul(Yt, V[kmq, k].reshape(naux * nao, nao)[None])
     Sig *= -1.0 / nk
     return herm(Sig) if symmetrize else Sig
 

@@ -39,6 +39,10 @@ struct gw_ctx {
   void *chA = nullptr, *chB = nullptr;
   size_t ch_bytes = 0;
   float2 *G32 = nullptr, *P32 = nullptr, *gam32 = nullptr;
+  // split-TF32 tensor-core operands (hi / lo planes, rows padded to 32 fp32)
+  float *Zhi = nullptr, *Zlo = nullptr, *Vhi = nullptr, *Vlo = nullptr;
+  float *Pchi = nullptr, *Pclo = nullptr, *VThi = nullptr, *VTlo = nullptr;
+  int64_t kpadP = 0, kpadS = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   double* partial = nullptr;
@@ -57,6 +61,10 @@ struct gw_ctx {
   size_t pused = 0;
   double pflops = 0.0;
   int64_t plaunch = 0;
+  std::vector<cudaEvent_t> uev;   // same for the tensor-core kernel
+  size_t uused = 0;
+  double uflops = 0.0;
+  int64_t ulaunch = 0;
 };
 
 static thread_local std::string g_init_err;
@@ -93,6 +101,8 @@ static void free_all(gw_ctx* c) {
   for (auto& e : c->ev) if (e) { cudaEventDestroy(e); e = nullptr; }
   for (auto& e : c->pev) cudaEventDestroy(e);
   c->pev.clear();
+  for (auto& e : c->uev) cudaEventDestroy(e);
+  c->uev.clear();
 }
 
 static inline void count(int n) { g_launches += n; }
@@ -113,6 +123,28 @@ static cudaError_t run_gett(const GettDesc& d, const void* A, Ty ta, const void*
   c->pused += 2;
   c->pflops += 8.0 * (double)d.M * (double)d.N * (double)d.K * (double)d.Z;
   c->plaunch += 1;
+  return r;
+}
+
+// tensor-core launch with optional event timing; flops = useful complex-MAC flops
+static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const UmmaOperand& B, int M, int N,
+                            int64_t Kpad, int batch, void* C, bool c_fp64, double alpha, bool accumulate, int64_t c_ld,
+                            int64_t c_zs) {
+  count(1);
+  if (c->prof) {
+    while (c->uev.size() < c->uused + 2) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      c->uev.push_back(e);
+    }
+    cudaEventRecord(c->uev[c->uused], c->st);
+  }
+  cudaError_t r = umma_gemm(A, B, M, N, Kpad, batch, C, c_fp64, alpha, accumulate, c_ld, c_zs, 3, c->info + 1, c->st);
+  if (c->prof) {
+    cudaEventRecord(c->uev[c->uused + 1], c->st);
+    c->uused += 2; c->uflops += flops; c->ulaunch += 1;
+  }
   return r;
 }
 
@@ -151,7 +183,7 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     return fail(nullptr, GW_ERR_ARG, "sizes must be positive");
   if (cfg->nao > 96) return fail(nullptr, GW_ERR_ARG, "nao > 96 is not supported by the Dyson kernel");
   if (!(cfg->beta > 0) || !cfg->fermi_n || !cfg->bose_m) return fail(nullptr, GW_ERR_ARG, "bad beta or index sets");
-  if (cfg->contract_prec != GW_FP64 && cfg->contract_prec != GW_FP32)
+  if (cfg->contract_prec != GW_FP64 && cfg->contract_prec != GW_FP32 && cfg->contract_prec != GW_SPLIT_TF32)
     return fail(nullptr, GW_ERR_ARG, "contract_prec not available");
   if ((cfg->flags & GW_BORROW_V) && !(cfg->flags & GW_INPUT_DEVICE))
     return fail(nullptr, GW_ERR_ARG, "GW_BORROW_V needs GW_INPUT_DEVICE");
@@ -191,7 +223,8 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   c->S = (double2*)need(A(nk * n2 * cb));
   if (cfg->flags & GW_BORROW_V) c->V = (double2*)V;
   else c->V = (double2*)need(A(vbytes));
-  if (cfg->contract_prec == GW_FP32) c->V32 = (float2*)need(A(vbytes / 2));
+  const bool lowp = cfg->contract_prec != GW_FP64;
+  if (lowp) c->V32 = (float2*)need(A(vbytes / 2));
   c->tau = (double*)need(A(ntau * 8)); c->lb = (double*)need(A(ntau * 8)); c->l0 = (double*)need(A(ntau * 8));
   c->wn = (double*)need(A(ntau * 8));
   c->TFf = (double2*)need(A((size_t)ntau * ntau * cb)); c->TBf = (double2*)need(A((size_t)ntau * ntau * cb));
@@ -207,11 +240,21 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   c->P0_tau = (double2*)need(A(psz)); c->P_iw = (double2*)need(A(psz)); c->P_tau = (double2*)need(A(psz));
   // chain intermediates: max(ntau * naux * n2, nk * naux * n2) complex of the contraction type
   size_t chn = (size_t)(ntau > nk ? ntau : nk) * naux * n2;
-  c->ch_bytes = chn * (cfg->contract_prec == GW_FP32 ? 8 : 16);
+  c->ch_bytes = chn * (lowp ? 8 : 16);
   c->chA = need(A(c->ch_bytes)); c->chB = need(A(c->ch_bytes));
-  if (cfg->contract_prec == GW_FP32) {
+  if (lowp) {
     c->G32 = (float2*)need(A(gsz / 2)); c->P32 = (float2*)need(A(psz / 2));
     c->gam32 = (float2*)need(A(nk * n2 * 8));
+  }
+  if (cfg->contract_prec == GW_SPLIT_TF32) {
+    c->kpadP = (2 * n2 + 31) / 32 * 32;
+    c->kpadS = (2 * (int64_t)naux + 31) / 32 * 32;
+    const size_t zb = (size_t)ntau * naux * c->kpadP * 4, vb = (size_t)2 * naux * c->kpadP * 4;
+    const size_t pb = (size_t)ntau * naux * c->kpadS * 4, tb = (size_t)2 * n2 * c->kpadS * 4;
+    c->Zhi = (float*)need(A(zb)); c->Zlo = (float*)need(A(zb));
+    c->Vhi = (float*)need(A(vb)); c->Vlo = (float*)need(A(vb));
+    c->Pchi = (float*)need(A(pb)); c->Pclo = (float*)need(A(pb));
+    c->VThi = (float*)need(A(tb)); c->VTlo = (float*)need(A(tb));
   }
   // workspace: split-K partials and the screened-solve panels
   size_t ws = screened_work_bytes(naux, (int64_t)nk * ntau);
@@ -262,7 +305,7 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   chk(density_weights(ntau, c->lb, c->TBf, c->r, st), "weights");
   chk(fermi_freqs(ntau, cfg->beta, c->d_fn, c->wn, st), "freqs");
   count(4);
-  if (cfg->contract_prec == GW_FP32) { chk(to_c64(c->V, c->V32, vbytes / cb, st), "V32"); count(1); }
+  if (lowp) { chk(to_c64(c->V, c->V32, vbytes / cb, st), "V32"); count(1); }
   // input checks
   chk(cudaMemsetAsync(c->dscr, 0, 64 * 8, st), "memset");
   if (!(cfg->flags & GW_SKIP_CHECKS)) {
@@ -374,7 +417,7 @@ static gw_status exchange(gw_ctx* c) {
   // K^k_ij = -(1/Nk) sum_{k',Q,a,b} V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q)    (Eq. HF_K)
   const int nk = c->nk, nao = c->nao, naux = c->naux;
   const int64_t n2 = c->n2, slab = (int64_t)naux * n2;
-  const bool f32 = c->cfg.contract_prec == GW_FP32;
+  const bool f32 = c->cfg.contract_prec != GW_FP64;
   const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = f32 ? Ty::C64 : Ty::C128;
   const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
   const void* gp = c->gamma;
@@ -421,12 +464,14 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
-  const bool f32 = c->cfg.contract_prec == GW_FP32;
+  const bool f32 = c->cfg.contract_prec != GW_FP64;
+  const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
   const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = tv;
   const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
   const void* Gp = c->G_tau;
   const size_t es = f32 ? 8 : 16;
   if (f32) { CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st)); count(1); Gp = c->G32; }
+  CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
   for (int q = 0; q < nk; ++q) {
     double2* Pq = c->P0_tau + (size_t)q * ntau * na2;
     for (int k = 0; k < nk; ++k) {
@@ -448,6 +493,19 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
       CK(run_gett(d2, Gm, tv, c->chA, tv, c->chB, tv, acc, c));
       // P[t][Q][Q'] += (s/Nk) sum_{(c,b)} Z[t][Q][(c,b)] V^{k+q,k}_{bc}(Q'),
       // with V^{k+q,k}_{bc}(Q') = conj V^{k,k+q}_{cb}(Q') (pairing checked at init)
+      if (tc) {
+        // tensor cores: split-TF32 real GEMM on the embedded operands
+        const int64_t kp = c->kpadP;
+        CK(split_rows(c->chB, false, (int64_t)ntau * naux, n2, n2, false, c->Zhi, c->Zlo, kp, c->st));
+        CK(embed_conj((const char*)c->V + ((size_t)k * nk + kq) * slab * 16, true, naux, n2, c->Vhi, c->Vlo, kp,
+                      c->st));
+        UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, kp, 0};
+        UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, kp, 0};
+        CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, kp, 1, Pq, true,
+                    c->spin / nk, k > 0, 2 * (int64_t)naux, 0));
+        count(2);
+        continue;
+      }
       GettDesc d3 = base_desc((int64_t)ntau * naux, naux, n2, 1);
       d3.am = I1(n2); d3.ak = I1(1);
       d3.bk = I1(1); d3.bn = I1(n2); d3.conjB = true;
@@ -456,6 +514,13 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
       d3.beta = make_double2(k == 0 ? 0.0 : 1.0, 0);
       CK(run_gett(d3, c->chB, tv, Vkq, tv, Pq, Ty::C128, acc, c));
     }
+  }
+  if (tc) {
+    int h = 0;
+    CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    memcpy(&h, c->h_scr, 4);
+    if (h) return fail(c, GW_ERR_TIMEOUT, "tensor-core contraction gave up waiting (code " + std::to_string(h) + ")");
   }
   CK(herm_batched(c->P0_tau, naux, (int64_t)nk * ntau, na2, c->st));
   count(1);
@@ -498,11 +563,13 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
 static gw_status sigma_dynamic(gw_ctx* c) {
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
-  const bool f32 = c->cfg.contract_prec == GW_FP32;
+  const bool f32 = c->cfg.contract_prec != GW_FP64;
+  const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
   const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = tv;
   const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
   const void* Gp = c->G_tau;
   const void* Pp = c->P_tau;
+  CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
   const size_t es = f32 ? 8 : 16;
   if (f32) {
     CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st));
@@ -512,8 +579,25 @@ static gw_status sigma_dynamic(gw_ctx* c) {
   }
   for (int q = 0; q < nk; ++q) {
     const char* Pq = (const char*)Pp + (size_t)q * ntau * na2 * es;
+    if (tc) {
+      // A operand of the tensor-core stage: conj P~^q(t) = P~^q(t)^T (Hermitian), split hi/lo
+      CK(split_rows(c->P_tau + (size_t)q * ntau * na2, true, (int64_t)ntau * naux, naux, naux, true, c->Pchi,
+                    c->Pclo, c->kpadS, c->st));
+      count(1);
+    }
     for (int k = 0; k < nk; ++k) {
       const int kmq = c->kminus[(size_t)q * nk + k];
+      if (tc) {
+        // X[t][Q'][(i,a)] = sum_Q conj(P~[t][Q'][Q]) V^{k,k-q}[Q][(i,a)] on tensor cores
+        const int64_t kp = c->kpadS;
+        CK(embed_t((const char*)c->V + ((size_t)k * nk + kmq) * slab * 16, true, naux, n2, c->VThi, c->VTlo, kp,
+                   c->st));
+        UmmaOperand oa{c->Pchi, c->Pclo, naux, ntau, kp, (int64_t)naux * kp};
+        UmmaOperand ob{c->VThi, c->VTlo, 2 * n2, 1, kp, 0};
+        CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, naux, (int)(2 * n2), kp, ntau, c->chA, false,
+                    1.0, false, 2 * n2, (int64_t)naux * 2 * n2));
+        count(1);
+      } else {
       // X[t][Q'][(i,a)] = sum_Q P~^q[t][Q][Q'] V^{k,k-q}[Q][(i,a)]
       GettDesc d1 = base_desc(naux, n2, naux, ntau);
       d1.am = I1(1); d1.ak = I1(naux); d1.az = I1(na2);
@@ -521,6 +605,7 @@ static gw_status sigma_dynamic(gw_ctx* c) {
       d1.cm = I1(n2); d1.cn = I1(1); d1.cz = I1(slab);
       const char* Vkk = (const char*)Vp + ((size_t)k * nk + kmq) * slab * es;
       CK(run_gett(d1, Pq, tv, Vkk, tv, c->chA, tv, acc, c));
+      }
       // Y[t][i][Q'][b] = sum_a X[t][Q'][i][a] G^{k-q}[t][a][b]
       GettDesc d2 = base_desc((int64_t)naux * nao, nao, nao, ntau);
       d2.am = I1(nao); d2.ak = I1(1); d2.az = I1(slab);
@@ -538,6 +623,13 @@ static gw_status sigma_dynamic(gw_ctx* c) {
       const char* Vk2 = (const char*)Vp + ((size_t)kmq * nk + k) * slab * es;
       CK(run_gett(d3, c->chB, tv, Vk2, tv, c->Stau + (size_t)k * n2, Ty::C128, acc, c));
     }
+  }
+  if (tc) {
+    int h = 0;
+    CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    memcpy(&h, c->h_scr, 4);
+    if (h) return fail(c, GW_ERR_TIMEOUT, "tensor-core contraction gave up waiting (code " + std::to_string(h) + ")");
   }
   CK(herm_batched(c->Stau, nao, (int64_t)ntau * nk, n2, c->st));
   count(1);
@@ -600,7 +692,14 @@ extern "C" gw_status gw_dyson(gw_ctx* c, double* mu_out) {
     if (h->done) break;
   }
   c->mu_steps = h->iter;
-  if (!h->done || h->status != 0) return fail(c, GW_ERR_NOT_CONVERGED, "chemical-potential search hit its cap");
+  if (!h->done || h->status != 0) {
+    char msg[320];
+    snprintf(msg, sizeof msg,
+             "chemical-potential search hit its cap: steps %d phase %d bracket [%.17g, %.17g] N(lo)=%.12g "
+             "N(hi)=%.12g last x=%.17g N(x)=%.12g target %.12g",
+             h->iter, h->phase, h->lo, h->hi, h->Nlo, h->Nhi, h->x, h->Nx, h->target);
+    return fail(c, GW_ERR_NOT_CONVERGED, msg);
+  }
   c->mu = h->x; c->have_mu = true; c->n_at_mu = h->Nx;
   // G(i w) at the final mu, then G(tau) = TBf G(i w), symmetrised
   CK(dyson_eval(a, &c->mus->x, c->G_iw, nullptr, nullptr, c->info, c->st));
@@ -663,19 +762,27 @@ extern "C" gw_status gw_profile(gw_ctx* c, int enable) {
   CK(cudaStreamSynchronize(c->st));
   c->prof = enable != 0;
   c->pused = 0; c->pflops = 0.0; c->plaunch = 0;
+  c->uused = 0; c->uflops = 0.0; c->ulaunch = 0;
   return GW_OK;
 }
 
-extern "C" gw_status gw_profile_read(gw_ctx* c, double* out3) {
-  if (!c || !out3) return GW_ERR_ARG;
+extern "C" gw_status gw_profile_read(gw_ctx* c, double* out6) {
+  if (!c || !out6) return GW_ERR_ARG;
   CK(cudaStreamSynchronize(c->st));
-  double ms = 0.0;
+  double ms = 0.0, ums = 0.0;
   for (size_t i = 0; i + 1 < c->pused; i += 2) {
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, c->pev[i], c->pev[i + 1]));
     ms += t;
   }
-  out3[0] = ms; out3[1] = c->pflops; out3[2] = (double)c->plaunch;
+  for (size_t i = 0; i + 1 < c->uused; i += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->uev[i], c->uev[i + 1]));
+    ums += t;
+  }
+  out6[0] = ms; out6[1] = c->pflops; out6[2] = (double)c->plaunch;
+  out6[3] = ums; out6[4] = c->uflops; out6[5] = (double)c->ulaunch;
   c->pused = 0; c->pflops = 0.0; c->plaunch = 0;
+  c->uused = 0; c->uflops = 0.0; c->ulaunch = 0;
   return GW_OK;
 }

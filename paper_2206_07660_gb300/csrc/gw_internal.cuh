@@ -92,4 +92,21 @@ cudaError_t check_herm(const double2* X, int64_t n, int64_t count, double* d_max
 cudaError_t maxabs_diff(const double2* a, const double2* b, int64_t n, double* d_out, cudaStream_t st);
 cudaError_t to_c64(const double2* x, float2* y, int64_t n, cudaStream_t st);
 
+// ------------------------------------------------------------------ tensor-core split-TF32 GEMM
+struct UmmaOperand {
+  const float* hi;
+  const float* lo;
+  int64_t rows, batch;   // rows per batch, batch count (1 = shared by all z)
+  int64_t ld, bs;        // row stride and batch stride in fp32 elements
+};
+cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
+                      bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
+                      cudaStream_t st);
+cudaError_t split_rows(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, float* hi,
+                       float* lo, int64_t Kpad, cudaStream_t st);
+cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, float* hi, float* lo, int64_t Kpad,
+                       cudaStream_t st);
+cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float* hi, float* lo, int64_t Kpad,
+                    cudaStream_t st);
+
 }  // namespace gwk

@@ -1,0 +1,437 @@
+// Tensor-core (tcgen05, sm_103a) real GEMM with split-TF32 operands for the two
+// dominant contractions of the method (Eq. tilde_P0_tau: P~0 += Z V^H, and
+// Eq. tilde_sigma2: X = P~^T V), after the complex-to-real embedding below.
+//
+//   D[z][m][n] (+)= alpha * sum_seg sum_k A_seg[z][m][k] * B_seg[z][n][k]
+//
+// Both operands are K-major fp32 arrays holding TF32 values, loaded by TMA
+// (3-D tensor maps {K, rows, batch}, 128-byte swizzle) into a 4-stage shared
+// memory ring; one elected thread issues tcgen05.mma (kind::tf32, M = 128,
+// N = BN) into a TMEM accumulator; four epilogue warps read it back with
+// tcgen05.ld and add it into an fp64 (or store into an fp32) output.
+// Split precision: x = hi + lo with hi = tf32(x), lo = tf32(x - hi); the
+// three segments are (A_hi, B_hi), (A_hi, B_lo), (A_lo, B_hi) (lo*lo dropped),
+// giving ~2^-22 relative accuracy per product with fp32 accumulation.
+//
+// Complex embedding: a complex matrix stored interleaved (re, im) is a real
+// matrix with twice the columns.  For C = A conj(B)^T the real operand B'' has
+// rows 2n = (Re b, Im b) and 2n+1 = (-Im b, Re b); for C = A B^T rows
+// 2n = (Re b, -Im b) and 2n+1 = (Im b, Re b).  The real product A' B''^T is
+// then C in interleaved form.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel records an error
+// code, skips the remaining work, releases its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include "gw_internal.cuh"
+
+namespace gwk {
+
+constexpr int UM_BM = 128;
+constexpr int UM_BK = 32;          // fp32 elements per 128-byte swizzle row
+constexpr int UM_STAGES = 4;
+constexpr int UM_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr uint32_t UM_SPIN_LIMIT = 1u << 26;
+
+struct UmmaArgs {
+  int M, N;            // real output rows / columns
+  int kblocks;         // K blocks of 32 per segment
+  int nseg;            // 1 (plain tf32) or 3 (split hi/lo)
+  int a_batched, b_batched;  // use z as the 3rd TMA coordinate (else 0)
+  void* C;
+  int c_fp64;          // 1: C is double and receives C += alpha*D (or = when !accumulate)
+  int accumulate;
+  double alpha;
+  int64_t c_ld;        // real elements between consecutive rows m
+  int64_t c_zs;        // real elements between batches
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// bounded wait; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t addr = smem_u32(bar);
+  for (uint32_t i = 0; i < UM_SPIN_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
+  uint64_t a = smem_u32(p);
+  return ((a & 0x3FFFFull) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(UM_THREADS, 1)
+    umma_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+                const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, UmmaArgs a) {
+  constexpr uint32_t A_BYTES = UM_BM * UM_BK * 4;
+  constexpr uint32_t B_BYTES = BN * UM_BK * 4;
+  constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + UM_STAGES * A_BYTES;
+  uint64_t* full = (uint64_t*)(sB + UM_STAGES * B_BYTES);
+  uint64_t* empty = full + UM_STAGES;
+  uint64_t* done = empty + UM_STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * UM_BM, z = blockIdx.z;
+  const int total = a.nseg * a.kblocks;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < UM_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
+      for (int it = 0; it < total; ++it) {
+        const int s = it % UM_STAGES;
+        const uint32_t ph = (uint32_t)(it / UM_STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); break; }
+        const int seg = it / a.kblocks, kb = it - seg * a.kblocks;
+        const CUtensorMap* ma = (seg == 2) ? &tA1 : &tA0;   // A_hi, A_hi, A_lo
+        const CUtensorMap* mb = (seg == 1) ? &tB1 : &tB0;   // B_hi, B_lo, B_hi
+        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+        tma_load_3d(sA + s * A_BYTES, ma, &full[s], kb * UM_BK, m0, za);
+        tma_load_3d(sB + s * B_BYTES, mb, &full[s], kb * UM_BK, n0, zb);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // instruction descriptor: D fp32, A/B tf32, both K-major, N = BN, M = 128
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)(UM_BM >> 4) << 24);
+      bool ok = true;
+      for (int it = 0; it < total; ++it) {
+        const int s = it % UM_STAGES;
+        const uint32_t ph = (uint32_t)(it / UM_STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph)) { atomicCAS(&s_fail, 0, 2); ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t ad = sw128_desc(sA + s * A_BYTES), bd = sw128_desc(sB + s * B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < UM_BK / 8; ++kk)   // K = 8 tf32 (32 bytes) per instruction
+          umma_tf32(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(&empty[s]);
+      }
+      if (ok) umma_commit(done);
+      else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(done)) : "memory");
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (its accessible lane quarter)
+    const int quarter = warp & 3;
+    const bool ok = mbar_wait(done, 0u);
+    if (!ok) atomicCAS(&s_fail, 0, 3);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + quarter * 32 + lane;
+    const bool live = ok && (s_fail == 0);
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!live || row >= a.M) continue;
+      const int64_t base = (int64_t)z * a.c_zs + (int64_t)row * a.c_ld;
+      if (a.c_fp64) {
+        double* C = (double*)a.C + base;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < a.N) {
+            const double v = a.alpha * (double)__uint_as_float(r[j]);
+            C[n] = a.accumulate ? C[n] + v : v;
+          }
+        }
+      } else {
+        float* C = (float*)a.C + base;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < a.N) {
+            const float v = (float)a.alpha * __uint_as_float(r[j]);
+            C[n] = a.accumulate ? C[n] + v : v;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && s_fail && a.err) atomicCAS(a.err, 0, 100 + s_fail);
+}
+
+// ------------------------------------------------------------------ host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 3-D fp32 tensor map {kdim, rows, batch} with row stride ld and batch stride bs (elements)
+static bool make_map(CUtensorMap* m, const float* base, int64_t kdim, int64_t rows, int64_t batch, int64_t ld,
+                     int64_t bs, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if (((uintptr_t)base & 15) || (ld * 4) % 16 || (bs * 4) % 16) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)(batch > 0 ? batch : 1)};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * 4), (cuuint64_t)((batch > 1 ? bs : ld * rows) * 4)};
+  cuuint32_t box[3] = {(cuuint32_t)UM_BK, box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+static size_t umma_smem() {
+  return 1024 + (size_t)UM_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + (2 * UM_STAGES + 1) * 8 + 16;
+}
+
+template <int BN>
+static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch, cudaStream_t st) {
+  size_t sm = umma_smem<BN>();
+  cudaError_t e = cudaFuncSetAttribute(umma_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.N + BN - 1) / BN, (a.M + UM_BM - 1) / UM_BM, batch);
+  umma_kernel<BN><<<grid, UM_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a);
+  return cudaGetLastError();
+}
+
+cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
+                      bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
+                      cudaStream_t st) {
+  if (Kpad % UM_BK) return cudaErrorInvalidValue;
+  CUtensorMap maps[4];
+  const int bn = N >= 160 ? 160 : N > 128 ? 160 : N > 64 ? 128 : N > 32 ? 64 : 32;
+  if (!make_map(&maps[0], A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
+      !make_map(&maps[1], nseg > 1 ? A.lo : A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
+      !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn) ||
+      !make_map(&maps[3], nseg > 1 ? B.lo : B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn))
+    return cudaErrorInvalidValue;
+  UmmaArgs a{};
+  a.M = M; a.N = N; a.kblocks = (int)(Kpad / UM_BK); a.nseg = nseg;
+  a.a_batched = A.batch > 1; a.b_batched = B.batch > 1;
+  a.C = C; a.c_fp64 = c_fp64; a.accumulate = accumulate; a.alpha = alpha; a.c_ld = c_ld; a.c_zs = c_zs;
+  a.err = err;
+  switch (bn) {
+    case 160: return launch_bn<160>(maps, a, batch, st);
+    case 128: return launch_bn<128>(maps, a, batch, st);
+    case 64: return launch_bn<64>(maps, a, batch, st);
+    default: return launch_bn<32>(maps, a, batch, st);
+  }
+}
+
+// ------------------------------------------------------------------ operand preparation
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void split2(double x, float& hi, float& lo) {
+  hi = tf32_rna((float)x);
+  lo = tf32_rna((float)(x - (double)hi));
+}
+
+// Rows of a complex matrix (element (r, k) at src + r*ld + k, complex units) into
+// real hi/lo rows of length Kpad (zero padded): out[r][2k + s] = (re, +-im).
+template <typename T>
+__global__ void split_rows_kernel(const T* __restrict__ src, int64_t rows, int64_t K, int64_t ld, int conj,
+                                  float* hi, float* lo, int64_t Kpad) {
+  const int64_t tot = rows * Kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Kpad, c = e - r * Kpad;
+    double v = 0.0;
+    if (c < 2 * K) {
+      const T x = src[r * ld + (c >> 1)];
+      v = (c & 1) ? (conj ? -(double)x.y : (double)x.y) : (double)x.x;
+    }
+    float h, l;
+    split2(v, h, l);
+    hi[e] = h;
+    if (lo) lo[e] = l;
+  }
+}
+
+// Doubled operand of C = A conj(B)^T from B (rows n, complex K): rows 2n = (re, im),
+// rows 2n+1 = (-im, re).
+template <typename T>
+__global__ void embed_conj_kernel(const T* __restrict__ src, int64_t rows, int64_t K, float* hi, float* lo,
+                                  int64_t Kpad) {
+  const int64_t tot = 2 * rows * Kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r2 = e / Kpad, c = e - r2 * Kpad, n = r2 >> 1;
+    double v = 0.0;
+    if (c < 2 * K) {
+      const T x = src[n * K + (c >> 1)];
+      if ((r2 & 1) == 0) v = (c & 1) ? (double)x.y : (double)x.x;
+      else v = (c & 1) ? (double)x.x : -(double)x.y;
+    }
+    float h, l;
+    split2(v, h, l);
+    hi[e] = h;
+    if (lo) lo[e] = l;
+  }
+}
+
+// Doubled operand of C = A B^T where B[n][k] = src[k][n] (src: K rows of N complex):
+// rows 2n = (re, -im), rows 2n+1 = (im, re), transposed through shared memory.
+template <typename T>
+__global__ void embed_t_kernel(const T* __restrict__ src, int64_t K, int64_t N, float* hi, float* lo, int64_t Kpad) {
+  __shared__ double2 tile[32][33];
+  const int64_t k0 = blockIdx.y * 32, nb = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t k = k0 + r, n = nb + tx;
+    double2 v = make_double2(0, 0);
+    if (k < K && n < N) { T x = src[k * N + n]; v = make_double2((double)x.x, (double)x.y); }
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  // write rows 2n, 2n+1 for n in block, columns 2k, 2k+1 for k in block
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t n = nb + r;
+    if (n >= N) continue;
+    const int64_t k = k0 + tx;
+    const double2 v = tile[tx][r];
+    float h, l;
+    if (k < K) {
+      float* h0 = hi + (2 * n) * Kpad + 2 * k;
+      float* h1 = hi + (2 * n + 1) * Kpad + 2 * k;
+      split2(v.x, h, l); h0[0] = h; if (lo) lo[(2 * n) * Kpad + 2 * k] = l;
+      split2(-v.y, h, l); h0[1] = h; if (lo) lo[(2 * n) * Kpad + 2 * k + 1] = l;
+      split2(v.y, h, l); h1[0] = h; if (lo) lo[(2 * n + 1) * Kpad + 2 * k] = l;
+      split2(v.x, h, l); h1[1] = h; if (lo) lo[(2 * n + 1) * Kpad + 2 * k + 1] = l;
+    }
+  }
+  // zero padding columns [2K, Kpad) once, by the first column of blocks
+  if (blockIdx.y == 0) {
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t n = nb + r;
+      if (n >= N) continue;
+      for (int64_t c = 2 * K + tx; c < Kpad; c += 32) {
+        hi[(2 * n) * Kpad + c] = 0.f; hi[(2 * n + 1) * Kpad + c] = 0.f;
+        if (lo) { lo[(2 * n) * Kpad + c] = 0.f; lo[(2 * n + 1) * Kpad + c] = 0.f; }
+      }
+    }
+  }
+}
+
+static inline int nb_(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 152 * 16 ? b : 152 * 16); }
+
+cudaError_t split_rows(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, float* hi,
+                       float* lo, int64_t Kpad, cudaStream_t st) {
+  if (src_c128) split_rows_kernel<double2><<<nb_(rows * Kpad), 256, 0, st>>>((const double2*)src, rows, K, ld, conj, hi, lo, Kpad);
+  else split_rows_kernel<float2><<<nb_(rows * Kpad), 256, 0, st>>>((const float2*)src, rows, K, ld, conj, hi, lo, Kpad);
+  return cudaGetLastError();
+}
+cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, float* hi, float* lo, int64_t Kpad,
+                       cudaStream_t st) {
+  if (src_c128) embed_conj_kernel<double2><<<nb_(2 * rows * Kpad), 256, 0, st>>>((const double2*)src, rows, K, hi, lo, Kpad);
+  else embed_conj_kernel<float2><<<nb_(2 * rows * Kpad), 256, 0, st>>>((const float2*)src, rows, K, hi, lo, Kpad);
+  return cudaGetLastError();
+}
+cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float* hi, float* lo, int64_t Kpad,
+                    cudaStream_t st) {
+  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32));
+  if (src_c128) embed_t_kernel<double2><<<grid, 256, 0, st>>>((const double2*)src, K, N, hi, lo, Kpad);
+  else embed_t_kernel<float2><<<grid, 256, 0, st>>>((const float2*)src, K, N, hi, lo, Kpad);
+  return cudaGetLastError();
+}
+
+}  // namespace gwk
+
+// ------------------------------------------------------------------ test hooks
+// Internal entry points for unit tests of the tensor-core GEMM (not part of the
+// public header).  All pointers are device pointers; the scratch is allocated
+// here with cudaMalloc.  Returns 0 on success, else a CUDA error or kernel code.
+
+extern "C" int gwdbg_umma_cgemm(const double2* A, const double2* B, int M, int N, int K, int conjB, int nseg,
+                                double* C) {
+  using namespace gwk;
+  const int64_t Kpad = ((2 * (int64_t)K + UM_BK - 1) / UM_BK) * UM_BK;
+  float *ah, *al, *bh, *bl;
+  int* err;
+  size_t asz = (size_t)M * Kpad * 4, bsz = (size_t)2 * N * Kpad * 4;
+  if (cudaMalloc(&ah, asz) || cudaMalloc(&al, asz) || cudaMalloc(&bh, bsz) || cudaMalloc(&bl, bsz) ||
+      cudaMalloc(&err, 4))
+    return -1;
+  cudaMemset(err, 0, 4);
+  cudaError_t e = split_rows(A, true, M, K, K, false, ah, al, Kpad, 0);
+  if (!e) {
+    if (conjB) e = embed_conj(B, true, N, K, bh, bl, Kpad, 0);
+    else e = embed_t(B, true, K, N, bh, bl, Kpad, 0);   // B given as [K][N]: C = A B
+  }
+  UmmaOperand oa{ah, al, M, 1, Kpad, 0}, ob{bh, bl, 2 * (int64_t)N, 1, Kpad, 0};
+  if (!e) e = umma_gemm(oa, ob, M, 2 * N, Kpad, 1, C, true, 1.0, false, 2 * N, 0, nseg, err, 0);
+  int herr = 0;
+  if (!e) e = cudaDeviceSynchronize();
+  cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+  cudaFree(ah); cudaFree(al); cudaFree(bh); cudaFree(bl); cudaFree(err);
+  return e ? (int)e : herr;
+}

@@ -248,10 +248,11 @@ class GW:
         self._check(self.lib.gw_profile(self.ctx, int(bool(enable))))
 
     def profile_read(self):
-        """(ms, flops, launches) of the contraction kernel since the last read."""
-        out = (ctypes.c_double * 3)()
+        """{'simt': (ms, flops, launches), 'tensor': (ms, flops, launches)} since the last read."""
+        out = (ctypes.c_double * 6)()
         self._check(self.lib.gw_profile_read(self.ctx, out))
-        return float(out[0]), float(out[1]), int(out[2])
+        return {"simt": (float(out[0]), float(out[1]), int(out[2])),
+                "tensor": (float(out[3]), float(out[4]), int(out[5]))}
 
     def kernel_launches(self):
         return int(self.lib.gw_kernel_launches(self.ctx))

@@ -28,9 +28,9 @@ SEED_BASE = 2206076600
 
 # Workloads: sizes of the paper-scale synthetic systems.
 CONFIGS = {
-    "C1": dict(nao=8, naux=32, kmesh=(2, 2, 2), ntau=32, beta=100.0),
-    "C2": dict(nao=26, naux=200, kmesh=(3, 3, 3), ntau=92, beta=1000.0),
-    "C3": dict(nao=52, naux=400, kmesh=(4, 4, 4), ntau=100, beta=1000.0),
+    "C1": dict(nao=8, naux=32, kmesh=(2, 2, 2), ntau=32, beta=100.0, cV_scale=1.0),
+    "C2": dict(nao=26, naux=200, kmesh=(3, 3, 3), ntau=92, beta=1000.0, cV_scale=0.35),
+    "C3": dict(nao=52, naux=400, kmesh=(4, 4, 4), ntau=100, beta=1000.0, cV_scale=0.35),
 }
 CONFIG_INDEX = {"C1": 1, "C2": 2, "C3": 3, "C4": 4, "C5": 5}
 
@@ -192,8 +192,9 @@ def make_config_system(name, system=0, trs=False, materialize_V=True, **over):
     """System plus grid integers for a named workload (sizes overridable)."""
     cfg = dict(CONFIGS[name])
     cfg.update(over)
+    cV = cfg.get("cV_scale", 1.0) / np.sqrt(cfg["nao"])
     sysd = make_system(cfg["nao"], cfg["naux"], cfg["kmesh"], config_seed(name, system),
-                       trs=trs, materialize_V=materialize_V)
+                       trs=trs, materialize_V=materialize_V, cV=cV)
     fn, bm = matsubara_indices(cfg["ntau"])
     sysd.update(ntau=int(cfg["ntau"]), beta=float(cfg["beta"]), fermi_n=fn, bose_m=bm,
                 n_elec=float(cfg.get("n_elec", cfg["nao"])))
