@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-q", type=int, default=1, help="q-slices in the CPU sample")
     p.add_argument("--peaks", action="store_true")
+    p.add_argument("--kmesh", default=None, help="override the k-mesh, e.g. 2,2,2 (profiling cases)")
     return p.parse_args()
 
 
@@ -119,12 +120,13 @@ class Clocks:
 
 # ---------------------------------------------------------------- inputs
 
-def make_inputs(workload, seed_offset=0):
-    from synth import CONFIGS, config_seed, make_system, matsubara_indices
+def make_inputs(workload, seed_offset=0, kmesh=None):
+    from synth import CONFIGS, make_config_system
     cfg = dict(CONFIGS[workload])
-    sysd = make_system(cfg["nao"], cfg["naux"], cfg["kmesh"], config_seed(workload, seed_offset))
-    fn, bm = matsubara_indices(cfg["ntau"])
-    sysd.update(beta=cfg["beta"], ntau=cfg["ntau"], fermi_n=fn, bose_m=bm, n_elec=float(cfg["nao"]))
+    over = {}
+    if kmesh:
+        cfg["kmesh"] = over["kmesh"] = tuple(int(x) for x in kmesh.split(","))
+    sysd = make_config_system(workload, system=seed_offset, **over)
     return cfg, sysd
 
 
@@ -214,7 +216,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cfg, sysd = make_inputs(args.workload)
+    cfg, sysd = make_inputs(args.workload, kmesh=args.kmesh)
     vals = []
     info = None
     for i in range(args.warmup + args.steps):
@@ -262,7 +264,7 @@ def run_gw(args):
             dist.barrier()
 
     # replicas: each rank runs its own seeded system of the same workload
-    cfg, sysd = make_inputs(args.workload, seed_offset=rank)
+    cfg, sysd = make_inputs(args.workload, seed_offset=rank, kmesh=args.kmesh)
     fl = flops(cfg)
     g = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
            sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision=args.precision)
