@@ -205,6 +205,29 @@ gw_status gw_profile(gw_ctx* ctx, int enable);
  * kernel.  Synchronises. */
 gw_status gw_profile_read(gw_ctx* ctx, double* out6);
 
+/* Allocation-free screened solve: P = [I - P0]^{-1} P0 for `count` complex
+ * n x n matrices (interleaved (re, im) doubles, row-major, contiguous), the
+ * operation of gw_screened without a context.  The paper has no counterpart;
+ * it exists for callers that cannot allocate device memory when they need the
+ * solve (memory owned by an arena or pool they do not control, hosts that
+ * forbid cudaMalloc after start-up, code that must not hit an allocator's
+ * implicit synchronisation).  P0 and P are device pointers owned by the caller
+ * (P == P0 solves in place).  Scratch is one fixed array of 64 MiB inside the
+ * library (GW_NOALLOC_SCRATCH_BYTES), resident on every device that loads the
+ * library until the process exits; n is limited to orders whose per-matrix
+ * workspace fits it (GW_ERR_ARG otherwise; n = 20000 fits).  The first call on
+ * a device looks up the array's device address; make that first call before
+ * any stream capture.  All calls share the array, so calls that overlap on the
+ * GPU (different streams or threads) race and must be serialised by the
+ * caller.  Work runs on `stream` (cudaStream_t, NULL = legacy default) and the
+ * call synchronises it to read the pivot status: GW_ERR_SINGULAR on a zero
+ * pivot.  No cudaMalloc, cudaFree or allocating library routine is called. */
+#define GW_NOALLOC_SCRATCH_BYTES (64u << 20)
+gw_status gw_screened_solve_noalloc(const double* P0, double* P, int64_t n, int64_t count, void* stream);
+
+/* Message of the last failure of gw_screened_solve_noalloc. */
+const char* gw_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif
