@@ -120,14 +120,62 @@ class Clocks:
 
 # ---------------------------------------------------------------- inputs
 
+HOST_V_LIMIT = 8e9   # bytes; larger V tensors are drawn slab by slab straight into HBM
+
+
 def make_inputs(workload, seed_offset=0, kmesh=None):
     from synth import CONFIGS, make_config_system
     cfg = dict(CONFIGS[workload])
     over = {}
     if kmesh:
         cfg["kmesh"] = over["kmesh"] = tuple(int(x) for x in kmesh.split(","))
-    sysd = make_config_system(workload, system=seed_offset, **over)
+    nk = cfg["kmesh"][0] * cfg["kmesh"][1] * cfg["kmesh"][2]
+    vbytes = nk * nk * cfg["naux"] * cfg["nao"] ** 2 * 16
+    sysd = make_config_system(workload, system=seed_offset, materialize_V=vbytes <= HOST_V_LIMIT, **over)
     return cfg, sysd
+
+
+class LazyV:
+    """V^{kk'}(Q) slabs drawn on demand (for oracle samples of large workloads)."""
+
+    def __init__(self, sysd):
+        self.sysd = sysd
+        nk, naux, nao = sysd["nk"], sysd["naux"], sysd["nao"]
+        self.shape = (nk, nk, naux, nao, nao)
+        self.cache = {}
+
+    def __getitem__(self, idx):
+        import numpy as np
+        from synth import v_slab
+        k, k2 = idx
+        if isinstance(k, np.ndarray):
+            return np.stack([self[(int(a), int(b))] for a, b in zip(k, k2)])
+        key = (int(k), int(k2))
+        if key not in self.cache:
+            self.cache[key] = v_slab(self.sysd, *key)
+        return self.cache[key]
+
+
+def device_V(sysd):
+    """The full V tensor in HBM, drawn slab by slab on host threads."""
+    import concurrent.futures as cf
+    import torch
+    from synth import v_slab
+    nk, naux, nao = sysd["nk"], sysd["naux"], sysd["nao"]
+    V = torch.empty((nk, nk, naux, nao, nao), dtype=torch.complex128, device="cuda")
+    pairs = [(k, k2) for k in range(nk) for k2 in range(k, nk)]
+
+    def draw(p):
+        return p, torch.from_numpy(v_slab(sysd, *p)).pin_memory()
+
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        for (k, k2), h in ex.map(draw, pairs):
+            d = h.to("cuda", non_blocking=False)
+            V[k, k2] = d
+            if k2 != k:
+                V[k2, k] = d.transpose(-1, -2).conj()
+    torch.cuda.synchronize()
+    return V
 
 
 def traffic_from_profiles(workload, precision):
@@ -148,43 +196,54 @@ def traffic_from_profiles(workload, precision):
 
 # ---------------------------------------------------------------- CPU oracle sample
 
-def cpu_sample(cfg, sysd, nq_sample=1):
+def cpu_sample(cfg, sysd, nq_sample=1, k_sample=None):
     """Time the oracle on a bounded slice of one iteration and extrapolate.
 
-    The slice: A2 (P~0), A4 (screened solve, all nw) and A6 (Sigma~
-    contribution) for nq_sample of the nq q-points, from the non-interacting
-    G; the q-independent rest (HF, transforms of Sigma, mu search and Dyson)
-    is timed in full.  Seconds per iteration = nq/nq_sample x slice + rest.
+    The slice: A2 (P~0) and A6 (Sigma~) for nq_sample q-points (and, for large
+    workloads, k_sample of the k-points in each), A4 (screened solve and its
+    transforms, all nw) for those q-points, the exchange term for one k', and
+    the q-independent rest (Hartree, Sigma transform, mu search and Dyson) in
+    full.  Seconds per iteration = each part x (total units / sampled units).
     """
     import numpy as np
     from oracle import gw as ogw
-    st = ogw.State(sysd)
+    V = sysd["V"] if sysd.get("V") is not None else LazyV(sysd)
+    s2 = dict(sysd, V=V)
+    st = ogw.State(s2)
     st.dyson()
     G = st.G_tau
-    km, V, grid = st.km, st.V, st.grid
+    km, grid = st.km, st.grid
     nk = km.nk
-    ntau, naux = grid.ntau, V.shape[2]
-    t0 = time.perf_counter()
     qs = list(range(nq_sample))
-    P = ogw.polarization_tau(V, G, km, qs=qs)
+    ks = None if k_sample is None else list(range(k_sample))
+    nks = nk if ks is None else len(ks)
+    t0 = time.perf_counter()
+    P = ogw.polarization_tau(V, G, km, qs=qs, ks=ks)
+    t_p = time.perf_counter() - t0
+    t0 = time.perf_counter()
     Piw = ogw.to_matsubara(grid.TFb, P[qs], 1)
     Pt = np.zeros_like(P)
     Pt[qs] = ogw.herm(ogw.to_matsubara(grid.TBb, ogw.screened(Piw), 1))
-    Sig = ogw.selfenergy_tau(V, G, Pt, km, qs=qs)
-    t_slice = time.perf_counter() - t0
-    t1 = time.perf_counter()
+    t_w = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Sig = ogw.selfenergy_tau(V, G, Pt, km, qs=qs, ks=ks)
+    t_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     gam = ogw.density_matrix(grid, G)
-    Sinf = ogw.hartree(V, gam) + ogw.exchange(V, gam)
+    Sinf = ogw.hartree(V, gam) + ogw.exchange(V, gam, kps=[0])
+    t_hf = time.perf_counter() - t0
+    t0 = time.perf_counter()
     Siw = ogw.to_matsubara(grid.TFf, Sig, 0)
     st.Sigma_inf, st.Sigma_iw = Sinf, Siw
     st.dyson()
-    t_rest = time.perf_counter() - t1
-    per_iter = t_slice * nk / nq_sample + t_rest
+    t_rest = time.perf_counter() - t0
+    scale_pairs = (nk * nk) / (nq_sample * nks)
+    per_iter = (t_p + t_s) * scale_pairs + t_w * nk / nq_sample + t_hf * nk + t_rest
     cores = len(os.sched_getaffinity(0))
-    return per_iter, dict(slice_s=t_slice, rest_s=t_rest, cores=cores,
-                          sample="oracle (NumPy complex128) on %d of %d q-slices of A2+A4+A6 plus the "
-                                 "full HF, Sigma transform, mu search and Dyson; seconds per iteration "
-                                 "extrapolated as nq/%d x slice + rest" % (nq_sample, nk, nq_sample))
+    what = ("A2+A6 on %d q x %d k of %d x %d pairs, A4 on %d of %d q, exchange on 1 of %d k', full Hartree, "
+            "Sigma transform, mu search and Dyson" % (nq_sample, nks, nk, nk, nq_sample, nk, nk))
+    return per_iter, dict(cores=cores, parts_s=dict(pairs=t_p + t_s, screened=t_w, hf=t_hf, rest=t_rest),
+                          sample="oracle (NumPy complex128): " + what + "; each part scaled by total/sampled units")
 
 
 # ---------------------------------------------------------------- peaks
@@ -220,7 +279,7 @@ def run_reference(args):
     vals = []
     info = None
     for i in range(args.warmup + args.steps):
-        v, info = cpu_sample(cfg, sysd, args.cpu_sample_q)
+        v, info = cpu_sample(cfg, sysd, args.cpu_sample_q, k_sample_for(cfg))
         if i >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
@@ -232,6 +291,12 @@ def run_reference(args):
                              "sample": info["sample"]},
             "e2e": {"value": value, "unit": "s/iteration", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def k_sample_for(cfg):
+    """k-points per q in the CPU sample: all for small workloads, 2 for the largest."""
+    nk = cfg["kmesh"][0] * cfg["kmesh"][1] * cfg["kmesh"][2]
+    return None if nk * cfg["naux"] * cfg["nao"] ** 2 < 2e7 else 2
 
 
 def workload_config(cfg, name, precision):
@@ -266,8 +331,15 @@ def run_gw(args):
     # replicas: each rank runs its own seeded system of the same workload
     cfg, sysd = make_inputs(args.workload, seed_offset=rank, kmesh=args.kmesh)
     fl = flops(cfg)
-    g = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
-           sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision=args.precision)
+    if sysd.get("V") is None:
+        Vd = device_V(sysd)
+        H0d, Sd = torch.from_numpy(sysd["H0"]).cuda(), torch.from_numpy(sysd["S"]).cuda()
+        g = GW(H0d, Sd, Vd, sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"], sysd["bose_m"],
+               n_elec=sysd["n_elec"], damping=0.5, precision=args.precision, borrow_V=True)
+    else:
+        Vd = None
+        g = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
+               sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision=args.precision)
     g.dyson()
     G0 = g.get("G_tau")
     mu0 = g.get("mu")
@@ -315,8 +387,12 @@ def run_gw(args):
         g.set("G_tau", G0); g.set("mu", mu0); g.reset_sigma()
         g.iterate(1)
         sig_mixed = (g.get("Sigma_inf"), g.get("Sigma_tau"))
-        g64 = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
-                 sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision="fp64")
+        if Vd is not None:
+            g64 = GW(H0d, Sd, Vd, sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"], sysd["bose_m"],
+                     n_elec=sysd["n_elec"], damping=0.5, precision="fp64", borrow_V=True)
+        else:
+            g64 = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
+                     sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision="fp64")
         g64.set("G_tau", G0); g64.set("mu", mu0)
         t64 = []
         for i in range(args.fp64_steps):
@@ -349,8 +425,10 @@ def run_gw(args):
         g.get("G_tau", out=outG)
         g.get("Sigma_iw", out=outS)
         e2e_t.append(time.perf_counter() - t0)
-    e2e = {"value": statistics.median(e2e_t), "unit": "s/iteration",
-           "h2d_bytes_per_step": hG.numel() * 16, "d2h_bytes_per_step": (outG.numel() + outS.numel()) * 16}
+    e2e = None
+    if e2e_t:
+        e2e = {"value": statistics.median(e2e_t), "unit": "s/iteration",
+               "h2d_bytes_per_step": hG.numel() * 16, "d2h_bytes_per_step": (outG.numel() + outS.numel()) * 16}
 
     achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
     traffic = traffic_from_profiles(args.workload, args.precision)
@@ -384,7 +462,7 @@ def run_gw(args):
     line.update(extra)
     g.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, info = cpu_sample(cfg, sysd, args.cpu_sample_q)
+        v, info = cpu_sample(cfg, sysd, args.cpu_sample_q, k_sample_for(cfg))
         line["cpu_baseline"] = {"value": v, "unit": "s/iteration", "cores": info["cores"], "kind": "oracle",
                                 "sample": info["sample"]}
     if rank == 0:

@@ -74,13 +74,15 @@ def hartree(V, gamma, s=2.0):
     return (s / nk) * np.einsum("kQij,Q->kij", Vd, t)
 
 
-def exchange(V, gamma):
-    """Eq. HF_K: K^k_ij = -(1/Nk) sum_{k',Q,ab} V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q)."""
+def exchange(V, gamma, kps=None):
+    """Eq. HF_K: K^k_ij = -(1/Nk) sum_{k',Q,ab} V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q).
+
+    `kps` restricts the k' sum (timing samples only)."""
     nk = gamma.shape[0]
     K = np.zeros_like(gamma)
     naux, nao = V.shape[2], V.shape[3]
     for k in range(nk):
-        for kp in range(nk):
+        for kp in (range(nk) if kps is None else kps):
             A = np.matmul(V[k, kp], gamma[kp])                # [Q, i, b]
             At = A.transpose(1, 0, 2).reshape(nao, naux * nao)  # [i, (Q, b)]
             K[k] -= At @ V[kp, k].reshape(naux * nao, nao)
@@ -89,19 +91,20 @@ def exchange(V, gamma):
 
 # ---------------------------------------------------------------- A2: P~0(tau)
 
-def polarization_tau(V, G_tau, km, s=2.0, symmetrize=True, qs=None):
+def polarization_tau(V, G_tau, km, s=2.0, symmetrize=True, qs=None, ks=None):
     """Eq. tilde_P0_tau (sign/orientation as in the module docstring).
 
     P~0^q_{QQ'}(tau) = (s/Nk) sum_k sum_abcd V^{k,k+q}_da(Q) G^{k+q}_ab(tau)
                                           V^{k+q,k}_bc(Q') G^k_cd(-tau)
-    Returns [nq, ntau, naux, naux] (only the q in `qs` are filled when given).
+    Returns [nq, ntau, naux, naux] (only the q in `qs` are filled when given;
+    `ks` restricts the k-sum, for timing samples only).
     """
     ntau, nk, nao = G_tau.shape[0], G_tau.shape[1], G_tau.shape[2]
     naux = V.shape[2]
     Gm = g_minus_tau(G_tau)
     P = np.zeros((nk, ntau, naux, naux), dtype=np.complex128)
     for q in (range(nk) if qs is None else qs):
-        for k in range(nk):
+        for k in (range(nk) if ks is None else ks):
             kq = km.add(k, q)
             # VG[t, Q, d, b] = sum_a V^{k,k+q}_da(Q) G^{k+q}_ab(t)
             VG = np.matmul(V[k, kq].reshape(naux * nao, nao)[None], G_tau[:, kq])
@@ -134,7 +137,7 @@ def screened(P0_iw):
 
 # ---------------------------------------------------------------- A6: Sigma~(tau)
 
-def selfenergy_tau(V, G_tau, P_tau, km, symmetrize=True, qs=None):
+def selfenergy_tau(V, G_tau, P_tau, km, symmetrize=True, qs=None, ks=None):
     """Eq. tilde_sigma2:
     Sigma~^k_ij(tau) = -(1/Nk) sum_q sum_ab sum_QQ' G^{k-q}_ab(tau) V^{k,k-q}_ia(Q)
                                                    P~^q_QQ'(tau) V^{k-q,k}_bj(Q')
@@ -146,7 +149,7 @@ def selfenergy_tau(V, G_tau, P_tau, km, symmetrize=True, qs=None):
     Sig = np.zeros((ntau, nk, nao, nao), dtype=np.complex128)
     for q in (range(nk) if qs is None else qs):
         PT = np.ascontiguousarray(P_tau[q].transpose(0, 2, 1))           # [t, Q', Q]
-        for k in range(nk):
+        for k in (range(nk) if ks is None else ks):
             kmq = km.sub(k, q)
             # X[t, Q', i, a] = sum_Q P~^q_QQ'(t) V^{k,k-q}_ia(Q)
             X = np.matmul(PT, V[k, kmq].reshape(naux, nao * nao)[None])

@@ -42,7 +42,10 @@ struct gw_ctx {
   // split-TF32 tensor-core operands (hi / lo planes, rows padded to 32 fp32)
   float *Zhi = nullptr, *Zlo = nullptr, *Vhi = nullptr, *Vlo = nullptr;
   float *Pchi = nullptr, *Pclo = nullptr, *VThi = nullptr, *VTlo = nullptr;
-  int64_t kpadP = 0, kpadS = 0;
+  float *Y3hi = nullptr, *Y3lo = nullptr, *W3hi = nullptr, *W3lo = nullptr;   // last Sigma step
+  int64_t kpadP = 0, kpadS = 0, kpad3 = 0;
+  size_t y3bytes = 0;
+  size_t zbytes = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   double* partial = nullptr;
@@ -129,7 +132,7 @@ static cudaError_t run_gett(const GettDesc& d, const void* A, Ty ta, const void*
 // tensor-core launch with optional event timing; flops = useful complex-MAC flops
 static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const UmmaOperand& B, int M, int N,
                             int64_t Kpad, int batch, void* C, bool c_fp64, double alpha, bool accumulate, int64_t c_ld,
-                            int64_t c_zs) {
+                            int64_t c_zs, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0) {
   count(1);
   if (c->prof) {
     while (c->uev.size() < c->uused + 2) {
@@ -140,12 +143,22 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
     }
     cudaEventRecord(c->uev[c->uused], c->st);
   }
-  cudaError_t r = umma_gemm(A, B, M, N, Kpad, batch, C, c_fp64, alpha, accumulate, c_ld, c_zs, 3, c->info + 1, c->st);
+  cudaError_t r = umma_gemm(A, B, M, N, Kpad, batch, C, c_fp64, alpha, accumulate, c_ld, c_zs, 3, c->info + 1, c->st,
+                            ksplit, row_inner, row_s1);
   if (c->prof) {
     cudaEventRecord(c->uev[c->uused + 1], c->st);
     c->uused += 2; c->uflops += flops; c->ulaunch += 1;
   }
   return r;
+}
+
+static cudaError_t run_bsm(gw_ctx* c, BsmDesc d) {
+  const int64_t tot = d.G * d.E;
+  const int64_t target = 152 * 2 * 4;
+  d.per_block = (int)((tot + target - 1) / target);
+  if (d.per_block < 1) d.per_block = 1;
+  count(1);
+  return bsm(d, c->st);
 }
 
 static GettDesc base_desc(int64_t M, int64_t N, int64_t K, int64_t Z) {
@@ -254,6 +267,13 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     c->Zhi = (float*)need(A(zb)); c->Zlo = (float*)need(A(zb));
     c->Vhi = (float*)need(A(vb)); c->Vlo = (float*)need(A(vb));
     c->Pchi = (float*)need(A(pb)); c->Pclo = (float*)need(A(pb));
+    c->zbytes = zb;
+    if (nao <= 64) {
+      c->kpad3 = (2 * (int64_t)naux * nao + 31) / 32 * 32;
+      c->y3bytes = (size_t)ntau * nao * c->kpad3 * 4;
+      c->Y3hi = (float*)need(A(c->y3bytes)); c->Y3lo = (float*)need(A(c->y3bytes));
+      c->W3hi = (float*)need(A((size_t)2 * nao * c->kpad3 * 4)); c->W3lo = (float*)need(A((size_t)2 * nao * c->kpad3 * 4));
+    }
     c->VThi = (float*)need(A(tb)); c->VTlo = (float*)need(A(tb));
   }
   // workspace: split-K partials and the screened-solve panels
@@ -295,6 +315,14 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   chk(cudaMemsetAsync(c->info, 0, 64, st), "memset");
   chk(cudaMemsetAsync(c->Sinf, 0, nk * n2 * cb, st), "memset");
   chk(cudaMemsetAsync(c->Siw, 0, gsz, st), "memset");
+  if (c->Zhi) {
+    chk(cudaMemsetAsync(c->Zhi, 0, c->zbytes, st), "memset");
+    chk(cudaMemsetAsync(c->Zlo, 0, c->zbytes, st), "memset");
+  }
+  if (c->Y3hi) {
+    chk(cudaMemsetAsync(c->Y3hi, 0, c->y3bytes, st), "memset");
+    chk(cudaMemsetAsync(c->Y3lo, 0, c->y3bytes, st), "memset");
+  }
   // grid and transforms
   chk(grid_build_ws(ntau, cfg->beta, c->d_fn, c->d_bm, ld, c->ws, c->tau, c->TFf, c->TFb, c->lb, c->l0, st), "grid");
   count(4);
@@ -432,7 +460,16 @@ static gw_status exchange(gw_ctx* c) {
     d.cm = I2(nao, nao, (int64_t)naux * nao); d.cn = I1(1); d.cz = I1(slab);
     const char* Vb = (const char*)Vp + (size_t)kp * slab * es;
     const char* gb = (const char*)gp + (size_t)kp * n2 * es;
-    CK(run_gett(d, Vb, tv, gb, tg, c->chA, tv, acc, c));
+    if (f32 && nao <= 64) {
+      BsmDesc b{};
+      b.M = b.N = b.K = nao; b.G = nk; b.E = naux; b.alpha = 1.f;
+      b.A = (const float2*)Vb; b.a_gs = (int64_t)nk * slab; b.a_es = n2; b.a_rs = nao; b.a_cs = 1;
+      b.B = (const float2*)gb; b.b_gs = 0; b.b_rs = nao; b.b_cs = 1; b.b_shared = 1;
+      b.C = (float2*)c->chA; b.c_gs = slab; b.c_es = nao; b.c_rs = (int64_t)naux * nao;
+      CK(run_bsm(c, b));
+    } else {
+      CK(run_gett(d, Vb, tv, gb, tg, c->chA, tv, acc, c));
+    }
     // K[k][i][j] += -(1/Nk) sum_{(Q,b)} Y[k][i][(Q,b)] V^{k' k}[Q][b][j]
     GettDesc e = base_desc(nao, nao, (int64_t)naux * nao, nk);
     e.am = I1((int64_t)naux * nao); e.ak = I1(1); e.az = I1(slab);
@@ -477,6 +514,28 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
     for (int k = 0; k < nk; ++k) {
       const int kq = c->kplus[(size_t)q * nk + k];
       const char* Vkq = (const char*)Vp + ((size_t)k * nk + kq) * slab * es;
+      const char* Gm = (const char*)Gp + ((size_t)(ntau - 1) * gstep + (size_t)k * n2) * es;
+      if (f32 && nao <= 64) {
+        // Y[t][Q][d][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b]   (G shared per t)
+        BsmDesc b1{};
+        b1.M = b1.N = b1.K = nao; b1.G = ntau; b1.E = naux; b1.alpha = 1.f;
+        b1.A = (const float2*)Vkq; b1.a_gs = 0; b1.a_es = n2; b1.a_rs = nao; b1.a_cs = 1;
+        b1.B = (const float2*)Gp + (size_t)kq * n2; b1.b_gs = gstep; b1.b_rs = nao; b1.b_cs = 1; b1.b_shared = 1;
+        b1.C = (float2*)c->chA; b1.c_gs = slab; b1.c_es = n2; b1.c_rs = nao;
+        CK(run_bsm(c, b1));
+        // Z[t][Q][c][b] = -sum_d G^k(t_{ntau-1-j})[c][d] Y[t][Q][d][b]   (G^k(-t) shared per t)
+        BsmDesc b2{};
+        b2.M = b2.N = b2.K = nao; b2.G = ntau; b2.E = naux; b2.alpha = -1.f;
+        b2.A = (const float2*)Gm; b2.a_gs = -gstep; b2.a_rs = nao; b2.a_cs = 1; b2.a_shared = 1;
+        b2.B = (const float2*)c->chA; b2.b_gs = slab; b2.b_es = n2; b2.b_rs = nao; b2.b_cs = 1;
+        if (tc) {   // straight into the TF32 hi/lo operand of the tensor-core GEMM
+          const int64_t hk = c->kpadP / 2;
+          b2.Chi = c->Zhi; b2.Clo = c->Zlo; b2.c_gs = (int64_t)naux * hk; b2.c_es = hk; b2.c_rs = nao;
+        } else {
+          b2.C = (float2*)c->chB; b2.c_gs = slab; b2.c_es = n2; b2.c_rs = nao;
+        }
+        CK(run_bsm(c, b2));
+      } else {
       // Y[t][(Q,d)][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b]
       GettDesc d1 = base_desc((int64_t)naux * nao, nao, nao, ntau);
       d1.am = I1(nao); d1.ak = I1(1); d1.az = I1(0);
@@ -489,21 +548,24 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
       d2.bk = I1(nao); d2.bn = I2(nao, n2, 1); d2.bz = I1(slab);
       d2.cm = I1(nao); d2.cn = I2(nao, n2, 1); d2.cz = I1(slab);
       d2.alpha = make_double2(-1, 0);
-      const char* Gm = (const char*)Gp + ((size_t)(ntau - 1) * gstep + (size_t)k * n2) * es;
       CK(run_gett(d2, Gm, tv, c->chA, tv, c->chB, tv, acc, c));
+      }
       // P[t][Q][Q'] += (s/Nk) sum_{(c,b)} Z[t][Q][(c,b)] V^{k+q,k}_{bc}(Q'),
       // with V^{k+q,k}_{bc}(Q') = conj V^{k,k+q}_{cb}(Q') (pairing checked at init)
       if (tc) {
         // tensor cores: split-TF32 real GEMM on the embedded operands
         const int64_t kp = c->kpadP;
-        CK(split_rows(c->chB, false, (int64_t)ntau * naux, n2, n2, false, c->Zhi, c->Zlo, kp, c->st));
+        if (nao > 64) {
+          CK(split_rows(c->chB, false, (int64_t)ntau * naux, n2, n2, false, c->Zhi, c->Zlo, kp, c->st));
+          count(1);
+        }
         CK(embed_conj((const char*)c->V + ((size_t)k * nk + kq) * slab * 16, true, naux, n2, c->Vhi, c->Vlo, kp,
                       c->st));
         UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, kp, 0};
         UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, kp, 0};
         CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, kp, 1, Pq, true,
                     c->spin / nk, k > 0, 2 * (int64_t)naux, 0));
-        count(2);
+        count(1);
         continue;
       }
       GettDesc d3 = base_desc((int64_t)ntau * naux, naux, n2, 1);
@@ -570,6 +632,8 @@ static gw_status sigma_dynamic(gw_ctx* c) {
   const void* Gp = c->G_tau;
   const void* Pp = c->P_tau;
   CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
+  const bool tc3 = tc && c->Y3hi != nullptr;   // last step on tensor cores (atomic fp64 accumulation)
+  if (tc3) CK(cudaMemsetAsync(c->Stau, 0, (size_t)ntau * gstep * 16, c->st));
   const size_t es = f32 ? 8 : 16;
   if (f32) {
     CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st));
@@ -607,12 +671,43 @@ static gw_status sigma_dynamic(gw_ctx* c) {
       CK(run_gett(d1, Pq, tv, Vkk, tv, c->chA, tv, acc, c));
       }
       // Y[t][i][Q'][b] = sum_a X[t][Q'][i][a] G^{k-q}[t][a][b]
+      if (f32 && nao <= 64) {
+        BsmDesc b{};
+        b.M = b.N = b.K = nao; b.G = ntau; b.E = naux; b.alpha = 1.f;
+        b.A = (const float2*)c->chA; b.a_gs = slab; b.a_es = n2; b.a_rs = nao; b.a_cs = 1;
+        b.B = (const float2*)Gp + (size_t)kmq * n2; b.b_gs = gstep; b.b_rs = nao; b.b_cs = 1; b.b_shared = 1;
+        if (tc3) {  // TF32 hi/lo rows (t, i), columns (Q', b): the A operand of the last step
+          const int64_t hk = c->kpad3 / 2;
+          b.Chi = c->Y3hi; b.Clo = c->Y3lo; b.c_gs = nao * hk; b.c_es = nao; b.c_rs = hk;
+        } else {
+          b.C = (float2*)c->chB; b.c_gs = slab; b.c_es = nao; b.c_rs = (int64_t)naux * nao;
+        }
+        CK(run_bsm(c, b));
+      } else {
       GettDesc d2 = base_desc((int64_t)naux * nao, nao, nao, ntau);
       d2.am = I1(nao); d2.ak = I1(1); d2.az = I1(slab);
       d2.bk = I1(nao); d2.bn = I1(1); d2.bz = I1(gstep);
       d2.cm = I2(nao, nao, (int64_t)naux * nao); d2.cn = I1(1); d2.cz = I1(slab);
       CK(run_gett(d2, c->chA, tv, (const char*)Gp + (size_t)kmq * n2 * es, tv, c->chB, tv, acc, c));
+      }
       // Sigma~[t][k][i][j] += -(1/Nk) sum_{(Q',b)} Y[t][i][(Q',b)] V^{k-q,k}[Q'][b][j]
+      if (tc3) {
+        // one GEMM over all (t, i) rows on tensor cores, K split over blocks
+        const int64_t kp = c->kpad3;
+        CK(embed_t((const char*)c->V + ((size_t)kmq * nk + k) * slab * 16, true, (int64_t)naux * nao, nao, c->W3hi,
+                   c->W3lo, kp, c->st));
+        UmmaOperand oa{c->Y3hi, c->Y3lo, (int64_t)ntau * nao, 1, kp, 0};
+        UmmaOperand ob{c->W3hi, c->W3lo, 2 * (int64_t)nao, 1, kp, 0};
+        const int64_t mt = ((int64_t)ntau * nao + 127) / 128, nt = (2 * (int64_t)nao + 159) / 160;
+        int64_t ks = (304 + mt * nt - 1) / (mt * nt);
+        if (ks > kp / 32) ks = kp / 32;
+        if (ks < 1) ks = 1;
+        CK(run_umma(c, 8.0 * ntau * nao * (double)nao * naux * nao, oa, ob, ntau * nao, 2 * nao, kp, 1,
+                    (double*)(c->Stau + (size_t)k * n2), true, -1.0 / nk, true, 2 * (int64_t)nao, 0, (int)ks, nao,
+                    2 * gstep));
+        count(1);
+        continue;
+      }
       GettDesc d3 = base_desc(nao, nao, (int64_t)naux * nao, ntau);
       d3.am = I1((int64_t)naux * nao); d3.ak = I1(1); d3.az = I1(slab);
       d3.bk = I1(nao); d3.bn = I1(1); d3.bz = I1(0);

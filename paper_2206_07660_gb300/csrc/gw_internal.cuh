@@ -92,6 +92,22 @@ cudaError_t check_herm(const double2* X, int64_t n, int64_t count, double* d_max
 cudaError_t maxabs_diff(const double2* a, const double2* b, int64_t n, double* d_out, cudaStream_t st);
 cudaError_t to_c64(const double2* x, float2* y, int64_t n, cudaStream_t st);
 
+// ------------------------------------------------------------------ batched small products (k_bsm.cu)
+// C[g][e] = alpha * A[g][e] * B[g][e] (complex64), M, N, K <= 64; element (r, c) of
+// an operand at base + r*rs + c*cs (complex units); A or B may be shared by all e.
+// Output: complex64 C (C != null) or TF32 hi/lo float planes Chi/Clo (complex index o
+// -> floats 2o, 2o+1); C element (m, n) at g*c_gs + e*c_es + m*c_rs + n.
+struct BsmDesc {
+  int M, N, K;
+  int64_t G, E;
+  int per_block;
+  const float2* A; int64_t a_gs, a_es, a_rs, a_cs; int a_shared, conjA;
+  const float2* B; int64_t b_gs, b_es, b_rs, b_cs; int b_shared, conjB;
+  float2* C; float* Chi; float* Clo; int64_t c_gs, c_es, c_rs;
+  float alpha;
+};
+cudaError_t bsm(const BsmDesc& d, cudaStream_t st);
+
 // ------------------------------------------------------------------ tensor-core split-TF32 GEMM
 struct UmmaOperand {
   const float* hi;
@@ -99,9 +115,12 @@ struct UmmaOperand {
   int64_t rows, batch;   // rows per batch, batch count (1 = shared by all z)
   int64_t ld, bs;        // row stride and batch stride in fp32 elements
 };
+// ksplit > 1: the K range is split over blocks and partial results are added to
+// an fp64 C with atomics (requires accumulate).  row_inner > 0: output row m =
+// o * row_inner + i is written at o * row_s1 + i * c_ld (real elements).
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
-                      cudaStream_t st);
+                      cudaStream_t st, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0);
 cudaError_t split_rows(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, float* hi,
                        float* lo, int64_t Kpad, cudaStream_t st);
 cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, float* hi, float* lo, int64_t Kpad,

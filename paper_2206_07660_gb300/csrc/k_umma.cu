@@ -5,10 +5,14 @@
 //   D[z][m][n] (+)= alpha * sum_seg sum_k A_seg[z][m][k] * B_seg[z][n][k]
 //
 // Both operands are K-major fp32 arrays holding TF32 values, loaded by TMA
-// (3-D tensor maps {K, rows, batch}, 128-byte swizzle) into a 4-stage shared
-// memory ring; one elected thread issues tcgen05.mma (kind::tf32, M = 128,
+// (3-D tensor maps {K, rows, batch}, 128-byte swizzle) into a 3-stage shared
+// memory ring (two blocks per SM, so one block's epilogue overlaps the other's
+// main loop); one elected thread issues tcgen05.mma (kind::tf32, M = 128,
 // N = BN) into a TMEM accumulator; four epilogue warps read it back with
-// tcgen05.ld and add it into an fp64 (or store into an fp32) output.
+// tcgen05.ld every UM_FLUSH k-blocks (double-buffered TMEM) into fp32 register
+// sums, then add the tile into an fp64 (or store into an fp32) output.
+// Short chunks matter: the tensor pipe truncates on each accumulation, which
+// over K ~ 1e4 builds a relative bias of ~1e-4 if left in one accumulator.
 // Split precision: x = hi + lo with hi = tf32(x), lo = tf32(x - hi); the
 // three segments are (A_hi, B_hi), (A_hi, B_lo), (A_lo, B_hi) (lo*lo dropped),
 // giving ~2^-22 relative accuracy per product with fp32 accumulation.
@@ -29,9 +33,10 @@ namespace gwk {
 
 constexpr int UM_BM = 128;
 constexpr int UM_BK = 32;          // fp32 elements per 128-byte swizzle row
-constexpr int UM_STAGES = 4;
+constexpr int UM_STAGES = 3;          // 3 stages x 2 resident blocks per SM
 constexpr int UM_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr uint32_t UM_SPIN_LIMIT = 1u << 26;
+constexpr int UM_FLUSH = 4;       // k-blocks per tensor-pipe accumulation chunk
 
 struct UmmaArgs {
   int M, N;            // real output rows / columns
@@ -42,8 +47,11 @@ struct UmmaArgs {
   int c_fp64;          // 1: C is double and receives C += alpha*D (or = when !accumulate)
   int accumulate;
   double alpha;
-  int64_t c_ld;        // real elements between consecutive rows m
+  int64_t c_ld;        // real elements between consecutive rows m (rows below row_inner)
   int64_t c_zs;        // real elements between batches
+  int64_t row_inner;   // rows m = o * row_inner + i land at o * row_s1 + i * c_ld
+  int64_t row_s1;
+  int ksplit;          // K range split over blockIdx.z; partial results are added atomically
   int* err;
 };
 
@@ -96,30 +104,37 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 }
 
 template <int BN>
-__global__ void __launch_bounds__(UM_THREADS, 1)
+__global__ void __launch_bounds__(UM_THREADS, 2)
     umma_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                 const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, UmmaArgs a) {
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "N tile");
   constexpr uint32_t A_BYTES = UM_BM * UM_BK * 4;
   constexpr uint32_t B_BYTES = BN * UM_BK * 4;
-  constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  constexpr uint32_t TMEM_COLS = 2 * BN <= 32 ? 32 : 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + UM_STAGES * A_BYTES;
   uint64_t* full = (uint64_t*)(sB + UM_STAGES * B_BYTES);
   uint64_t* empty = full + UM_STAGES;
-  uint64_t* done = empty + UM_STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* accf = empty + UM_STAGES;    // accumulator buffer b holds a finished chunk
+  uint64_t* acce = accf + 2;             // accumulator buffer b has been drained
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * UM_BM, z = blockIdx.z;
-  const int total = a.nseg * a.kblocks;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * UM_BM;
+  const int z = blockIdx.z / a.ksplit, split = blockIdx.z - z * a.ksplit;
+  const int kbs = (a.kblocks + a.ksplit - 1) / a.ksplit;
+  const int kb0 = split * kbs, kb1 = min(a.kblocks, kb0 + kbs);
+  const int nkb = kb1 > kb0 ? kb1 - kb0 : 0;
+  const int total = a.nseg * nkb;
+  const int nchunks = (total + UM_FLUSH - 1) / UM_FLUSH;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int s = 0; s < UM_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -139,7 +154,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
         const int s = it % UM_STAGES;
         const uint32_t ph = (uint32_t)(it / UM_STAGES) & 1u;
         if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); break; }
-        const int seg = it / a.kblocks, kb = it - seg * a.kblocks;
+        const int seg = it / nkb, kb = kb0 + (it - seg * nkb);
         const CUtensorMap* ma = (seg == 2) ? &tA1 : &tA0;   // A_hi, A_hi, A_lo
         const CUtensorMap* mb = (seg == 1) ? &tB1 : &tB0;   // B_hi, B_lo, B_hi
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
@@ -152,58 +167,93 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       // instruction descriptor: D fp32, A/B tf32, both K-major, N = BN, M = 128
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                              ((uint32_t)(UM_BM >> 4) << 24);
-      bool ok = true;
+      uint32_t dcur = tmem;
       for (int it = 0; it < total; ++it) {
         const int s = it % UM_STAGES;
         const uint32_t ph = (uint32_t)(it / UM_STAGES) & 1u;
-        if (!mbar_wait(&full[s], ph)) { atomicCAS(&s_fail, 0, 2); ok = false; break; }
+        const int c = it / UM_FLUSH, b = c & 1;
+        const bool chunk_first = (it % UM_FLUSH) == 0;
+        if (chunk_first && c >= 2) {   // buffer b must have been drained (its use c/2 - 1)
+          if (!mbar_wait(&acce[b], (uint32_t)((c / 2 - 1) & 1))) { atomicCAS(&s_fail, 0, 4); break; }
+        }
+        if (!mbar_wait(&full[s], ph)) { atomicCAS(&s_fail, 0, 2); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        dcur = tmem + (uint32_t)(b * BN);
         const uint64_t ad = sw128_desc(sA + s * A_BYTES), bd = sw128_desc(sB + s * B_BYTES);
 #pragma unroll
         for (int kk = 0; kk < UM_BK / 8; ++kk)   // K = 8 tf32 (32 bytes) per instruction
-          umma_tf32(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          umma_tf32(dcur, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                    (!chunk_first || kk > 0) ? 1u : 0u);
         umma_commit(&empty[s]);
+        if ((it % UM_FLUSH) == UM_FLUSH - 1 || it == total - 1) umma_commit(&accf[b]);
       }
-      if (ok) umma_commit(done);
-      else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(done)) : "memory");
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (its accessible lane quarter)
+    // Epilogue warps: warp w owns TMEM lanes 32*(w%4) .. +31, i.e. 32 output rows.
+    // Each finished chunk of at most UM_FLUSH k-blocks is added into fp32 register
+    // sums (round to nearest), which keeps the tensor pipe's own accumulation
+    // short; at the end the row sums go through a shared-memory tile and are
+    // written as whole row segments.
     const int quarter = warp & 3;
-    const bool ok = mbar_wait(done, 0u);
-    if (!ok) atomicCAS(&s_fail, 0, 3);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = m0 + quarter * 32 + lane;
-    const bool live = ok && (s_fail == 0);
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (!live || row >= a.M) continue;
-      const int64_t base = (int64_t)z * a.c_zs + (int64_t)row * a.c_ld;
-      if (a.c_fp64) {
-        double* C = (double*)a.C + base;
+    float acc[BN];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = n0 + c0 + j;
-          if (n < a.N) {
-            const double v = a.alpha * (double)__uint_as_float(r[j]);
-            C[n] = a.accumulate ? C[n] + v : v;
+    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait(&accf[b], (uint32_t)((c / 2) & 1))) { atomicCAS(&s_fail, 0, 3); ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+    }
+    // all MMAs done (their last chunk was drained) -> the pipeline buffers are idle
+    constexpr int LDT = BN + 1;
+    float* tile = (float*)smem;
+    const int r_local = quarter * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < BN; ++j) tile[r_local * LDT + j] = acc[j];
+    asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps only
+    const bool live = ok && (s_fail == 0) && total > 0;
+    const int ew = warp - 2;
+    if (live) {
+      for (int rr = ew; rr < UM_BM; rr += 4) {
+        const int row = m0 + rr;
+        if (row >= a.M) break;
+        const int64_t ro = row / a.row_inner, ri = row - ro * a.row_inner;
+        const int64_t base = (int64_t)z * a.c_zs + ro * a.row_s1 + ri * a.c_ld;
+        const float* trow = tile + rr * LDT;
+        if (a.c_fp64) {
+          double* C = (double*)a.C + base;
+          for (int col = lane; col < BN; col += 32) {
+            const int n = n0 + col;
+            if (n < a.N) {
+              const double v = a.alpha * (double)trow[col];
+              if (a.ksplit > 1) atomicAdd(C + n, v);
+              else C[n] = a.accumulate ? C[n] + v : v;
+            }
           }
-        }
-      } else {
-        float* C = (float*)a.C + base;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = n0 + c0 + j;
-          if (n < a.N) {
-            const float v = (float)a.alpha * __uint_as_float(r[j]);
-            C[n] = a.accumulate ? C[n] + v : v;
+        } else {
+          float* C = (float*)a.C + base;
+          for (int col = lane; col < BN; col += 32) {
+            const int n = n0 + col;
+            if (n < a.N) {
+              const float v = (float)a.alpha * trow[col];
+              C[n] = a.accumulate ? C[n] + v : v;
+            }
           }
         }
       }
@@ -249,7 +299,8 @@ static bool make_map(CUtensorMap* m, const float* base, int64_t kdim, int64_t ro
 
 template <int BN>
 static size_t umma_smem() {
-  return 1024 + (size_t)UM_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + (2 * UM_STAGES + 1) * 8 + 16;
+  static_assert(UM_BM * (BN + 1) * 4 <= UM_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4), "epilogue tile must fit");
+  return 1024 + (size_t)UM_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + (2 * UM_STAGES + 4) * 8 + 16;
 }
 
 template <int BN>
@@ -257,17 +308,28 @@ static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch,
   size_t sm = umma_smem<BN>();
   cudaError_t e = cudaFuncSetAttribute(umma_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.N + BN - 1) / BN, (a.M + UM_BM - 1) / UM_BM, batch);
+  dim3 grid((a.N + BN - 1) / BN, (a.M + UM_BM - 1) / UM_BM, batch * a.ksplit);
   umma_kernel<BN><<<grid, UM_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a);
   return cudaGetLastError();
 }
 
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
-                      cudaStream_t st) {
+                      cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1) {
   if (Kpad % UM_BK) return cudaErrorInvalidValue;
+  if (ksplit < 1) ksplit = 1;
+  if (ksplit > 1 && (!c_fp64 || !accumulate)) return cudaErrorInvalidValue;   // split partials add atomically
+  if ((int64_t)batch * ksplit > 65535) return cudaErrorInvalidValue;
   CUtensorMap maps[4];
-  const int bn = N >= 160 ? 160 : N > 128 ? 160 : N > 64 ? 128 : N > 32 ? 64 : 32;
+  // N tile: trade the padding of the last tile against the per-tile cost of
+  // re-reading the A tile (modelled as 32 extra columns per tile)
+  int bn = 128;
+  double best = -1.0;
+  for (int cand : {128, 112, 96, 80, 64, 48, 32}) {
+    const int64_t nt = (N + cand - 1) / cand;
+    const double eff = (double)N / (double)(nt * cand) * (double)cand / (double)(cand + 32);
+    if (eff > best + 1e-9) { best = eff; bn = cand; }
+  }
   if (!make_map(&maps[0], A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
       !make_map(&maps[1], nseg > 1 ? A.lo : A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
       !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn) ||
@@ -277,11 +339,17 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   a.M = M; a.N = N; a.kblocks = (int)(Kpad / UM_BK); a.nseg = nseg;
   a.a_batched = A.batch > 1; a.b_batched = B.batch > 1;
   a.C = C; a.c_fp64 = c_fp64; a.accumulate = accumulate; a.alpha = alpha; a.c_ld = c_ld; a.c_zs = c_zs;
+  a.ksplit = ksplit;
+  a.row_inner = row_inner > 0 ? row_inner : (int64_t)1 << 40;
+  a.row_s1 = row_s1;
   a.err = err;
   switch (bn) {
-    case 160: return launch_bn<160>(maps, a, batch, st);
     case 128: return launch_bn<128>(maps, a, batch, st);
+    case 112: return launch_bn<112>(maps, a, batch, st);
+    case 96: return launch_bn<96>(maps, a, batch, st);
+    case 80: return launch_bn<80>(maps, a, batch, st);
     case 64: return launch_bn<64>(maps, a, batch, st);
+    case 48: return launch_bn<48>(maps, a, batch, st);
     default: return launch_bn<32>(maps, a, batch, st);
   }
 }
@@ -433,5 +501,35 @@ extern "C" int gwdbg_umma_cgemm(const double2* A, const double2* B, int M, int N
   if (!e) e = cudaDeviceSynchronize();
   cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
   cudaFree(ah); cudaFree(al); cudaFree(bh); cudaFree(bl); cudaFree(err);
+  return e ? (int)e : herr;
+}
+
+// Times `iters` launches of the split-TF32 GEMM on operands of the given shape
+// (contents arbitrary); *ms receives the mean device time per launch.
+extern "C" int gwdbg_umma_bench(int M, int N, int Kpad, int batch, int c_fp64, int iters, double* ms) {
+  using namespace gwk;
+  float *ah, *bh;
+  void* C;
+  int* err;
+  size_t asz = (size_t)M * Kpad * 4 * batch, bsz = (size_t)N * Kpad * 4;
+  if (cudaMalloc(&ah, asz) || cudaMalloc(&bh, bsz) || cudaMalloc(&C, (size_t)M * N * 8 * batch) || cudaMalloc(&err, 4))
+    return -1;
+  cudaMemset(ah, 0, asz); cudaMemset(bh, 0, bsz); cudaMemset(C, 0, (size_t)M * N * 8 * batch); cudaMemset(err, 0, 4);
+  UmmaOperand oa{ah, ah, M, batch, Kpad, (int64_t)M * Kpad}, ob{bh, bh, N, 1, Kpad, 0};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  cudaError_t e = umma_gemm(oa, ob, M, N, Kpad, batch, C, c_fp64, 1.0, true, N, (int64_t)M * N, 3, err, 0);
+  cudaEventRecord(e0, 0);
+  for (int i = 0; i < iters && !e; ++i)
+    e = umma_gemm(oa, ob, M, N, Kpad, batch, C, c_fp64, 1.0, true, N, (int64_t)M * N, 3, err, 0);
+  cudaEventRecord(e1, 0);
+  if (!e) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / iters;
+  int herr = 0;
+  cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+  cudaFree(ah); cudaFree(bh); cudaFree(C); cudaFree(err);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
   return e ? (int)e : herr;
 }

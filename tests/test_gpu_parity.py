@@ -179,14 +179,17 @@ def test_rejects_bad_inputs():
         g.polarization()     # no G yet
 
 
-@pytest.mark.parametrize("nao,naux,kmesh,ntau", [(5, 70, (3, 1, 1), 12), (13, 20, (2, 1, 1), 10)])
-def test_split_tf32_stages(nao, naux, kmesh, ntau):
-    # ragged sizes (K = 2 nao^2 and 2 naux not multiples of the 32-wide tensor-core K block)
+@pytest.mark.parametrize("precision", ["fp32", "split_tf32"])
+@pytest.mark.parametrize("nao,naux,kmesh,ntau", [(5, 70, (3, 1, 1), 12), (13, 20, (2, 1, 1), 10),
+                                                 (64, 9, (1, 1, 1), 6), (65, 6, (1, 1, 1), 4)])
+def test_lowp_stages(nao, naux, kmesh, ntau, precision):
+    # ragged sizes (K = 2 nao^2 and 2 naux not multiples of the 32-wide tensor-core K
+    # block; nao = 64 is the largest batched-small-product size, 65 takes the general kernel)
     sysd = system(nao, naux, kmesh, ntau, 60.0, 21)
     st, G = _perturbed_green(sysd, 6)
     nk = st.km.nk
     P = hermitian_noise((nk, ntau, naux, naux), 0.1, 9)
-    g = gpu(sysd, precision="split_tf32")
+    g = gpu(sysd, precision=precision)
     g.set("G_tau", G)
     g.polarization()
     P0 = ogw.polarization_tau(st.V, G, st.km)
