@@ -153,10 +153,15 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
 }
 
 static cudaError_t run_bsm(gw_ctx* c, BsmDesc d) {
+  // elements per block: a few waves of 2 blocks per SM, and a multiple of the
+  // products one block computes at a time
+  const int T = ((d.M + 3) / 4) * ((d.N + 3) / 4);
+  const int ep = 256 / T < 1 ? 1 : 256 / T;
   const int64_t tot = d.G * d.E;
   const int64_t target = 152 * 2 * 4;
-  d.per_block = (int)((tot + target - 1) / target);
-  if (d.per_block < 1) d.per_block = 1;
+  int64_t per = (tot + target - 1) / target;
+  per = (per + ep - 1) / ep * ep;
+  d.per_block = (int)(per < 1 ? 1 : per);
   count(1);
   return bsm(d, c->st);
 }
