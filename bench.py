@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gw", choices=["gw", "reference"])
-    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3"])
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4"])
     p.add_argument("--precision", default="split_tf32", choices=["split_tf32", "fp32", "fp64"])
     p.add_argument("--fp64-steps", type=int, default=1, help="timed fp64-path iterations for the comparison")
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -286,7 +286,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/iteration",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": workload_config(cfg, args.workload, "fp64-oracle"),
+            "data": "synthetic", "config": workload_config(cfg, args.workload, args.precision),
+            "reference_note": "the CPU oracle (fp64 NumPy) on a bounded sample of the same workload",
             "cpu_baseline": {"value": value, "unit": "s/iteration", "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
             "e2e": {"value": value, "unit": "s/iteration", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -471,12 +472,81 @@ def run_gw(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """C4: 16 seeded systems of uneven sizes, iterated together from captured graphs."""
+    import numpy as np
+    import torch
+    from paper_2206_07660_gb300 import GW
+    from paper_2206_07660_gb300.gw import batch_iterate
+    from synth import batch_configs, make_batch_system
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    prec = args.precision if args.precision != "split_tf32" else "fp32"
+    cfgs = batch_configs()
+    systems, gws = [], []
+    for cfg in cfgs:
+        nk = cfg["kmesh"][0] ** 3
+        big = nk * nk * cfg["naux"] * cfg["nao"] ** 2 * 16 > HOST_V_LIMIT
+        sysd = make_batch_system(cfg, materialize_V=not big)
+        if big:
+            Vd = device_V(sysd)
+            g = GW(torch.from_numpy(sysd["H0"]).cuda(), torch.from_numpy(sysd["S"]).cuda(), Vd, sysd["kmesh"],
+                   sysd["ntau"], sysd["beta"], sysd["fermi_n"], sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5,
+                   precision=prec, borrow_V=True)
+            g._keep = Vd
+        else:
+            g = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
+                   sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision=prec)
+        systems.append(sysd)
+        gws.append(g)
+    flop = sum(flops(dict(c))["P0"] * 2 for c in cfgs)
+    batch_iterate(gws, args.warmup)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    l0 = gws[0].kernel_launches()
+    t0 = time.perf_counter()
+    batch_iterate(gws, args.steps)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    launches = gws[0].kernel_launches() - l0
+    clk = clocks.stop()
+    # the same systems one after another, plain (uncaptured) iterations
+    t0 = time.perf_counter()
+    for g in gws:
+        g.iterate(1)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    line = {"metric": METRIC, "value": dt, "unit": "s/batch-iteration (16 systems)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "c64", "fp64": "c128"}[prec],
+            "data": "synthetic",
+            "config": {"workload": "C4: 16 systems, nao in {8,12,16,26,40}, naux = 8 nao, k-meshes 2^3..4^3, "
+                                   "ntau = nw = 64, beta = 100, %s contractions, captured graphs on per-system "
+                                   "streams" % prec,
+                       "systems": [{"nao": c["nao"], "nk": c["kmesh"][0] ** 3} for c in cfgs],
+                       "l2": "inputs larger than L2", "parallelism": "single GPU"},
+            "contraction_tflops": flop / dt / 1e12, "sequential_plain_s": seq, "batch_speedup": seq / dt,
+            "gpu_launches": None, "clocks": clk}
+    if not args.no_cpu_baseline:
+        tot, parts = 0.0, []
+        for cfg, sysd in zip(cfgs, systems):
+            v, info = cpu_sample(cfg, sysd, 1, k_sample_for(cfg))
+            tot += v
+        line["cpu_baseline"] = {"value": tot, "unit": "s/batch-iteration (16 systems)", "cores": info["cores"],
+                                "kind": "oracle", "sample": "per system: " + info["sample"] + "; summed"}
+    for g in gws:
+        g.close()
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.peaks:
         return measure_peaks()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "C4":
+        return run_batch(args)
     return run_gw(args)
 
 

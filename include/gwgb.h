@@ -183,6 +183,23 @@ gw_status gw_dyson(gw_ctx* ctx, double* mu_out);
  * stats_out (may be NULL) receives the record of the last iteration. */
 gw_status gw_iterate(gw_ctx* ctx, int32_t n_iter, gw_iter_stats* stats_out);
 
+/* n_iter GW iterations replayed from a CUDA graph: the first call captures one
+ * iteration (gw_polarization, gw_screened, gw_selfenergy and a device-side mu
+ * search of min(mu_maxit, 96) bisection steps plus Dyson) on a private stream
+ * of the context and later calls replay it, ordered after cfg->stream by
+ * events.  Status checks are deferred to the end of the call (one
+ * synchronisation).  A first, unmixed GW iteration is run uncaptured when no
+ * self-energy exists yet.  stats_out (may be NULL) gets mu, n_elec, mu_steps
+ * and the mean device time per replay in ms_total. */
+gw_status gw_iterate_graph(gw_ctx* ctx, int32_t n_iter, gw_iter_stats* stats_out);
+
+/* n_iter captured iterations of each of n independent systems (contexts of any
+ * sizes): the systems' graphs are launched round-robin on their own streams so
+ * the GPU overlaps them (the batching pattern of many uneven systems).
+ * Synchronises every context at the end; on failure gw_last_error(NULL) names
+ * the system. */
+gw_status gw_batch_iterate(gw_ctx* const* ctxs, int32_t n, int32_t n_iter);
+
 /* Drop the stored self-energy so that the next gw_selfenergy is not mixed. */
 gw_status gw_reset_sigma(gw_ctx* ctx);
 
@@ -204,6 +221,20 @@ gw_status gw_profile(gw_ctx* ctx, int enable);
  * complex multiply-add), launches; out6[3..5]: the same for the tensor-core
  * kernel.  Synchronises. */
 gw_status gw_profile_read(gw_ctx* ctx, double* out6);
+
+/* Adjoint of gw_polarization's P~0(tau) (Eq. tilde_P0_tau, symmetrised) with
+ * respect to G(tau), at the context's current G: Gbar = sum conj(dP~0/dG) Pbar
+ * for a real loss (PyTorch's conjugate-Wirtinger convention).  Pbar
+ * [nq][ntau][naux][naux] and Gbar [ntau][nk][nao][nao] are device pointers;
+ * Gbar is overwritten.  Runs in fp64 whatever contract_prec is; allocates
+ * three chain buffers of ntau*naux*nao^2 complex on first use. */
+gw_status gw_polarization_vjp(gw_ctx* ctx, const double* Pbar, double* Gbar);
+
+/* Adjoint of gw_selfenergy's Sigma~(tau) (Eq. tilde_sigma2, symmetrised) with
+ * respect to G(tau) and P~(tau), at the context's current G and P~(tau).
+ * Sbar [ntau][nk][nao][nao]; outputs Gbar [ntau][nk][nao][nao] and Pbar
+ * [nq][ntau][naux][naux] are overwritten.  Device pointers; fp64. */
+gw_status gw_selfenergy_vjp(gw_ctx* ctx, const double* Sbar, double* Gbar, double* Pbar);
 
 /* Allocation-free screened solve: P = [I - P0]^{-1} P0 for `count` complex
  * n x n matrices (interleaved (re, im) doubles, row-major, contiguous), the

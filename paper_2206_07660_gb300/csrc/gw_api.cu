@@ -45,6 +45,16 @@ struct gw_ctx {
   float *Y3hi = nullptr, *Y3lo = nullptr, *W3hi = nullptr, *W3lo = nullptr;   // last Sigma step
   int64_t kpadP = 0, kpadS = 0, kpad3 = 0;
   size_t y3bytes = 0;
+  double2 *adjA = nullptr, *adjB = nullptr, *adjC = nullptr;   // fp64 chains of the adjoints (lazy)
+  // captured iteration (gw_iterate_graph): status checks are deferred while capturing
+  bool deferred = false;
+  cudaStream_t gst = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t gev[3]{};
+  // nao-sized steps on tensor cores: V slab split, doubled G(tau) per k, X hi/lo
+  float *Vs_hi = nullptr, *Vs_lo = nullptr, *Ge_hi = nullptr, *Ge_lo = nullptr, *Xs_hi = nullptr, *Xs_lo = nullptr;
+  int64_t kpadA = 0;
   size_t zbytes = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -71,6 +81,11 @@ struct gw_ctx {
 };
 
 static thread_local std::string g_init_err;
+
+// The nao-sized chain steps (K = 2 nao) can run on the tensor-core GEMM, but with
+// one tile per block its fixed per-block cost dominates at these K (measured at
+// nao 52: ~3.8 ms per launch against ~2.2 ms for the batched SIMT kernel).
+static constexpr bool kTensorSmallSteps = false;
 
 #define CK(x)                                                                        \
   do {                                                                               \
@@ -106,6 +121,11 @@ static void free_all(gw_ctx* c) {
   c->pev.clear();
   for (auto& e : c->uev) cudaEventDestroy(e);
   c->uev.clear();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->gst) cudaStreamDestroy(c->gst);
+  for (auto& e : c->gev) if (e) { cudaEventDestroy(e); e = nullptr; }
+  c->gexec = nullptr; c->graph = nullptr; c->gst = nullptr;
 }
 
 static inline void count(int n) { g_launches += n; }
@@ -132,7 +152,8 @@ static cudaError_t run_gett(const GettDesc& d, const void* A, Ty ta, const void*
 // tensor-core launch with optional event timing; flops = useful complex-MAC flops
 static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const UmmaOperand& B, int M, int N,
                             int64_t Kpad, int batch, void* C, bool c_fp64, double alpha, bool accumulate, int64_t c_ld,
-                            int64_t c_zs, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0) {
+                            int64_t c_zs, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
+                            int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr) {
   count(1);
   if (c->prof) {
     while (c->uev.size() < c->uused + 2) {
@@ -144,7 +165,7 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
     cudaEventRecord(c->uev[c->uused], c->st);
   }
   cudaError_t r = umma_gemm(A, B, M, N, Kpad, batch, C, c_fp64, alpha, accumulate, c_ld, c_zs, 3, c->info + 1, c->st,
-                            ksplit, row_inner, row_s1);
+                            ksplit, row_inner, row_s1, col_inner, col_s1, C_lo);
   if (c->prof) {
     cudaEventRecord(c->uev[c->uused + 1], c->st);
     c->uused += 2; c->uflops += flops; c->ulaunch += 1;
@@ -164,6 +185,18 @@ static cudaError_t run_bsm(gw_ctx* c, BsmDesc d) {
   d.per_block = (int)(per < 1 ? 1 : per);
   count(1);
   return bsm(d, c->st);
+}
+
+// Ge[k][t] = doubled operand of conj(G^k(t)) for C = A conj(Ge)^T (TF32 hi/lo); with a
+// Hermitian G(t) that product is A G(t).
+static cudaError_t build_gemb(gw_ctx* c) {
+  const int64_t n2 = c->n2, gstep = (int64_t)c->nk * n2, per = 2 * (int64_t)c->nao * c->kpadA;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < c->nk && !e; ++k)
+    e = embed_conj_batched(c->G_tau + (size_t)k * n2, c->ntau, gstep, c->nao, c->nao, c->Ge_hi + (size_t)k * c->ntau * per,
+                           c->Ge_lo + (size_t)k * c->ntau * per, c->kpadA, per, c->st);
+  count(c->nk);
+  return e;
 }
 
 static GettDesc base_desc(int64_t M, int64_t N, int64_t K, int64_t Z) {
@@ -274,6 +307,14 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     c->Pchi = (float*)need(A(pb)); c->Pclo = (float*)need(A(pb));
     c->zbytes = zb;
     if (nao <= 64) {
+      if (kTensorSmallSteps) {   // nao-sized steps on tensor cores (off: the batched SIMT kernel is faster)
+        c->kpadA = (2 * (int64_t)nao + 31) / 32 * 32;
+        const size_t vs = (size_t)naux * nao * c->kpadA * 4, ge = (size_t)nk * ntau * 2 * nao * c->kpadA * 4;
+        const size_t xs = (size_t)ntau * naux * nao * c->kpadA * 4;
+        c->Vs_hi = (float*)need(A(vs)); c->Vs_lo = (float*)need(A(vs));
+        c->Ge_hi = (float*)need(A(ge)); c->Ge_lo = (float*)need(A(ge));
+        c->Xs_hi = (float*)need(A(xs)); c->Xs_lo = (float*)need(A(xs));
+      }
       c->kpad3 = (2 * (int64_t)naux * nao + 31) / 32 * 32;
       c->y3bytes = (size_t)ntau * nao * c->kpad3 * 4;
       c->Y3hi = (float*)need(A(c->y3bytes)); c->Y3lo = (float*)need(A(c->y3bytes));
@@ -327,6 +368,11 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   if (c->Y3hi) {
     chk(cudaMemsetAsync(c->Y3hi, 0, c->y3bytes, st), "memset");
     chk(cudaMemsetAsync(c->Y3lo, 0, c->y3bytes, st), "memset");
+    if (c->Xs_hi) {
+      const size_t xs = (size_t)ntau * naux * nao * c->kpadA * 4;
+      chk(cudaMemsetAsync(c->Xs_hi, 0, xs, st), "memset");
+      chk(cudaMemsetAsync(c->Xs_lo, 0, xs, st), "memset");
+    }
   }
   // grid and transforms
   chk(grid_build_ws(ntau, cfg->beta, c->d_fn, c->d_bm, ld, c->ws, c->tau, c->TFf, c->TFb, c->lb, c->l0, st), "grid");
@@ -513,13 +559,27 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
   const void* Gp = c->G_tau;
   const size_t es = f32 ? 8 : 16;
   if (f32) { CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st)); count(1); Gp = c->G32; }
-  CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
+  if (!c->deferred) CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
+  const bool tca = tc && c->Vs_hi != nullptr;   // nao-sized first step on tensor cores
+  if (tca) CK(build_gemb(c));
   for (int q = 0; q < nk; ++q) {
     double2* Pq = c->P0_tau + (size_t)q * ntau * na2;
     for (int k = 0; k < nk; ++k) {
       const int kq = c->kplus[(size_t)q * nk + k];
       const char* Vkq = (const char*)Vp + ((size_t)k * nk + kq) * slab * es;
       const char* Gm = (const char*)Gp + ((size_t)(ntau - 1) * gstep + (size_t)k * n2) * es;
+      if (tca) {
+        // Y[t][(Q,d)][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b] on tensor cores (G Hermitian)
+        const int64_t ka = c->kpadA, per = 2 * (int64_t)nao * ka;
+        CK(split_rows((const char*)c->V + ((size_t)k * nk + kq) * slab * 16, true, (int64_t)naux * nao, nao, nao, false,
+                      c->Vs_hi, c->Vs_lo, ka, c->st));
+        UmmaOperand oa{c->Vs_hi, c->Vs_lo, (int64_t)naux * nao, 1, ka, 0};
+        UmmaOperand ob{c->Ge_hi + (size_t)kq * ntau * per, c->Ge_lo + (size_t)kq * ntau * per, 2 * (int64_t)nao, ntau, ka,
+                       per};
+        CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, oa, ob, naux * nao, 2 * nao, ka, ntau, c->chA, false, 1.0,
+                    false, 2 * (int64_t)nao, 2 * slab));
+        count(1);
+      }
       if (f32 && nao <= 64) {
         // Y[t][Q][d][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b]   (G shared per t)
         BsmDesc b1{};
@@ -527,7 +587,7 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
         b1.A = (const float2*)Vkq; b1.a_gs = 0; b1.a_es = n2; b1.a_rs = nao; b1.a_cs = 1;
         b1.B = (const float2*)Gp + (size_t)kq * n2; b1.b_gs = gstep; b1.b_rs = nao; b1.b_cs = 1; b1.b_shared = 1;
         b1.C = (float2*)c->chA; b1.c_gs = slab; b1.c_es = n2; b1.c_rs = nao;
-        CK(run_bsm(c, b1));
+        if (!tca) CK(run_bsm(c, b1));
         // Z[t][Q][c][b] = -sum_d G^k(t_{ntau-1-j})[c][d] Y[t][Q][d][b]   (G^k(-t) shared per t)
         BsmDesc b2{};
         b2.M = b2.N = b2.K = nao; b2.G = ntau; b2.E = naux; b2.alpha = -1.f;
@@ -582,7 +642,7 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
       CK(run_gett(d3, c->chB, tv, Vkq, tv, Pq, Ty::C128, acc, c));
     }
   }
-  if (tc) {
+  if (tc && !c->deferred) {
     int h = 0;
     CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -605,8 +665,8 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
   if (!c->have_P0) return fail(c, GW_ERR_STATE, "no polarization yet");
   const int nk = c->nk, naux = c->naux, ntau = c->ntau;
   const int64_t na2 = c->na2;
-  CK(cudaMemsetAsync(c->info, 0, 4, c->st));
-  CK(screened_inplace(c->P_iw, naux, (int64_t)nk * c->nw, (double2*)c->ws, c->ws_bytes, c->info, c->st));
+  if (!c->deferred) CK(cudaMemsetAsync(c->info + 2, 0, 4, c->st));
+  CK(screened_inplace(c->P_iw, naux, (int64_t)nk * c->nw, (double2*)c->ws, c->ws_bytes, c->info + 2, c->st));
   {
     int64_t nbk = (naux + 63) / 64;
     count((int)(2 + nbk * 6));
@@ -615,12 +675,14 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
   CK(transform(c, c->TBb, c->P_iw, c->P_tau, ntau, na2, nk, (int64_t)c->nw * na2, (int64_t)ntau * na2));
   CK(herm_batched(c->P_tau, naux, (int64_t)nk * ntau, na2, c->st));
   count(1);
-  int h = 0;
-  CK(cudaMemcpyAsync(c->h_scr, c->info, 4, cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
-  memcpy(&h, c->h_scr, 4);
   c->have_P0 = false;   // P~0(i Omega) was overwritten
-  if (h) return fail(c, GW_ERR_SINGULAR, "zero pivot in the screened solve");
+  if (!c->deferred) {
+    int h = 0;
+    CK(cudaMemcpyAsync(c->h_scr, c->info + 2, 4, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    memcpy(&h, c->h_scr, 4);
+    if (h) return fail(c, GW_ERR_SINGULAR, "zero pivot in the screened solve");
+  }
   c->have_P = true;
   return GW_OK;
 }
@@ -636,9 +698,11 @@ static gw_status sigma_dynamic(gw_ctx* c) {
   const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
   const void* Gp = c->G_tau;
   const void* Pp = c->P_tau;
-  CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
+  if (!c->deferred) CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
   const bool tc3 = tc && c->Y3hi != nullptr;   // last step on tensor cores (atomic fp64 accumulation)
   if (tc3) CK(cudaMemsetAsync(c->Stau, 0, (size_t)ntau * gstep * 16, c->st));
+  const bool tc2 = tc3 && c->Xs_hi != nullptr;   // middle step on tensor cores too
+  if (tc2) CK(build_gemb(c));
   const size_t es = f32 ? 8 : 16;
   if (f32) {
     CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st));
@@ -663,8 +727,16 @@ static gw_status sigma_dynamic(gw_ctx* c) {
                    c->st));
         UmmaOperand oa{c->Pchi, c->Pclo, naux, ntau, kp, (int64_t)naux * kp};
         UmmaOperand ob{c->VThi, c->VTlo, 2 * n2, 1, kp, 0};
-        CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, naux, (int)(2 * n2), kp, ntau, c->chA, false,
-                    1.0, false, 2 * n2, (int64_t)naux * 2 * n2));
+        if (tc2) {
+          // X written as TF32 hi/lo rows (t, Q', i) of length kpadA: the A operand of the next step
+          const int64_t ka = c->kpadA;
+          CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, naux, (int)(2 * n2), kp, ntau, c->Xs_hi, false,
+                      1.0, false, (int64_t)nao * ka, (int64_t)naux * nao * ka, 1, 0, 0, 2 * (int64_t)nao, ka,
+                      c->Xs_lo));
+        } else {
+          CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, naux, (int)(2 * n2), kp, ntau, c->chA, false,
+                      1.0, false, 2 * n2, (int64_t)naux * 2 * n2));
+        }
         count(1);
       } else {
       // X[t][Q'][(i,a)] = sum_Q P~^q[t][Q][Q'] V^{k,k-q}[Q][(i,a)]
@@ -676,7 +748,16 @@ static gw_status sigma_dynamic(gw_ctx* c) {
       CK(run_gett(d1, Pq, tv, Vkk, tv, c->chA, tv, acc, c));
       }
       // Y[t][i][Q'][b] = sum_a X[t][Q'][i][a] G^{k-q}[t][a][b]
-      if (f32 && nao <= 64) {
+      if (tc2) {
+        // on tensor cores: rows (Q', i) per t, written as hi/lo rows (t, i) at column block Q'
+        const int64_t ka = c->kpadA, per = 2 * (int64_t)nao * ka;
+        UmmaOperand oa{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka};
+        UmmaOperand ob{c->Ge_hi + (size_t)kmq * ntau * per, c->Ge_lo + (size_t)kmq * ntau * per, 2 * (int64_t)nao, ntau,
+                       ka, per};
+        CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, oa, ob, naux * nao, 2 * nao, ka, ntau, c->Y3hi, false, 1.0,
+                    false, c->kpad3, (int64_t)nao * c->kpad3, 1, nao, 2 * (int64_t)nao, 0, 0, c->Y3lo));
+        count(1);
+      } else if (f32 && nao <= 64) {
         BsmDesc b{};
         b.M = b.N = b.K = nao; b.G = ntau; b.E = naux; b.alpha = 1.f;
         b.A = (const float2*)c->chA; b.a_gs = slab; b.a_es = n2; b.a_rs = nao; b.a_cs = 1;
@@ -724,7 +805,7 @@ static gw_status sigma_dynamic(gw_ctx* c) {
       CK(run_gett(d3, c->chB, tv, Vk2, tv, c->Stau + (size_t)k * n2, Ty::C128, acc, c));
     }
   }
-  if (tc) {
+  if (tc && !c->deferred) {
     int h = 0;
     CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -818,6 +899,29 @@ extern "C" gw_status gw_dyson(gw_ctx* c, double* mu_out) {
   return GW_OK;
 }
 
+// mu search and Dyson with every step on the device (no host reads): the form
+// captured into a graph.  The search restarts around the previous mu and runs a
+// fixed number of (evaluate, step) pairs; converged pairs exit at once.
+static gw_status dyson_device(gw_ctx* c) {
+  DysonArgs a = dyson_args(c);
+  const int64_t nsys = (int64_t)c->nw * c->nk;
+  const double scale = -c->spin / c->nk;
+  const int steps = c->cfg.mu_maxit < 96 ? c->cfg.mu_maxit : 96;
+  CK(mu_init_device(c->mus, c->cfg.n_elec, c->cfg.mu_tol, 1e-13, steps, c->st));
+  count(1);
+  for (int j = 0; j < steps; ++j) {
+    CK(dyson_eval(a, &c->mus->x, nullptr, c->partial, &c->mus->done, c->info, c->st));
+    CK(mu_step(c->mus, c->partial, nsys, scale, c->st));
+    count(2);
+  }
+  CK(dyson_eval(a, &c->mus->x, c->G_iw, nullptr, nullptr, c->info, c->st));
+  const int64_t gstep = (int64_t)c->nk * c->n2;
+  CK(transform(c, c->TBf, c->G_iw, c->G_tau, c->ntau, gstep, 1, 0, 0));
+  CK(herm_batched(c->G_tau, c->nao, (int64_t)c->ntau * c->nk, c->n2, c->st));
+  count(2);
+  return GW_OK;
+}
+
 // ------------------------------------------------------------------ iteration
 
 extern "C" gw_status gw_iterate(gw_ctx* c, int32_t n_iter, gw_iter_stats* stats) {
@@ -884,5 +988,193 @@ extern "C" gw_status gw_profile_read(gw_ctx* c, double* out6) {
   out6[3] = ums; out6[4] = c->uflops; out6[5] = (double)c->ulaunch;
   c->pused = 0; c->pflops = 0.0; c->plaunch = 0;
   c->uused = 0; c->uflops = 0.0; c->ulaunch = 0;
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ adjoints (A10)
+
+namespace gwadj {
+struct View {
+  int nao, naux, nk, ntau;
+  double spin;
+  const double2* V;
+  const double2* G_tau;
+  const double2* P_tau;
+  const int* kplus;
+  const int* kminus;
+  void* ws;
+  size_t ws_bytes;
+  double2 *bufA, *bufB, *bufC;
+  cudaStream_t st;
+};
+cudaError_t polarization_vjp(const View& v, const double2* Pbar, double2* Gbar, int64_t* launches);
+cudaError_t selfenergy_vjp(const View& v, const double2* Sbar, double2* Gbar, double2* Pbar, int64_t* launches);
+}  // namespace gwadj
+
+static gw_status adj_view(gw_ctx* c, gwadj::View* v) {
+  const int64_t n2 = c->n2;
+  size_t need = (size_t)c->ntau * c->naux * n2;
+  if ((size_t)c->ntau * c->na2 > need) need = (size_t)c->ntau * c->na2;
+  if ((size_t)c->ntau * c->nk * n2 > need) need = (size_t)c->ntau * c->nk * n2;
+  if (!c->adjA) {
+    c->adjA = (double2*)dalloc(c, need * 16);
+    c->adjB = (double2*)dalloc(c, need * 16);
+    c->adjC = (double2*)dalloc(c, need * 16);
+    if (!c->adjA || !c->adjB || !c->adjC) return fail(c, GW_ERR_OOM, "adjoint buffers");
+  }
+  v->nao = c->nao; v->naux = c->naux; v->nk = c->nk; v->ntau = c->ntau; v->spin = c->spin;
+  v->V = c->V; v->G_tau = c->G_tau; v->P_tau = c->P_tau;
+  v->kplus = c->kplus.data(); v->kminus = c->kminus.data();
+  v->ws = c->ws; v->ws_bytes = c->ws_bytes;
+  v->bufA = c->adjA; v->bufB = c->adjB; v->bufC = c->adjC;
+  v->st = c->st;
+  return GW_OK;
+}
+
+extern "C" gw_status gw_polarization_vjp(gw_ctx* c, const double* Pbar, double* Gbar) {
+  if (!c || !Pbar || !Gbar) return fail(c, GW_ERR_ARG, "null argument");
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  gwadj::View v;
+  gw_status s = adj_view(c, &v);
+  if (s != GW_OK) return s;
+  CK(cudaMemsetAsync(Gbar, 0, (size_t)c->ntau * c->nk * c->n2 * 16, c->st));
+  int64_t l = 0;
+  CK(gwadj::polarization_vjp(v, (const double2*)Pbar, (double2*)Gbar, &l));
+  count((int)l);
+  return GW_OK;
+}
+
+extern "C" gw_status gw_selfenergy_vjp(gw_ctx* c, const double* Sbar, double* Gbar, double* Pbar) {
+  if (!c || !Sbar || !Gbar || !Pbar) return fail(c, GW_ERR_ARG, "null argument");
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  if (!c->have_P) return fail(c, GW_ERR_STATE, "no screened interaction yet");
+  gwadj::View v;
+  gw_status s = adj_view(c, &v);
+  if (s != GW_OK) return s;
+  CK(cudaMemsetAsync(Gbar, 0, (size_t)c->ntau * c->nk * c->n2 * 16, c->st));
+  CK(cudaMemsetAsync(Pbar, 0, (size_t)c->nk * c->ntau * c->na2 * 16, c->st));
+  int64_t l = 0;
+  CK(gwadj::selfenergy_vjp(v, (const double2*)Sbar, (double2*)Gbar, (double2*)Pbar, &l));
+  count((int)l);
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ captured iterations (A9)
+
+static gw_status capture_iteration(gw_ctx* c) {
+  if (c->gexec) return GW_OK;
+  if (!c->gst) {
+    CK(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking));
+    for (auto& e : c->gev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  const int64_t gsz = (int64_t)c->ntau * c->nk * c->n2;
+  cudaStream_t keep = c->st;
+  c->st = c->gst;
+  c->deferred = true;
+  gw_status s = GW_OK;
+  cudaError_t e = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(c->info, 0, 16, c->gst);
+    cudaMemcpyAsync(c->G_prev, c->G_tau, gsz * 16, cudaMemcpyDeviceToDevice, c->gst);
+    if (s == GW_OK) s = gw_polarization(c);
+    if (s == GW_OK) s = gw_screened(c);
+    if (s == GW_OK) s = gw_selfenergy(c);
+    if (s == GW_OK) s = dyson_device(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->gst, &g);
+    if (s == GW_OK && e2 != cudaSuccess) s = fail(c, GW_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2));
+    if (s == GW_OK) {
+      c->graph = g;
+      e2 = cudaGraphInstantiate(&c->gexec, g, 0);
+      if (e2 != cudaSuccess) s = fail(c, GW_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e2));
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+  } else {
+    s = fail(c, GW_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  }
+  c->deferred = false;
+  c->st = keep;
+  return s;
+}
+
+static gw_status launch_graph(gw_ctx* c) {
+  CK(cudaEventRecord(c->gev[0], c->st));
+  CK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
+  CK(cudaGraphLaunch(c->gexec, c->gst));
+  CK(cudaEventRecord(c->gev[1], c->gst));
+  CK(cudaStreamWaitEvent(c->st, c->gev[1], 0));
+  return GW_OK;
+}
+
+static gw_status finish_graph(gw_ctx* c, gw_iter_stats* stats) {
+  CK(cudaMemcpyAsync(c->h_mus, c->mus, sizeof(MuState), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(c->h_scr + 20, c->info, 16, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  int flags[4];
+  memcpy(flags, c->h_scr + 20, 16);
+  const MuState* h = c->h_mus;
+  c->mu_steps = h->iter;
+  if (flags[1]) return fail(c, GW_ERR_TIMEOUT, "tensor-core contraction gave up waiting");
+  if (flags[2]) return fail(c, GW_ERR_SINGULAR, "zero pivot in the screened solve");
+  if (flags[0]) return fail(c, GW_ERR_SINGULAR, "zero pivot in the Dyson inversion");
+  if (!h->done || h->status != 0) return fail(c, GW_ERR_NOT_CONVERGED, "chemical-potential search hit its cap");
+  c->mu = h->x; c->have_mu = true; c->n_at_mu = h->Nx;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->mu = c->mu; stats->n_elec = c->n_at_mu; stats->mu_steps = c->mu_steps;
+  }
+  return GW_OK;
+}
+
+static gw_status graph_prologue(gw_ctx* c, int32_t* n_iter) {
+  gw_status s;
+  if (!c->have_G) { if ((s = gw_dyson(c, nullptr)) != GW_OK) return s; }
+  if (!c->have_sigma && *n_iter > 0) {   // the first GW iteration is not mixed: run it uncaptured
+    if ((s = gw_iterate(c, 1, nullptr)) != GW_OK) return s;
+    *n_iter -= 1;
+  }
+  return capture_iteration(c);
+}
+
+extern "C" gw_status gw_iterate_graph(gw_ctx* c, int32_t n_iter, gw_iter_stats* stats) {
+  if (!c || n_iter < 0) return GW_ERR_ARG;
+  gw_status s = graph_prologue(c, &n_iter);
+  if (s != GW_OK) return s;
+  CK(cudaEventRecord(c->ev[0], c->st));
+  for (int it = 0; it < n_iter; ++it)
+    if ((s = launch_graph(c)) != GW_OK) return s;
+  CK(cudaEventRecord(c->ev[4], c->st));
+  s = finish_graph(c, stats);
+  if (s == GW_OK && stats && n_iter > 0) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
+    stats->ms_total = ms / n_iter;
+  }
+  return s;
+}
+
+extern "C" gw_status gw_batch_iterate(gw_ctx* const* ctxs, int32_t n, int32_t n_iter) {
+  if (!ctxs || n <= 0 || n_iter < 0) return fail(nullptr, GW_ERR_ARG, "bad batch");
+  std::vector<int32_t> left(n, n_iter);
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(nullptr, GW_ERR_ARG, "null context in batch");
+    gw_status s = graph_prologue(ctxs[i], &left[i]);
+    if (s != GW_OK) { g_init_err = "system " + std::to_string(i) + ": " + ctxs[i]->err; return s; }
+  }
+  // round-robin launches: each system's graph runs on its own stream, so the
+  // GPU overlaps the systems
+  int32_t maxleft = 0;
+  for (int i = 0; i < n; ++i) maxleft = left[i] > maxleft ? left[i] : maxleft;
+  for (int it = 0; it < maxleft; ++it)
+    for (int i = 0; i < n; ++i)
+      if (it < left[i]) {
+        gw_status s = launch_graph(ctxs[i]);
+        if (s != GW_OK) { g_init_err = "system " + std::to_string(i) + ": " + ctxs[i]->err; return s; }
+      }
+  for (int i = 0; i < n; ++i) {
+    gw_status s = finish_graph(ctxs[i], nullptr);
+    if (s != GW_OK) { g_init_err = "system " + std::to_string(i) + ": " + ctxs[i]->err; return s; }
+  }
   return GW_OK;
 }

@@ -78,6 +78,7 @@ struct MuState {
 };
 cudaError_t mu_step(MuState* s, const double* partial, int64_t count, double scale, cudaStream_t st);
 size_t dyson_smem(int nao, int nt);
+cudaError_t mu_init_device(MuState* s, double target, double tol, double width, int maxit, cudaStream_t st);
 
 cudaError_t density_gamma(const double2* G_tau, const double* lb, double2* gamma, int ntau, int64_t nelem,
                           cudaStream_t st);
@@ -117,15 +118,20 @@ struct UmmaOperand {
 };
 // ksplit > 1: the K range is split over blocks and partial results are added to
 // an fp64 C with atomics (requires accumulate).  row_inner > 0: output row m =
-// o * row_inner + i is written at o * row_s1 + i * c_ld (real elements).
+// o * row_inner + i is written at o * row_s1 + i * c_ld (real elements); col_inner
+// > 0: column n = o * col_inner + i at o * col_s1 + i.  C_lo != null: fp32 output
+// written as TF32 hi (C) / lo (C_lo) planes.
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
-                      cudaStream_t st, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0);
+                      cudaStream_t st, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
+                      int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr);
 cudaError_t split_rows(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, float* hi,
                        float* lo, int64_t Kpad, cudaStream_t st);
 cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, float* hi, float* lo, int64_t Kpad,
                        cudaStream_t st);
 cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float* hi, float* lo, int64_t Kpad,
                     cudaStream_t st);
+cudaError_t embed_conj_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
+                               float* lo, int64_t Kpad, int64_t ds, cudaStream_t st);
 
 }  // namespace gwk

@@ -133,6 +133,19 @@ __global__ void __launch_bounds__(1024) mu_step_kernel(MuState* s, const double*
   if (!s->done && s->iter >= s->maxit) { s->done = 1; s->status = 1; }
 }
 
+// Re-arms the search around the previous converged x (device-side, for captured graphs).
+__global__ void mu_init_kernel(MuState* s, double target, double tol, double width, int maxit) {
+  const double center = s->x;
+  s->lo = center - 1.0; s->hi = center + 1.0; s->x = s->lo;
+  s->Nlo = s->Nhi = s->Nx = 0.0;
+  s->target = target; s->tol = tol; s->width = width;
+  s->phase = 0; s->iter = 0; s->maxit = maxit; s->done = 0; s->status = 0;
+}
+cudaError_t mu_init_device(MuState* s, double target, double tol, double width, int maxit, cudaStream_t st) {
+  mu_init_kernel<<<1, 1, 0, st>>>(s, target, tol, width, maxit);
+  return cudaGetLastError();
+}
+
 cudaError_t mu_step(MuState* s, const double* partial, int64_t count, double scale, cudaStream_t st) {
   mu_step_kernel<<<1, 1024, 0, st>>>(s, partial, count, scale);
   return cudaGetLastError();

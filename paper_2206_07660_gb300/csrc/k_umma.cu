@@ -37,6 +37,7 @@ constexpr int UM_STAGES = 3;          // 3 stages x 2 resident blocks per SM
 constexpr int UM_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr uint32_t UM_SPIN_LIMIT = 1u << 26;
 constexpr int UM_FLUSH = 4;       // k-blocks per tensor-pipe accumulation chunk
+static int g_persistent = 0;      // 1: persistent tile loop (umma_pkernel); 0: one tile per block
 
 struct UmmaArgs {
   int M, N;            // real output rows / columns
@@ -51,6 +52,9 @@ struct UmmaArgs {
   int64_t c_zs;        // real elements between batches
   int64_t row_inner;   // rows m = o * row_inner + i land at o * row_s1 + i * c_ld
   int64_t row_s1;
+  int64_t col_inner;   // columns n = o * col_inner + i land at o * col_s1 + i
+  int64_t col_s1;
+  float* C_lo;         // non-null: fp32 output split into TF32 hi (C) and lo (C_lo) planes
   int ksplit;          // K range split over blockIdx.z; partial results are added atomically
   int* err;
 };
@@ -101,6 +105,12 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+__device__ __forceinline__ float tf32_rna_dev(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 template <int BN>
@@ -248,14 +258,231 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
           }
         } else {
           float* C = (float*)a.C + base;
+          float* Cl = a.C_lo ? a.C_lo + base : nullptr;
           for (int col = lane; col < BN; col += 32) {
             const int n = n0 + col;
             if (n < a.N) {
+              const int64_t co = n / a.col_inner, ci = n - co * a.col_inner;
+              const int64_t off = co * a.col_s1 + ci;
               const float v = (float)a.alpha * trow[col];
-              C[n] = a.accumulate ? C[n] + v : v;
+              if (Cl) {
+                const float h = tf32_rna_dev(v);
+                C[off] = h;
+                Cl[off] = tf32_rna_dev(v - h);
+              } else {
+                C[off] = a.accumulate ? C[off] + v : v;
+              }
             }
           }
         }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && s_fail && a.err) atomicCAS(a.err, 0, 100 + s_fail);
+}
+
+// ------------------------------------------------------------------ persistent variant
+// One block per SM walks a static list of output tiles (n fastest, so blocks
+// running together share A tiles in L2).  Stage and chunk counters continue
+// across tiles; four TMEM chunk buffers let the MMA thread run up to three
+// chunks ahead of the epilogue, whose write-out of tile t overlaps the main
+// loop of tile t+1.  The write-out goes through a 32 x 33 staging tile per
+// epilogue warp (coalesced rows).
+constexpr int UP_STAGES = 6;
+constexpr int UP_TBUF = 4;
+
+__device__ __forceinline__ void umma_store(const UmmaArgs& a, int z, int row, int n, float acc) {
+  const int64_t ro = row / a.row_inner, ri = row - ro * a.row_inner;
+  const int64_t base = (int64_t)z * a.c_zs + ro * a.row_s1 + ri * a.c_ld;
+  if (a.c_fp64) {
+    double* C = (double*)a.C + base;
+    const double v = a.alpha * (double)acc;
+    if (a.ksplit > 1) atomicAdd(C + n, v);
+    else C[n] = a.accumulate ? C[n] + v : v;
+  } else {
+    const int64_t co = n / a.col_inner, ci = n - co * a.col_inner;
+    const int64_t off = base + co * a.col_s1 + ci;
+    const float v = (float)a.alpha * acc;
+    float* C = (float*)a.C;
+    if (a.C_lo) {
+      const float h = tf32_rna_dev(v);
+      C[off] = h;
+      a.C_lo[off] = tf32_rna_dev(v - h);
+    } else {
+      C[off] = a.accumulate ? C[off] + v : v;
+    }
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(UM_THREADS, 1)
+    umma_pkernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+                 const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, UmmaArgs a,
+                 int ntn, int ntm, int ntiles) {
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "N tile");
+  constexpr uint32_t A_BYTES = UM_BM * UM_BK * 4;
+  constexpr uint32_t B_BYTES = BN * UM_BK * 4;
+  constexpr uint32_t NEED = UP_TBUF * BN;
+  constexpr uint32_t TMEM_COLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + UP_STAGES * A_BYTES;
+  float* stage_all = (float*)(sB + UP_STAGES * B_BYTES);          // 4 warps x 32 x 33 floats
+  uint64_t* full = (uint64_t*)(stage_all + 4 * 32 * 33);
+  uint64_t* empty = full + UP_STAGES;
+  uint64_t* accf = empty + UP_STAGES;
+  uint64_t* acce = accf + UP_TBUF;
+  uint32_t* tmem_slot = (uint32_t*)(acce + UP_TBUF);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kbs = (a.kblocks + a.ksplit - 1) / a.ksplit;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < UP_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < UP_TBUF; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // tile t -> (n tile, m tile, batch*split)
+  auto decode = [&](int t, int& n0, int& m0, int& z, int& kb0, int& nkb) {
+    const int tn = t % ntn, r = t / ntn, tm = r % ntm, zz = r / ntm;
+    z = zz / a.ksplit;
+    const int split = zz - z * a.ksplit;
+    n0 = tn * BN; m0 = tm * UM_BM;
+    kb0 = split * kbs;
+    const int kb1 = min(a.kblocks, kb0 + kbs);
+    nkb = kb1 > kb0 ? kb1 - kb0 : 0;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (*(volatile int*)&s_fail) break;
+        int n0, m0, z, kb0, nkb;
+        decode(t, n0, m0, z, kb0, nkb);
+        const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
+        const int total = a.nseg * nkb;
+        bool ok = true;
+        for (int it = 0; it < total; ++it, ++g) {
+          const int s = g % UP_STAGES;
+          const uint32_t ph = (g / UP_STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); ok = false; break; }
+          const int seg = it / nkb, kb = kb0 + (it - seg * nkb);
+          const CUtensorMap* ma = (seg == 2) ? &tA1 : &tA0;
+          const CUtensorMap* mb = (seg == 1) ? &tB1 : &tB0;
+          mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+          tma_load_3d(sA + s * A_BYTES, ma, &full[s], kb * UM_BK, m0, za);
+          tma_load_3d(sB + s * B_BYTES, mb, &full[s], kb * UM_BK, n0, zb);
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)(UM_BM >> 4) << 24);
+      uint32_t g = 0, cg = 0;   // global k-iteration and chunk counters
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (*(volatile int*)&s_fail) break;
+        int n0, m0, z, kb0, nkb;
+        decode(t, n0, m0, z, kb0, nkb);
+        const int total = a.nseg * nkb;
+        bool ok = true;
+        for (int it = 0; it < total; ++it, ++g) {
+          const int s = g % UP_STAGES;
+          const uint32_t ph = (g / UP_STAGES) & 1u;
+          const uint32_t chunk = cg + (uint32_t)(it / UM_FLUSH);
+          const int b = chunk % UP_TBUF;
+          const uint32_t u = chunk / UP_TBUF;
+          const bool chunk_first = (it % UM_FLUSH) == 0;
+          if (chunk_first && u >= 1) {
+            if (!mbar_wait(&acce[b], (u - 1) & 1u)) { atomicCAS(&s_fail, 0, 4); ok = false; break; }
+          }
+          if (!mbar_wait(&full[s], ph)) { atomicCAS(&s_fail, 0, 2); ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d = tmem + (uint32_t)(b * BN);
+          const uint64_t ad = sw128_desc(sA + s * A_BYTES), bd = sw128_desc(sB + s * B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < UM_BK / 8; ++kk)
+            umma_tf32(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (!chunk_first || kk > 0) ? 1u : 0u);
+          umma_commit(&empty[s]);
+          if ((it % UM_FLUSH) == UM_FLUSH - 1 || it == total - 1) umma_commit(&accf[b]);
+        }
+        if (!ok) break;
+        cg += (uint32_t)((total + UM_FLUSH - 1) / UM_FLUSH);
+      }
+    }
+  } else {
+    const int quarter = warp & 3;
+    float* stg = stage_all + (warp - 2) * 32 * 33;
+    uint32_t cg = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      if (*(volatile int*)&s_fail) break;
+      int n0, m0, z, kb0, nkb;
+      decode(t, n0, m0, z, kb0, nkb);
+      const int total = a.nseg * nkb;
+      const int nch = (total + UM_FLUSH - 1) / UM_FLUSH;
+      float acc[BN];
+#pragma unroll
+      for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+      bool ok = true;
+      for (int c = 0; c < nch; ++c) {
+        const uint32_t chunk = cg + (uint32_t)c;
+        const int b = chunk % UP_TBUF;
+        const uint32_t u = chunk / UP_TBUF;
+        if (!mbar_wait(&accf[b], u & 1u)) { atomicCAS(&s_fail, 0, 3); ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+      }
+      if (!ok) break;
+      cg += (uint32_t)nch;
+      if (total == 0) continue;
+      // write-out: 32 x 32 blocks through the staging tile, one row per lane-sweep
+#pragma unroll
+      for (int cb = 0; cb < BN; cb += 32) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (cb + j < BN) stg[lane * 33 + j] = acc[cb + j];
+        __syncwarp();
+        for (int r = 0; r < 32; ++r) {
+          const int row = m0 + quarter * 32 + r;
+          const int col = cb + lane, n = n0 + col;
+          if (row < a.M && col < BN && n < a.N) umma_store(a, z, row, n, stg[r * 33 + lane]);
+        }
+        __syncwarp();
       }
     }
   }
@@ -304,7 +531,32 @@ static size_t umma_smem() {
 }
 
 template <int BN>
+static size_t umma_psmem() {
+  return 1024 + (size_t)UP_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + 4 * 32 * 33 * 4 +
+         (2 * UP_STAGES + 2 * UP_TBUF) * 8 + 16;
+}
+
+static int g_num_sms = 0;
+
+template <int BN>
 static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch, cudaStream_t st) {
+  if (g_persistent) {
+    if (!g_num_sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+      if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    size_t sm = umma_psmem<BN>();
+    cudaError_t e = cudaFuncSetAttribute(umma_pkernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int ntn = (a.N + BN - 1) / BN, ntm = (a.M + UM_BM - 1) / UM_BM;
+    const int64_t ntiles = (int64_t)ntn * ntm * batch * a.ksplit;
+    if (ntiles > INT32_MAX) return cudaErrorInvalidValue;
+    const int grid = (int)(ntiles < g_num_sms ? ntiles : g_num_sms);
+    umma_pkernel<BN><<<grid, UM_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a, ntn, ntm, (int)ntiles);
+    return cudaGetLastError();
+  }
   size_t sm = umma_smem<BN>();
   cudaError_t e = cudaFuncSetAttribute(umma_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -315,7 +567,8 @@ static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch,
 
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
-                      cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1) {
+                      cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1, int64_t col_inner,
+                      int64_t col_s1, float* C_lo) {
   if (Kpad % UM_BK) return cudaErrorInvalidValue;
   if (ksplit < 1) ksplit = 1;
   if (ksplit > 1 && (!c_fp64 || !accumulate)) return cudaErrorInvalidValue;   // split partials add atomically
@@ -342,6 +595,10 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   a.ksplit = ksplit;
   a.row_inner = row_inner > 0 ? row_inner : (int64_t)1 << 40;
   a.row_s1 = row_s1;
+  a.col_inner = col_inner > 0 ? col_inner : (int64_t)1 << 40;
+  a.col_s1 = col_s1;
+  a.C_lo = C_lo;
+  if (C_lo && (c_fp64 || accumulate)) return cudaErrorInvalidValue;
   a.err = err;
   switch (bn) {
     case 128: return launch_bn<128>(maps, a, batch, st);
@@ -407,6 +664,26 @@ __global__ void embed_conj_kernel(const T* __restrict__ src, int64_t rows, int64
   }
 }
 
+// Batched embed_conj: `count` matrices of `rows` x K complex (src stride `ss` complex
+// elements) into `count` doubled operands of 2*rows x Kpad floats (dst stride `ds`).
+__global__ void embed_conj_batched_kernel(const double2* __restrict__ src, int64_t count, int64_t ss, int64_t rows,
+                                          int64_t K, float* hi, float* lo, int64_t Kpad, int64_t ds) {
+  const int64_t per = 2 * rows * Kpad, tot = per * count;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t z = e / per, r = e - z * per, r2 = r / Kpad, c = r - r2 * Kpad, n = r2 >> 1;
+    double v = 0.0;
+    if (c < 2 * K) {
+      const double2 x = src[z * ss + n * K + (c >> 1)];
+      if ((r2 & 1) == 0) v = (c & 1) ? x.y : x.x;
+      else v = (c & 1) ? x.x : -x.y;
+    }
+    float h, l;
+    split2(v, h, l);
+    hi[z * ds + r] = h;
+    lo[z * ds + r] = l;
+  }
+}
+
 // Doubled operand of C = A B^T where B[n][k] = src[k][n] (src: K rows of N complex):
 // rows 2n = (re, -im), rows 2n+1 = (im, re), transposed through shared memory.
 template <typename T>
@@ -464,6 +741,12 @@ cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, 
   else embed_conj_kernel<float2><<<nb_(2 * rows * Kpad), 256, 0, st>>>((const float2*)src, rows, K, hi, lo, Kpad);
   return cudaGetLastError();
 }
+cudaError_t embed_conj_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
+                               float* lo, int64_t Kpad, int64_t ds, cudaStream_t st) {
+  embed_conj_batched_kernel<<<nb_(2 * rows * Kpad * count), 256, 0, st>>>(src, count, ss, rows, K, hi, lo, Kpad, ds);
+  return cudaGetLastError();
+}
+
 cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float* hi, float* lo, int64_t Kpad,
                     cudaStream_t st) {
   dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32));
@@ -479,8 +762,27 @@ cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float*
 // public header).  All pointers are device pointers; the scratch is allocated
 // here with cudaMalloc.  Returns 0 on success, else a CUDA error or kernel code.
 
+// Selects the kernel variant used by every later tensor-core GEMM of this
+// process: 1 = persistent tile loop (the default), 0 = one output tile per block.
+extern "C" int gwdbg_umma_set_persistent(int on) {
+  const int old = gwk::g_persistent;
+  gwk::g_persistent = on ? 1 : 0;
+  return old;
+}
+
+// C[M][N] = A[M][K] * op(B) with complex128 operands, op(B) = conj(B[N][K])^T
+// (conjB) or B[K][N].  ksplit > 1 splits the K range over blocks and adds the
+// partial sums atomically into C, which is zeroed first.
+extern "C" int gwdbg_umma_cgemm_split(const double2* A, const double2* B, int M, int N, int K, int conjB, int nseg,
+                                      int ksplit, double* C);
+
 extern "C" int gwdbg_umma_cgemm(const double2* A, const double2* B, int M, int N, int K, int conjB, int nseg,
                                 double* C) {
+  return gwdbg_umma_cgemm_split(A, B, M, N, K, conjB, nseg, 1, C);
+}
+
+extern "C" int gwdbg_umma_cgemm_split(const double2* A, const double2* B, int M, int N, int K, int conjB, int nseg,
+                                      int ksplit, double* C) {
   using namespace gwk;
   const int64_t Kpad = ((2 * (int64_t)K + UM_BK - 1) / UM_BK) * UM_BK;
   float *ah, *al, *bh, *bl;
@@ -496,7 +798,8 @@ extern "C" int gwdbg_umma_cgemm(const double2* A, const double2* B, int M, int N
     else e = embed_t(B, true, K, N, bh, bl, Kpad, 0);   // B given as [K][N]: C = A B
   }
   UmmaOperand oa{ah, al, M, 1, Kpad, 0}, ob{bh, bl, 2 * (int64_t)N, 1, Kpad, 0};
-  if (!e) e = umma_gemm(oa, ob, M, 2 * N, Kpad, 1, C, true, 1.0, false, 2 * N, 0, nseg, err, 0);
+  if (!e && ksplit > 1) e = cudaMemset(C, 0, (size_t)M * 2 * N * 8);
+  if (!e) e = umma_gemm(oa, ob, M, 2 * N, Kpad, 1, C, true, 1.0, ksplit > 1, 2 * N, 0, nseg, err, 0, ksplit);
   int herr = 0;
   if (!e) e = cudaDeviceSynchronize();
   cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);

@@ -72,15 +72,29 @@ def load():
     lib.gw_iterate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(GwIterStats)]
     lib.gw_last_error.argtypes = [P]
     lib.gw_last_error.restype = ctypes.c_char_p
+    lib.gw_iterate_graph.argtypes = [P, ctypes.c_int32, ctypes.POINTER(GwIterStats)]
+    lib.gw_batch_iterate.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32]
+    lib.gw_polarization_vjp.argtypes = [P, P, P]
+    lib.gw_selfenergy_vjp.argtypes = [P, P, P, P]
     lib.gw_profile.argtypes = [P, ctypes.c_int]
     lib.gw_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.gw_kernel_launches.argtypes = [P]
     lib.gw_kernel_launches.restype = ctypes.c_int64
     for name in ("gw_init", "gw_destroy", "gw_set", "gw_get", "gw_hf", "gw_polarization", "gw_screened",
-                 "gw_selfenergy", "gw_dyson", "gw_iterate", "gw_reset_sigma", "gw_profile", "gw_profile_read"):
+                 "gw_selfenergy", "gw_dyson", "gw_iterate", "gw_reset_sigma", "gw_profile", "gw_profile_read",
+                 "gw_polarization_vjp", "gw_selfenergy_vjp", "gw_iterate_graph", "gw_batch_iterate"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def batch_iterate(systems, n=1):
+    """n captured iterations of several GW contexts, overlapped on their own streams."""
+    lib = load()
+    arr = (ctypes.c_void_p * len(systems))(*[s.ctx.value if hasattr(s.ctx, "value") else s.ctx for s in systems])
+    st = lib.gw_batch_iterate(arr, len(systems), int(n))
+    if st != GW_OK:
+        raise GWError(st, lib.gw_last_error(None).decode())
 
 
 class GWError(RuntimeError):
@@ -244,6 +258,24 @@ class GW:
         self._check(self.lib.gw_iterate(self.ctx, int(n), ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in GwIterStats._fields_}
 
+    # -- adjoints (device tensors, complex128, contiguous)
+    def polarization_vjp(self, Pbar):
+        """Gbar = VJP of the symmetrised P~0(tau) w.r.t. G(tau) at the current G."""
+        torch = self.torch
+        Pbar = Pbar.contiguous()
+        Gbar = torch.empty(self.shape_of("G_tau"), dtype=torch.complex128, device=Pbar.device)
+        self._check(self.lib.gw_polarization_vjp(self.ctx, Pbar.data_ptr(), Gbar.data_ptr()))
+        return Gbar
+
+    def selfenergy_vjp(self, Sbar):
+        """(Gbar, Pbar) = VJP of the symmetrised Sigma~(tau) w.r.t. (G(tau), P~(tau))."""
+        torch = self.torch
+        Sbar = Sbar.contiguous()
+        Gbar = torch.empty(self.shape_of("G_tau"), dtype=torch.complex128, device=Sbar.device)
+        Pbar = torch.empty(self.shape_of("P_tau"), dtype=torch.complex128, device=Sbar.device)
+        self._check(self.lib.gw_selfenergy_vjp(self.ctx, Sbar.data_ptr(), Gbar.data_ptr(), Pbar.data_ptr()))
+        return Gbar, Pbar
+
     def profile(self, enable=True):
         self._check(self.lib.gw_profile(self.ctx, int(bool(enable))))
 
@@ -253,6 +285,12 @@ class GW:
         self._check(self.lib.gw_profile_read(self.ctx, out))
         return {"simt": (float(out[0]), float(out[1]), int(out[2])),
                 "tensor": (float(out[3]), float(out[4]), int(out[5]))}
+
+    def iterate_graph(self, n=1):
+        """n iterations replayed from a captured CUDA graph (see gw_iterate_graph)."""
+        s = GwIterStats()
+        self._check(self.lib.gw_iterate_graph(self.ctx, int(n), ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in GwIterStats._fields_}
 
     def kernel_launches(self):
         return int(self.lib.gw_kernel_launches(self.ctx))

@@ -4,8 +4,9 @@ Holds no arithmetic of the GW method itself: it only draws H0(k), S(k),
 V^{kk'}(Q), picks the sampled Matsubara integers and names the workloads.
 """
 from .generate import (CONFIGS, SEED_BASE, config_seed, matsubara_indices, v_slab,
-                       make_config_system,
+                       make_config_system, batch_configs, make_batch_system,
                        make_system, kmesh_size)
 
 __all__ = ["CONFIGS", "SEED_BASE", "config_seed", "matsubara_indices", "v_slab", "make_config_system",
+           "batch_configs", "make_batch_system",
            "make_system", "kmesh_size"]

@@ -188,6 +188,28 @@ def v_slab(sysd, k, k2):
 
 
 
+def batch_configs(n_systems=16, nao_set=(8, 12, 16, 26, 40), mesh_set=(2, 3, 4), ntau=64, beta=100.0,
+                  name="C4"):
+    """Sizes of the uneven batch: per system nao from nao_set and an n x n x n
+    mesh from mesh_set, drawn from the system's own seed; naux = 8 nao."""
+    out = []
+    for s in range(n_systems):
+        rng = np.random.Generator(np.random.PCG64(config_seed(name, s) + 1))
+        nao = int(rng.choice(nao_set))
+        n = int(rng.choice(mesh_set))
+        out.append(dict(nao=nao, naux=8 * nao, kmesh=(n, n, n), ntau=ntau, beta=beta, cV_scale=0.35,
+                        seed=config_seed(name, s)))
+    return out
+
+
+def make_batch_system(cfg, materialize_V=True):
+    cV = cfg.get("cV_scale", 1.0) / np.sqrt(cfg["nao"])
+    sysd = make_system(cfg["nao"], cfg["naux"], cfg["kmesh"], cfg["seed"], materialize_V=materialize_V, cV=cV)
+    fn, bm = matsubara_indices(cfg["ntau"])
+    sysd.update(ntau=int(cfg["ntau"]), beta=float(cfg["beta"]), fermi_n=fn, bose_m=bm, n_elec=float(cfg["nao"]))
+    return sysd
+
+
 def make_config_system(name, system=0, trs=False, materialize_V=True, **over):
     """System plus grid integers for a named workload (sizes overridable)."""
     cfg = dict(CONFIGS[name])
