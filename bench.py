@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--impl", default="gw", choices=["gw", "reference"])
     p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4"])
     p.add_argument("--precision", default="split_tf32", choices=["split_tf32", "fp32", "fp64"])
+    p.add_argument("--small-steps", default="auto", choices=["auto", "tensor", "simt"],
+                   help="placement of the nao-sized chain steps in the split_tf32 path")
     p.add_argument("--fp64-steps", type=int, default=1, help="timed fp64-path iterations for the comparison")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -336,11 +338,13 @@ def run_gw(args):
         Vd = device_V(sysd)
         H0d, Sd = torch.from_numpy(sysd["H0"]).cuda(), torch.from_numpy(sysd["S"]).cuda()
         g = GW(H0d, Sd, Vd, sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"], sysd["bose_m"],
-               n_elec=sysd["n_elec"], damping=0.5, precision=args.precision, borrow_V=True)
+               n_elec=sysd["n_elec"], damping=0.5, precision=args.precision, borrow_V=True,
+               small_steps=args.small_steps)
     else:
         Vd = None
         g = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
-               sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision=args.precision)
+               sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision=args.precision,
+               small_steps=args.small_steps)
     g.dyson()
     G0 = g.get("G_tau")
     mu0 = g.get("mu")

@@ -71,7 +71,11 @@ typedef enum {
 enum {
   GW_INPUT_DEVICE = 1u << 0, /* H0, S, V passed to gw_init are device pointers   */
   GW_BORROW_V     = 1u << 1, /* with GW_INPUT_DEVICE: use V in place, no copy     */
-  GW_SKIP_CHECKS  = 1u << 2  /* skip the Hermiticity / pairing checks of gw_init  */
+  GW_SKIP_CHECKS  = 1u << 2, /* skip the Hermiticity / pairing checks of gw_init  */
+  GW_SMALL_TENSOR = 1u << 3, /* GW_SPLIT_TF32, nao <= 64: the nao-sized steps of the
+                                P~0 / Sigma~ chains also on tensor cores (split TF32)  */
+  GW_SMALL_SIMT   = 1u << 4  /* GW_SPLIT_TF32, nao <= 64: those steps on the FP32
+                                SIMT small-product kernel.  Neither flag: library default */
 };
 
 typedef void* (*gw_alloc_fn)(void* user, size_t bytes);
@@ -95,7 +99,8 @@ typedef struct {
   gw_alloc_fn dev_alloc;  /* optional device allocator                            */
   gw_free_fn dev_free;
   void* alloc_user;
-  uint64_t flags;         /* GW_INPUT_DEVICE | GW_BORROW_V | GW_SKIP_CHECKS        */
+  uint64_t flags;         /* GW_INPUT_DEVICE | GW_BORROW_V | GW_SKIP_CHECKS |
+                             GW_SMALL_TENSOR | GW_SMALL_SIMT                        */
 } gw_config;
 
 /* Quantities readable with gw_get / writable with gw_set.  Sizes in bytes. */

@@ -54,6 +54,7 @@ struct gw_ctx {
   cudaEvent_t gev[3]{};
   // nao-sized steps on tensor cores: V slab split, doubled G(tau) per k, X hi/lo
   float *Vs_hi = nullptr, *Vs_lo = nullptr, *Ge_hi = nullptr, *Ge_lo = nullptr, *Xs_hi = nullptr, *Xs_lo = nullptr;
+  float *Gp_hi = nullptr, *Gp_lo = nullptr;
   int64_t kpadA = 0;
   size_t zbytes = 0;
   void* ws = nullptr;
@@ -85,7 +86,7 @@ static thread_local std::string g_init_err;
 // The nao-sized chain steps (K = 2 nao) can run on the tensor-core GEMM, but with
 // one tile per block its fixed per-block cost dominates at these K (measured at
 // nao 52: ~3.8 ms per launch against ~2.2 ms for the batched SIMT kernel).
-static constexpr bool kTensorSmallSteps = false;
+static constexpr bool kTensorSmallSteps = false;   // GW_SMALL_TENSOR / GW_SMALL_SIMT override
 
 #define CK(x)                                                                        \
   do {                                                                               \
@@ -188,13 +189,21 @@ static cudaError_t run_bsm(gw_ctx* c, BsmDesc d) {
 }
 
 // Ge[k][t] = doubled operand of conj(G^k(t)) for C = A conj(Ge)^T (TF32 hi/lo); with a
-// Hermitian G(t) that product is A G(t).
+// Hermitian G(t) that product is A G(t).  Gp (polarization only) holds the reversed
+// plain operands G^k(t_{ntau-1-j}).
 static cudaError_t build_gemb(gw_ctx* c) {
   const int64_t n2 = c->n2, gstep = (int64_t)c->nk * n2, per = 2 * (int64_t)c->nao * c->kpadA;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < c->nk && !e; ++k)
     e = embed_conj_batched(c->G_tau + (size_t)k * n2, c->ntau, gstep, c->nao, c->nao, c->Ge_hi + (size_t)k * c->ntau * per,
                            c->Ge_lo + (size_t)k * c->ntau * per, c->kpadA, per, c->st);
+  count(c->nk);
+  if (!c->Gp_hi) return e;
+  // Gp[k][j] = doubled operand of G^k(t_{ntau-1-j}) for C = A Gp^T (the G(-t) factor up to its sign)
+  for (int k = 0; k < c->nk && !e; ++k)
+    e = embed_plain_batched(c->G_tau + (size_t)(c->ntau - 1) * gstep + (size_t)k * n2, c->ntau, -gstep, c->nao, c->nao,
+                            c->Gp_hi + (size_t)k * c->ntau * per, c->Gp_lo + (size_t)k * c->ntau * per, c->kpadA, per,
+                            c->st);
   count(c->nk);
   return e;
 }
@@ -307,12 +316,15 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     c->Pchi = (float*)need(A(pb)); c->Pclo = (float*)need(A(pb));
     c->zbytes = zb;
     if (nao <= 64) {
-      if (kTensorSmallSteps) {   // nao-sized steps on tensor cores (off: the batched SIMT kernel is faster)
+      const bool small_tc = (cfg->flags & GW_SMALL_TENSOR) ? true : (cfg->flags & GW_SMALL_SIMT) ? false
+                                                                                                 : kTensorSmallSteps;
+      if (small_tc) {   // nao-sized steps on tensor cores
         c->kpadA = (2 * (int64_t)nao + 31) / 32 * 32;
         const size_t vs = (size_t)naux * nao * c->kpadA * 4, ge = (size_t)nk * ntau * 2 * nao * c->kpadA * 4;
         const size_t xs = (size_t)ntau * naux * nao * c->kpadA * 4;
         c->Vs_hi = (float*)need(A(vs)); c->Vs_lo = (float*)need(A(vs));
         c->Ge_hi = (float*)need(A(ge)); c->Ge_lo = (float*)need(A(ge));
+        c->Gp_hi = (float*)need(A(ge)); c->Gp_lo = (float*)need(A(ge));
         c->Xs_hi = (float*)need(A(xs)); c->Xs_lo = (float*)need(A(xs));
       }
       c->kpad3 = (2 * (int64_t)naux * nao + 31) / 32 * 32;
@@ -569,25 +581,32 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
       const char* Vkq = (const char*)Vp + ((size_t)k * nk + kq) * slab * es;
       const char* Gm = (const char*)Gp + ((size_t)(ntau - 1) * gstep + (size_t)k * n2) * es;
       if (tca) {
-        // Y[t][(Q,d)][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b] on tensor cores (G Hermitian)
+        // Y[t][Q][d][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b] on tensor cores (G Hermitian), written
+        // transposed per Q as TF32 hi/lo rows (t, Q, b) of (d, re/im): the A operand of the next step
         const int64_t ka = c->kpadA, per = 2 * (int64_t)nao * ka;
         CK(split_rows((const char*)c->V + ((size_t)k * nk + kq) * slab * 16, true, (int64_t)naux * nao, nao, nao, false,
                       c->Vs_hi, c->Vs_lo, ka, c->st));
+        count(1);
         UmmaOperand oa{c->Vs_hi, c->Vs_lo, (int64_t)naux * nao, 1, ka, 0};
         UmmaOperand ob{c->Ge_hi + (size_t)kq * ntau * per, c->Ge_lo + (size_t)kq * ntau * per, 2 * (int64_t)nao, ntau, ka,
                        per};
-        CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, oa, ob, naux * nao, 2 * nao, ka, ntau, c->chA, false, 1.0,
-                    false, 2 * (int64_t)nao, 2 * slab));
-        count(1);
-      }
-      if (f32 && nao <= 64) {
+        CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, oa, ob, naux * nao, 2 * nao, ka, ntau, c->Xs_hi, false, 1.0,
+                    false, 2, (int64_t)naux * nao * ka, 1, nao, (int64_t)nao * ka, 2, ka, c->Xs_lo));
+        // Z[t][Q][c][b] = -sum_d G^k(t_{ntau-1-j})[c][d] Y[t][Q][d][b] as rows (t, Q, b) of (c, re/im),
+        // written into the (c, b) layout of the last step's A operand
+        UmmaOperand ya{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka};
+        UmmaOperand gb{c->Gp_hi + (size_t)k * ntau * per, c->Gp_lo + (size_t)k * ntau * per, 2 * (int64_t)nao, ntau, ka,
+                       per};
+        CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, ya, gb, naux * nao, 2 * nao, ka, ntau, c->Zhi, false, -1.0,
+                    false, 2, (int64_t)naux * c->kpadP, 1, nao, c->kpadP, 2, 2 * (int64_t)nao, c->Zlo));
+      } else if (f32 && nao <= 64) {
         // Y[t][Q][d][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b]   (G shared per t)
         BsmDesc b1{};
         b1.M = b1.N = b1.K = nao; b1.G = ntau; b1.E = naux; b1.alpha = 1.f;
         b1.A = (const float2*)Vkq; b1.a_gs = 0; b1.a_es = n2; b1.a_rs = nao; b1.a_cs = 1;
         b1.B = (const float2*)Gp + (size_t)kq * n2; b1.b_gs = gstep; b1.b_rs = nao; b1.b_cs = 1; b1.b_shared = 1;
         b1.C = (float2*)c->chA; b1.c_gs = slab; b1.c_es = n2; b1.c_rs = nao;
-        if (!tca) CK(run_bsm(c, b1));
+        CK(run_bsm(c, b1));
         // Z[t][Q][c][b] = -sum_d G^k(t_{ntau-1-j})[c][d] Y[t][Q][d][b]   (G^k(-t) shared per t)
         BsmDesc b2{};
         b2.M = b2.N = b2.K = nao; b2.G = ntau; b2.E = naux; b2.alpha = -1.f;

@@ -133,5 +133,7 @@ cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float*
                     cudaStream_t st);
 cudaError_t embed_conj_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
                                float* lo, int64_t Kpad, int64_t ds, cudaStream_t st);
+cudaError_t embed_plain_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
+                                float* lo, int64_t Kpad, int64_t ds, cudaStream_t st);
 
 }  // namespace gwk

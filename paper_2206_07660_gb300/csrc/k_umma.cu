@@ -37,7 +37,7 @@ constexpr int UM_STAGES = 3;          // 3 stages x 2 resident blocks per SM
 constexpr int UM_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr uint32_t UM_SPIN_LIMIT = 1u << 26;
 constexpr int UM_FLUSH = 4;       // k-blocks per tensor-pipe accumulation chunk
-static int g_persistent = 0;      // 1: persistent tile loop (umma_pkernel); 0: one tile per block
+static int g_persistent = 1;      // 1: persistent tile loop (umma_pkernel); 0: one tile per block
 
 struct UmmaArgs {
   int M, N;            // real output rows / columns
@@ -288,57 +288,125 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
 
 // ------------------------------------------------------------------ persistent variant
 // One block per SM walks a static list of output tiles (n fastest, so blocks
-// running together share A tiles in L2).  Stage and chunk counters continue
-// across tiles; four TMEM chunk buffers let the MMA thread run up to three
-// chunks ahead of the epilogue, whose write-out of tile t overlaps the main
-// loop of tile t+1.  The write-out goes through a 32 x 33 staging tile per
-// epilogue warp (coalesced rows).
-constexpr int UP_STAGES = 6;
-constexpr int UP_TBUF = 4;
+// running together share A tiles in L2).  Stage counters continue across
+// tiles, so the next tile starts loading while the previous one is still being
+// multiplied.  Two epilogue warpgroups take the tiles in turn ("ping-pong"):
+// while one drains and writes out tile i, the MMA thread already accumulates
+// tile i+1 into the other group's TMEM buffers.  Each group has two chunk
+// buffers of BN columns (4 x BN <= 512 TMEM columns).  The write-out goes
+// through a 32 x 33 staging tile per epilogue warp (coalesced rows).
+constexpr int UP_STAGES = 5;
+constexpr int UP_THREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2..5 group 0, warps 6..9 group 1
 
-__device__ __forceinline__ void umma_store(const UmmaArgs& a, int z, int row, int n, float acc) {
-  const int64_t ro = row / a.row_inner, ri = row - ro * a.row_inner;
-  const int64_t base = (int64_t)z * a.c_zs + ro * a.row_s1 + ri * a.c_ld;
+// Writes one 32 x 32 block of a finished tile: lane l holds the row sums of
+// output row r0 + l in stg[l * 33 + j] (j = column - c0).  Rows are written
+// one at a time with the 32 lanes along the columns; the old values of an
+// accumulating output are loaded for 16 rows at a time before their stores so
+// that the load latencies overlap.
+__device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r0, int n0, int ncol,
+                                                 const float* stg, int lane) {
+  // per-row base offsets (one division per lane), broadcast below
+  int64_t myoff = 0;
+  {
+    const int row = r0 + lane;
+    const int64_t ro = row / a.row_inner, ri = row - ro * a.row_inner;
+    myoff = (int64_t)z * a.c_zs + ro * a.row_s1 + ri * a.c_ld;
+  }
+  const int n = n0 + lane;
+  const bool colok = lane < ncol && n < a.N;
+  const int nrow = a.M - r0 < 32 ? a.M - r0 : 32;
   if (a.c_fp64) {
-    double* C = (double*)a.C + base;
-    const double v = a.alpha * (double)acc;
-    if (a.ksplit > 1) atomicAdd(C + n, v);
-    else C[n] = a.accumulate ? C[n] + v : v;
-  } else {
-    const int64_t co = n / a.col_inner, ci = n - co * a.col_inner;
-    const int64_t off = base + co * a.col_s1 + ci;
-    const float v = (float)a.alpha * acc;
-    float* C = (float*)a.C;
-    if (a.C_lo) {
-      const float h = tf32_rna_dev(v);
-      C[off] = h;
-      a.C_lo[off] = tf32_rna_dev(v - h);
+    double* C = (double*)a.C;
+    const double al = a.alpha;
+    if (a.ksplit > 1) {
+      for (int r = 0; r < 32; ++r) {
+        const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+        if (r < nrow && colok) atomicAdd(C + base + n, al * (double)stg[r * 33 + lane]);
+      }
+    } else if (a.accumulate) {
+      for (int h = 0; h < 32; h += 16) {
+        double old[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int64_t base = __shfl_sync(0xffffffffu, myoff, h + r);
+          old[r] = (h + r < nrow && colok) ? C[base + n] : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int64_t base = __shfl_sync(0xffffffffu, myoff, h + r);
+          if (h + r < nrow && colok) C[base + n] = old[r] + al * (double)stg[(h + r) * 33 + lane];
+        }
+      }
     } else {
-      C[off] = a.accumulate ? C[off] + v : v;
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+        if (r < nrow && colok) C[base + n] = al * (double)stg[r * 33 + lane];
+      }
+    }
+  } else {
+    int64_t coff = 0;
+    if (colok) {
+      const int64_t co = n / a.col_inner, ci = n - co * a.col_inner;
+      coff = co * a.col_s1 + ci;
+    }
+    float* C = (float*)a.C;
+    const float al = (float)a.alpha;
+    if (a.C_lo) {
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+        if (r < nrow && colok) {
+          const float v = al * stg[r * 33 + lane];
+          const float h = tf32_rna_dev(v);
+          C[base + coff] = h;
+          a.C_lo[base + coff] = tf32_rna_dev(v - h);
+        }
+      }
+    } else if (a.accumulate) {
+      for (int h = 0; h < 32; h += 16) {
+        float old[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int64_t base = __shfl_sync(0xffffffffu, myoff, h + r);
+          old[r] = (h + r < nrow && colok) ? C[base + coff] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int64_t base = __shfl_sync(0xffffffffu, myoff, h + r);
+          if (h + r < nrow && colok) C[base + coff] = old[r] + al * stg[(h + r) * 33 + lane];
+        }
+      }
+    } else {
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+        if (r < nrow && colok) C[base + coff] = al * stg[r * 33 + lane];
+      }
     }
   }
 }
 
 template <int BN>
-__global__ void __launch_bounds__(UM_THREADS, 1)
+__global__ void __launch_bounds__(UP_THREADS, 1)
     umma_pkernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                  const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, UmmaArgs a,
                  int ntn, int ntm, int ntiles) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "N tile");
   constexpr uint32_t A_BYTES = UM_BM * UM_BK * 4;
   constexpr uint32_t B_BYTES = BN * UM_BK * 4;
-  constexpr uint32_t NEED = UP_TBUF * BN;
+  constexpr uint32_t NEED = 4 * BN;   // 2 groups x 2 chunk buffers
   constexpr uint32_t TMEM_COLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + UP_STAGES * A_BYTES;
-  float* stage_all = (float*)(sB + UP_STAGES * B_BYTES);          // 4 warps x 32 x 33 floats
-  uint64_t* full = (uint64_t*)(stage_all + 4 * 32 * 33);
+  float* stage_all = (float*)(sB + UP_STAGES * B_BYTES);          // 8 warps x 32 x 33 floats
+  uint64_t* full = (uint64_t*)(stage_all + 8 * 32 * 33);
   uint64_t* empty = full + UP_STAGES;
-  uint64_t* accf = empty + UP_STAGES;
-  uint64_t* acce = accf + UP_TBUF;
-  uint32_t* tmem_slot = (uint32_t*)(acce + UP_TBUF);
+  uint64_t* accf = empty + UP_STAGES;   // [group][buffer]: chunk in TMEM is complete
+  uint64_t* acce = accf + 4;            // [group][buffer]: chunk drained by the group's 4 warps
+  uint32_t* tmem_slot = (uint32_t*)(acce + 4);
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -347,7 +415,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int s = 0; s < UP_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < UP_TBUF; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
+    for (int b = 0; b < 4; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -360,7 +428,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  // tile t -> (n tile, m tile, batch*split)
+  // tile t -> (n tile, m tile, batch entry z, k range)
   auto decode = [&](int t, int& n0, int& m0, int& z, int& kb0, int& nkb) {
     const int tn = t % ntn, r = t / ntn, tm = r % ntm, zz = r / ntm;
     z = zz / a.ksplit;
@@ -382,12 +450,12 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
         const int total = a.nseg * nkb;
         bool ok = true;
         for (int it = 0; it < total; ++it, ++g) {
-          const int s = g % UP_STAGES;
+          const int s = (int)(g % UP_STAGES);
           const uint32_t ph = (g / UP_STAGES) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); ok = false; break; }
           const int seg = it / nkb, kb = kb0 + (it - seg * nkb);
-          const CUtensorMap* ma = (seg == 2) ? &tA1 : &tA0;
-          const CUtensorMap* mb = (seg == 1) ? &tB1 : &tB0;
+          const CUtensorMap* ma = (seg == 2) ? &tA1 : &tA0;   // A_hi, A_hi, A_lo
+          const CUtensorMap* mb = (seg == 1) ? &tB1 : &tB0;   // B_hi, B_lo, B_hi
           mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
           tma_load_3d(sA + s * A_BYTES, ma, &full[s], kb * UM_BK, m0, za);
           tma_load_3d(sB + s * B_BYTES, mb, &full[s], kb * UM_BK, n0, zb);
@@ -397,44 +465,51 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      // instruction descriptor: D fp32, A/B tf32, both K-major, N = BN, M = 128
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                              ((uint32_t)(UM_BM >> 4) << 24);
-      uint32_t g = 0, cg = 0;   // global k-iteration and chunk counters
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      uint32_t g = 0;
+      uint32_t cg[2] = {0u, 0u};   // chunks issued so far into each group's buffers
+      int li = 0;                  // local tile index: group = li & 1
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++li) {
         if (*(volatile int*)&s_fail) break;
         int n0, m0, z, kb0, nkb;
         decode(t, n0, m0, z, kb0, nkb);
+        const int grp = li & 1;
         const int total = a.nseg * nkb;
         bool ok = true;
         for (int it = 0; it < total; ++it, ++g) {
-          const int s = g % UP_STAGES;
+          const int s = (int)(g % UP_STAGES);
           const uint32_t ph = (g / UP_STAGES) & 1u;
-          const uint32_t chunk = cg + (uint32_t)(it / UM_FLUSH);
-          const int b = chunk % UP_TBUF;
-          const uint32_t u = chunk / UP_TBUF;
+          const uint32_t chunk = cg[grp] + (uint32_t)(it / UM_FLUSH);
+          const int b = (int)(chunk & 1u);
+          const uint32_t u = chunk >> 1;   // use count of this buffer
           const bool chunk_first = (it % UM_FLUSH) == 0;
           if (chunk_first && u >= 1) {
-            if (!mbar_wait(&acce[b], (u - 1) & 1u)) { atomicCAS(&s_fail, 0, 4); ok = false; break; }
+            if (!mbar_wait(&acce[grp * 2 + b], (u - 1) & 1u)) { atomicCAS(&s_fail, 0, 4); ok = false; break; }
           }
           if (!mbar_wait(&full[s], ph)) { atomicCAS(&s_fail, 0, 2); ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t d = tmem + (uint32_t)(b * BN);
+          const uint32_t d = tmem + (uint32_t)((grp * 2 + b) * BN);
           const uint64_t ad = sw128_desc(sA + s * A_BYTES), bd = sw128_desc(sB + s * B_BYTES);
 #pragma unroll
           for (int kk = 0; kk < UM_BK / 8; ++kk)
             umma_tf32(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (!chunk_first || kk > 0) ? 1u : 0u);
           umma_commit(&empty[s]);
-          if ((it % UM_FLUSH) == UM_FLUSH - 1 || it == total - 1) umma_commit(&accf[b]);
+          if ((it % UM_FLUSH) == UM_FLUSH - 1 || it == total - 1) umma_commit(&accf[grp * 2 + b]);
         }
         if (!ok) break;
-        cg += (uint32_t)((total + UM_FLUSH - 1) / UM_FLUSH);
+        cg[grp] += (uint32_t)((total + UM_FLUSH - 1) / UM_FLUSH);
       }
     }
   } else {
-    const int quarter = warp & 3;
+    // epilogue group grp = 0 (warps 2..5) or 1 (warps 6..9) takes local tiles grp, grp+2, ...
+    const int grp = (warp - 2) >> 2;
+    const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31 = tile rows
     float* stg = stage_all + (warp - 2) * 32 * 33;
     uint32_t cg = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int li = grp;
+    for (int t = blockIdx.x + grp * gridDim.x; t < ntiles; t += 2 * gridDim.x, li += 2) {
       if (*(volatile int*)&s_fail) break;
       int n0, m0, z, kb0, nkb;
       decode(t, n0, m0, z, kb0, nkb);
@@ -446,42 +521,49 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       bool ok = true;
       for (int c = 0; c < nch; ++c) {
         const uint32_t chunk = cg + (uint32_t)c;
-        const int b = chunk % UP_TBUF;
-        const uint32_t u = chunk / UP_TBUF;
-        if (!mbar_wait(&accf[b], u & 1u)) { atomicCAS(&s_fail, 0, 3); ok = false; break; }
+        const int b = (int)(chunk & 1u);
+        const uint32_t u = chunk >> 1;
+        if (!mbar_wait(&accf[grp * 2 + b], u & 1u)) { atomicCAS(&s_fail, 0, 3); ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // GRP columns in flight per wait (fewer load round trips; bounded by registers)
+        constexpr int GRP = BN > 80 ? 32 : 64;
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          uint32_t r[16];
-          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-              : "r"(taddr));
+        for (int c0 = 0; c0 < BN; c0 += GRP) {
+          uint32_t r[GRP];
+#pragma unroll
+          for (int q = 0; q < GRP; q += 16) {
+            if (c0 + q < BN) {
+              const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((grp * 2 + b) * BN + c0 + q);
+              asm volatile(
+                  "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                  : "=r"(r[q + 0]), "=r"(r[q + 1]), "=r"(r[q + 2]), "=r"(r[q + 3]), "=r"(r[q + 4]), "=r"(r[q + 5]),
+                    "=r"(r[q + 6]), "=r"(r[q + 7]), "=r"(r[q + 8]), "=r"(r[q + 9]), "=r"(r[q + 10]), "=r"(r[q + 11]),
+                    "=r"(r[q + 12]), "=r"(r[q + 13]), "=r"(r[q + 14]), "=r"(r[q + 15])
+                  : "r"(taddr));
+            }
+          }
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+          for (int j = 0; j < GRP; ++j)
+            if (c0 + j < BN) acc[c0 + j] += __uint_as_float(r[j]);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[grp * 2 + b])) : "memory");
       }
       if (!ok) break;
       cg += (uint32_t)nch;
       if (total == 0) continue;
-      // write-out: 32 x 32 blocks through the staging tile, one row per lane-sweep
+      // write-out: 32 x 32 blocks through the staging tile
+      if (m0 + quarter * 32 >= a.M) continue;
 #pragma unroll
       for (int cb = 0; cb < BN; cb += 32) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if (cb + j < BN) stg[lane * 33 + j] = acc[cb + j];
         __syncwarp();
-        for (int r = 0; r < 32; ++r) {
-          const int row = m0 + quarter * 32 + r;
-          const int col = cb + lane, n = n0 + col;
-          if (row < a.M && col < BN && n < a.N) umma_store(a, z, row, n, stg[r * 33 + lane]);
-        }
+        umma_write_block(a, z, m0 + quarter * 32, n0 + cb, BN - cb, stg, lane);
         __syncwarp();
       }
     }
@@ -532,8 +614,8 @@ static size_t umma_smem() {
 
 template <int BN>
 static size_t umma_psmem() {
-  return 1024 + (size_t)UP_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + 4 * 32 * 33 * 4 +
-         (2 * UP_STAGES + 2 * UP_TBUF) * 8 + 16;
+  return 1024 + (size_t)UP_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + 8 * 32 * 33 * 4 +
+         (2 * UP_STAGES + 8) * 8 + 16;
 }
 
 static int g_num_sms = 0;
@@ -554,7 +636,7 @@ static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch,
     const int64_t ntiles = (int64_t)ntn * ntm * batch * a.ksplit;
     if (ntiles > INT32_MAX) return cudaErrorInvalidValue;
     const int grid = (int)(ntiles < g_num_sms ? ntiles : g_num_sms);
-    umma_pkernel<BN><<<grid, UM_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a, ntn, ntm, (int)ntiles);
+    umma_pkernel<BN><<<grid, UP_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a, ntn, ntm, (int)ntiles);
     return cudaGetLastError();
   }
   size_t sm = umma_smem<BN>();
@@ -684,6 +766,27 @@ __global__ void embed_conj_batched_kernel(const double2* __restrict__ src, int64
   }
 }
 
+// Batched doubled operand of C = A B^T with B[n][k] = src[z][n][k] taken as is:
+// rows 2n = (re, -im), rows 2n+1 = (im, re).  Matrix z is read at src + z*ss
+// (complex elements; ss may be negative to walk a tau axis backwards).
+__global__ void embed_plain_batched_kernel(const double2* __restrict__ src, int64_t count, int64_t ss, int64_t rows,
+                                           int64_t K, float* hi, float* lo, int64_t Kpad, int64_t ds) {
+  const int64_t per = 2 * rows * Kpad, tot = per * count;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t z = e / per, r = e - z * per, r2 = r / Kpad, c = r - r2 * Kpad, n = r2 >> 1;
+    double v = 0.0;
+    if (c < 2 * K) {
+      const double2 x = src[z * ss + n * K + (c >> 1)];
+      if ((r2 & 1) == 0) v = (c & 1) ? -x.y : x.x;
+      else v = (c & 1) ? x.x : x.y;
+    }
+    float h, l;
+    split2(v, h, l);
+    hi[z * ds + r] = h;
+    lo[z * ds + r] = l;
+  }
+}
+
 // Doubled operand of C = A B^T where B[n][k] = src[k][n] (src: K rows of N complex):
 // rows 2n = (re, -im), rows 2n+1 = (im, re), transposed through shared memory.
 template <typename T>
@@ -744,6 +847,12 @@ cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, 
 cudaError_t embed_conj_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
                                float* lo, int64_t Kpad, int64_t ds, cudaStream_t st) {
   embed_conj_batched_kernel<<<nb_(2 * rows * Kpad * count), 256, 0, st>>>(src, count, ss, rows, K, hi, lo, Kpad, ds);
+  return cudaGetLastError();
+}
+
+cudaError_t embed_plain_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
+                                float* lo, int64_t Kpad, int64_t ds, cudaStream_t st) {
+  embed_plain_batched_kernel<<<nb_(2 * rows * Kpad * count), 256, 0, st>>>(src, count, ss, rows, K, hi, lo, Kpad, ds);
   return cudaGetLastError();
 }
 

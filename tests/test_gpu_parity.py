@@ -148,12 +148,12 @@ def test_single_orbital_closed_form():
     assert abs(g.get("Sigma_inf_new")[0, 0, 0] - (cl["J"] + cl["K"])) < 1e-13
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split_tf32"])
-def test_lowp_contractions_c1(precision):
+@pytest.mark.parametrize("precision,small", [("fp32", "auto"), ("split_tf32", "simt"), ("split_tf32", "tensor")])
+def test_lowp_contractions_c1(precision, small):
     # complex64 SIMT products, or split-TF32 tensor-core products, against the
     # fp64 oracle: errors stay at the 1e-5 Ha level of fp32-class arithmetic
     sysd = make_config_system("C1")
-    g = gpu(sysd, precision=precision)
+    g = gpu(sysd, precision=precision, small_steps=small)
     st = oracle_state(sysd)
     g.iterate(1)
     st.iterate()
@@ -179,17 +179,17 @@ def test_rejects_bad_inputs():
         g.polarization()     # no G yet
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split_tf32"])
+@pytest.mark.parametrize("precision,small", [("fp32", "auto"), ("split_tf32", "simt"), ("split_tf32", "tensor")])
 @pytest.mark.parametrize("nao,naux,kmesh,ntau", [(5, 70, (3, 1, 1), 12), (13, 20, (2, 1, 1), 10),
                                                  (64, 9, (1, 1, 1), 6), (65, 6, (1, 1, 1), 4)])
-def test_lowp_stages(nao, naux, kmesh, ntau, precision):
+def test_lowp_stages(nao, naux, kmesh, ntau, precision, small):
     # ragged sizes (K = 2 nao^2 and 2 naux not multiples of the 32-wide tensor-core K
     # block; nao = 64 is the largest batched-small-product size, 65 takes the general kernel)
     sysd = system(nao, naux, kmesh, ntau, 60.0, 21)
     st, G = _perturbed_green(sysd, 6)
     nk = st.km.nk
     P = hermitian_noise((nk, ntau, naux, naux), 0.1, 9)
-    g = gpu(sysd, precision=precision)
+    g = gpu(sysd, precision=precision, small_steps=small)
     g.set("G_tau", G)
     g.polarization()
     P0 = ogw.polarization_tau(st.V, G, st.km)
