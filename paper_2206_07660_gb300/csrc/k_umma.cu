@@ -295,8 +295,22 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
 // tile i+1 into the other group's TMEM buffers.  Each group has two chunk
 // buffers of BN columns (4 x BN <= 512 TMEM columns).  The write-out goes
 // through a 32 x 33 staging tile per epilogue warp (coalesced rows).
-constexpr int UP_STAGES = 5;
 constexpr int UP_THREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2..5 group 0, warps 6..9 group 1
+// A stage holds one 32-wide k-block of A_hi, B_hi and (three products) A_lo, B_lo,
+// so each operand tile crosses L2 once for all three products.
+template <int BN>
+struct UpCfg {
+  static constexpr uint32_t A_BYTES = UM_BM * UM_BK * 4;
+  static constexpr uint32_t B_BYTES = BN * UM_BK * 4;
+  static constexpr uint32_t STAGE = 2 * (A_BYTES + B_BYTES);
+  static constexpr uint32_t STAGING = 8 * 32 * 33 * 4;
+  static constexpr int STAGES_FIT = (int)((232448u - 1024u - STAGING - 256u) / STAGE);
+  static constexpr int STAGES = STAGES_FIT > 4 ? 4 : STAGES_FIT;
+  static_assert(STAGES >= 2, "pipeline depth");
+};
+// k-blocks per tensor-pipe accumulation chunk in the persistent kernel: 12 MMAs
+// with three products, 16 with one (as in the one-tile-per-block kernel)
+__device__ __forceinline__ int up_chunk_len(int nseg) { return nseg == 3 ? 1 : UM_FLUSH; }
 
 // Writes one 32 x 32 block of a finished tile: lane l holds the row sums of
 // output row r0 + l in stg[l * 33 + j] (j = column - c0).  Rows are written
@@ -393,18 +407,19 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
                  const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, UmmaArgs a,
                  int ntn, int ntm, int ntiles) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "N tile");
-  constexpr uint32_t A_BYTES = UM_BM * UM_BK * 4;
-  constexpr uint32_t B_BYTES = BN * UM_BK * 4;
+  using Cf = UpCfg<BN>;
+  constexpr uint32_t A_BYTES = Cf::A_BYTES, B_BYTES = Cf::B_BYTES;
+  constexpr int NS = Cf::STAGES;
   constexpr uint32_t NEED = 4 * BN;   // 2 groups x 2 chunk buffers
   constexpr uint32_t TMEM_COLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + UP_STAGES * A_BYTES;
-  float* stage_all = (float*)(sB + UP_STAGES * B_BYTES);          // 8 warps x 32 x 33 floats
+  // stage s: [A_hi | A_lo | B_hi | B_lo], each tile 1024-byte aligned
+  uint8_t* sStage = smem;
+  float* stage_all = (float*)(sStage + NS * Cf::STAGE);          // 8 warps x 32 x 33 floats
   uint64_t* full = (uint64_t*)(stage_all + 8 * 32 * 33);
-  uint64_t* empty = full + UP_STAGES;
-  uint64_t* accf = empty + UP_STAGES;   // [group][buffer]: chunk in TMEM is complete
+  uint64_t* empty = full + NS;
+  uint64_t* accf = empty + NS;          // [group][buffer]: chunk in TMEM is complete
   uint64_t* acce = accf + 4;            // [group][buffer]: chunk drained by the group's 4 warps
   uint32_t* tmem_slot = (uint32_t*)(acce + 4);
   __shared__ int s_fail;
@@ -414,7 +429,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
 
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int s = 0; s < UP_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 4; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -447,18 +462,21 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         int n0, m0, z, kb0, nkb;
         decode(t, n0, m0, z, kb0, nkb);
         const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
-        const int total = a.nseg * nkb;
+        const bool three = a.nseg == 3;
         bool ok = true;
-        for (int it = 0; it < total; ++it, ++g) {
-          const int s = (int)(g % UP_STAGES);
-          const uint32_t ph = (g / UP_STAGES) & 1u;
+        for (int it = 0; it < nkb; ++it, ++g) {
+          const int s = (int)(g % NS);
+          const uint32_t ph = (g / NS) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); ok = false; break; }
-          const int seg = it / nkb, kb = kb0 + (it - seg * nkb);
-          const CUtensorMap* ma = (seg == 2) ? &tA1 : &tA0;   // A_hi, A_hi, A_lo
-          const CUtensorMap* mb = (seg == 1) ? &tB1 : &tB0;   // B_hi, B_lo, B_hi
-          mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-          tma_load_3d(sA + s * A_BYTES, ma, &full[s], kb * UM_BK, m0, za);
-          tma_load_3d(sB + s * B_BYTES, mb, &full[s], kb * UM_BK, n0, zb);
+          const int kb = kb0 + it;
+          uint8_t* st = sStage + s * Cf::STAGE;
+          mbar_expect_tx(&full[s], three ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES);
+          tma_load_3d(st, &tA0, &full[s], kb * UM_BK, m0, za);
+          tma_load_3d(st + 2 * A_BYTES, &tB0, &full[s], kb * UM_BK, n0, zb);
+          if (three) {
+            tma_load_3d(st + A_BYTES, &tA1, &full[s], kb * UM_BK, m0, za);
+            tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tB1, &full[s], kb * UM_BK, n0, zb);
+          }
         }
         if (!ok) break;
       }
@@ -476,30 +494,39 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         int n0, m0, z, kb0, nkb;
         decode(t, n0, m0, z, kb0, nkb);
         const int grp = li & 1;
-        const int total = a.nseg * nkb;
+        const bool three = a.nseg == 3;
+        const int CL = up_chunk_len(a.nseg);
         bool ok = true;
-        for (int it = 0; it < total; ++it, ++g) {
-          const int s = (int)(g % UP_STAGES);
-          const uint32_t ph = (g / UP_STAGES) & 1u;
-          const uint32_t chunk = cg[grp] + (uint32_t)(it / UM_FLUSH);
+        for (int it = 0; it < nkb; ++it, ++g) {
+          const int s = (int)(g % NS);
+          const uint32_t ph = (g / NS) & 1u;
+          const uint32_t chunk = cg[grp] + (uint32_t)(it / CL);
           const int b = (int)(chunk & 1u);
           const uint32_t u = chunk >> 1;   // use count of this buffer
-          const bool chunk_first = (it % UM_FLUSH) == 0;
+          const bool chunk_first = (it % CL) == 0;
           if (chunk_first && u >= 1) {
             if (!mbar_wait(&acce[grp * 2 + b], (u - 1) & 1u)) { atomicCAS(&s_fail, 0, 4); ok = false; break; }
           }
           if (!mbar_wait(&full[s], ph)) { atomicCAS(&s_fail, 0, 2); ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t d = tmem + (uint32_t)((grp * 2 + b) * BN);
-          const uint64_t ad = sw128_desc(sA + s * A_BYTES), bd = sw128_desc(sB + s * B_BYTES);
+          uint8_t* st = sStage + s * Cf::STAGE;
+          const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_BYTES);
+          const uint64_t bh = sw128_desc(st + 2 * A_BYTES), bl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < UM_BK / 8; ++kk)
-            umma_tf32(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (!chunk_first || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < UM_BK / 8; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 2);
+            umma_tf32(d, ah + o, bh + o, idesc, (!chunk_first || kk > 0) ? 1u : 0u);   // hi * hi
+            if (three) {
+              umma_tf32(d, ah + o, bl + o, idesc, 1u);                                   // hi * lo
+              umma_tf32(d, al + o, bh + o, idesc, 1u);                                   // lo * hi
+            }
+          }
           umma_commit(&empty[s]);
-          if ((it % UM_FLUSH) == UM_FLUSH - 1 || it == total - 1) umma_commit(&accf[grp * 2 + b]);
+          if ((it % CL) == CL - 1 || it == nkb - 1) umma_commit(&accf[grp * 2 + b]);
         }
         if (!ok) break;
-        cg[grp] += (uint32_t)((total + UM_FLUSH - 1) / UM_FLUSH);
+        cg[grp] += (uint32_t)((nkb + CL - 1) / CL);
       }
     }
   } else {
@@ -513,20 +540,21 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
       if (*(volatile int*)&s_fail) break;
       int n0, m0, z, kb0, nkb;
       decode(t, n0, m0, z, kb0, nkb);
-      const int total = a.nseg * nkb;
-      const int nch = (total + UM_FLUSH - 1) / UM_FLUSH;
+      const int CL = up_chunk_len(a.nseg);
+      const int nch = (nkb + CL - 1) / CL;
       float acc[BN];
 #pragma unroll
       for (int j = 0; j < BN; ++j) acc[j] = 0.f;
       bool ok = true;
+      int blast = 0;
       for (int c = 0; c < nch; ++c) {
         const uint32_t chunk = cg + (uint32_t)c;
         const int b = (int)(chunk & 1u);
         const uint32_t u = chunk >> 1;
         if (!mbar_wait(&accf[grp * 2 + b], u & 1u)) { atomicCAS(&s_fail, 0, 3); ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // GRP columns in flight per wait (fewer load round trips; bounded by registers)
-        constexpr int GRP = BN > 80 ? 32 : 64;
+        // GRP columns in flight per wait (fewer load round trips, within the register budget)
+        constexpr int GRP = BN >= 112 ? 16 : BN > 80 ? 32 : 64;
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += GRP) {
           uint32_t r[GRP];
@@ -547,25 +575,64 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           for (int j = 0; j < GRP; ++j)
             if (c0 + j < BN) acc[c0 + j] += __uint_as_float(r[j]);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0)
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[grp * 2 + b])) : "memory");
+        if (c + 1 < nch) {
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[grp * 2 + b])) : "memory");
+        } else {
+          blast = b;
+        }
       }
       if (!ok) break;
       cg += (uint32_t)nch;
-      if (total == 0) continue;
-      // write-out: 32 x 32 blocks through the staging tile
-      if (m0 + quarter * 32 >= a.M) continue;
+      if (nch == 0) continue;
+      // The finished row sums go back into the last chunk's TMEM buffer (released to
+      // the MMA thread only after the write-out below), so that the register sums
+      // are not live during the write-out.
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((grp * 2 + blast) * BN);
 #pragma unroll
-      for (int cb = 0; cb < BN; cb += 32) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (cb + j < BN) stg[lane * 33 + j] = acc[cb + j];
-        __syncwarp();
-        umma_write_block(a, z, m0 + quarter * 32, n0 + cb, BN - cb, stg, lane);
-        __syncwarp();
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+            ::"r"(tbase + (uint32_t)c0), "r"(__float_as_uint(acc[c0 + 0])), "r"(__float_as_uint(acc[c0 + 1])),
+              "r"(__float_as_uint(acc[c0 + 2])), "r"(__float_as_uint(acc[c0 + 3])), "r"(__float_as_uint(acc[c0 + 4])),
+              "r"(__float_as_uint(acc[c0 + 5])), "r"(__float_as_uint(acc[c0 + 6])), "r"(__float_as_uint(acc[c0 + 7])),
+              "r"(__float_as_uint(acc[c0 + 8])), "r"(__float_as_uint(acc[c0 + 9])), "r"(__float_as_uint(acc[c0 + 10])),
+              "r"(__float_as_uint(acc[c0 + 11])), "r"(__float_as_uint(acc[c0 + 12])), "r"(__float_as_uint(acc[c0 + 13])),
+              "r"(__float_as_uint(acc[c0 + 14])), "r"(__float_as_uint(acc[c0 + 15]))
+            : "memory");
       }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      // write-out: 32 x 32 blocks through the staging tile
+      if (m0 + quarter * 32 < a.M) {
+        for (int cb = 0; cb < BN; cb += 32) {
+          uint32_t v[32];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(tbase + (uint32_t)cb));
+          if (cb + 16 < BN) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+                  "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                  "=r"(v[30]), "=r"(v[31])
+                : "r"(tbase + (uint32_t)(cb + 16)));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
+          __syncwarp();
+          umma_write_block(a, z, m0 + quarter * 32, n0 + cb, BN - cb, stg, lane);
+          __syncwarp();
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[grp * 2 + blast])) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -614,8 +681,8 @@ static size_t umma_smem() {
 
 template <int BN>
 static size_t umma_psmem() {
-  return 1024 + (size_t)UP_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + 8 * 32 * 33 * 4 +
-         (2 * UP_STAGES + 8) * 8 + 16;
+  using Cf = UpCfg<BN>;
+  return 1024 + (size_t)Cf::STAGES * Cf::STAGE + Cf::STAGING + (2 * Cf::STAGES + 8) * 8 + 16;
 }
 
 static int g_num_sms = 0;
@@ -930,10 +997,12 @@ extern "C" int gwdbg_umma_bench(int M, int N, int Kpad, int batch, int c_fp64, i
   UmmaOperand oa{ah, ah, M, batch, Kpad, (int64_t)M * Kpad}, ob{bh, bh, N, 1, Kpad, 0};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0); cudaEventCreate(&e1);
-  cudaError_t e = umma_gemm(oa, ob, M, N, Kpad, batch, C, c_fp64, 1.0, true, N, (int64_t)M * N, 3, err, 0);
+  // fp64 output accumulates (C += A B^T, as the cross-slab sums do); fp32 output is stored
+  const bool acc = c_fp64 != 0;
+  cudaError_t e = umma_gemm(oa, ob, M, N, Kpad, batch, C, c_fp64, 1.0, acc, N, (int64_t)M * N, 3, err, 0);
   cudaEventRecord(e0, 0);
   for (int i = 0; i < iters && !e; ++i)
-    e = umma_gemm(oa, ob, M, N, Kpad, batch, C, c_fp64, 1.0, true, N, (int64_t)M * N, 3, err, 0);
+    e = umma_gemm(oa, ob, M, N, Kpad, batch, C, c_fp64, 1.0, acc, N, (int64_t)M * N, 3, err, 0);
   cudaEventRecord(e1, 0);
   if (!e) e = cudaEventSynchronize(e1);
   float t = 0.f;
