@@ -183,7 +183,8 @@ def device_V(sysd):
 def traffic_from_profiles(workload, precision):
     """Per-launch DRAM bytes of the contraction kernel from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2206_07660_gb300", "csrc", "k_gett.cu")
+    kern = "k_umma.cu" if precision == "split_tf32" else "k_gett.cu"
+    src = os.path.join(ROOT, "paper_2206_07660_gb300", "csrc", kern)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "contraction_%s_%s.md" % (workload, precision))
     if not os.path.exists(path):

@@ -83,10 +83,11 @@ struct gw_ctx {
 
 static thread_local std::string g_init_err;
 
-// The nao-sized chain steps (K = 2 nao) can run on the tensor-core GEMM, but with
-// one tile per block its fixed per-block cost dominates at these K (measured at
-// nao 52: ~3.8 ms per launch against ~2.2 ms for the batched SIMT kernel).
-static constexpr bool kTensorSmallSteps = false;   // GW_SMALL_TENSOR / GW_SMALL_SIMT override
+// The nao-sized chain steps (K = 2 nao) run on the tensor-core GEMM by default:
+// with the persistent kernel and lane-per-row stores of the transposed outputs they
+// beat the FP32 SIMT small-product kernel (C3 shapes with a 2x2x2 k-mesh: P~0 stage
+// 327 ms against 530 ms, Sigma~ 244 ms against 331 ms per iteration).
+static constexpr bool kTensorSmallSteps = true;   // GW_SMALL_TENSOR / GW_SMALL_SIMT override
 
 #define CK(x)                                                                        \
   do {                                                                               \

@@ -56,6 +56,7 @@ struct UmmaArgs {
   int64_t col_s1;
   float* C_lo;         // non-null: fp32 output split into TF32 hi (C) and lo (C_lo) planes
   int ksplit;          // K range split over blockIdx.z; partial results are added atomically
+  int direct;          // persistent kernel: transposed complex output stored lane-per-row (see umma_gemm)
   int* err;
 };
 
@@ -604,8 +605,55 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
             : "memory");
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      // write-out: 32 x 32 blocks through the staging tile
-      if (m0 + quarter * 32 < a.M) {
+      // write-out
+      const int row = m0 + quarter * 32 + lane;
+      if (a.direct && m0 + quarter * 32 < a.M) {
+        // complex output written transposed (real/imag column pairs land next to each
+        // other, rows 2 floats apart): each lane stores its own row, so a warp's
+        // float2 stores cover 256 contiguous bytes
+        int64_t myoff = 0;
+        {
+          const int64_t ro = row / a.row_inner, ri = row - ro * a.row_inner;
+          myoff = (int64_t)z * a.c_zs + ro * a.row_s1 + ri * a.c_ld;
+        }
+        const bool rok = row < a.M;
+        float* C = (float*)a.C;
+        const float al = (float)a.alpha;
+        for (int cb = 0; cb < BN; cb += 32) {
+          uint32_t v[32];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(tbase + (uint32_t)cb));
+          if (cb + 16 < BN) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+                  "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                  "=r"(v[30]), "=r"(v[31])
+                : "r"(tbase + (uint32_t)(cb + 16)));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (rok) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const int n = n0 + cb + j;
+              if (cb + j < BN && n < a.N) {
+                const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
+                const float re = al * __uint_as_float(v[j]), im = al * __uint_as_float(v[j + 1]);
+                if (a.C_lo) {
+                  const float hr = tf32_rna_dev(re), hi_ = tf32_rna_dev(im);
+                  *(float2*)(C + off) = make_float2(hr, hi_);
+                  *(float2*)(a.C_lo + off) = make_float2(tf32_rna_dev(re - hr), tf32_rna_dev(im - hi_));
+                } else {
+                  *(float2*)(C + off) = make_float2(re, im);
+                }
+              }
+            }
+          }
+        }
+      } else if (m0 + quarter * 32 < a.M) {
         for (int cb = 0; cb < BN; cb += 32) {
           uint32_t v[32];
           asm volatile(
@@ -748,6 +796,11 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   a.col_s1 = col_s1;
   a.C_lo = C_lo;
   if (C_lo && (c_fp64 || accumulate)) return cudaErrorInvalidValue;
+  // (re, im) column pairs of a complex output that land next to each other while
+  // consecutive rows are 2 floats apart: stored row by row from the tile lanes
+  a.direct = (!c_fp64 && !accumulate && col_inner == 2 && c_ld == 2 && (N % 2) == 0 && (c_zs % 2) == 0 &&
+              (a.row_s1 % 2) == 0 && (col_s1 % 2) == 0 && ((uintptr_t)C % 8) == 0 &&
+              ((uintptr_t)C_lo % 8) == 0) ? 1 : 0;
   a.err = err;
   switch (bn) {
     case 128: return launch_bn<128>(maps, a, batch, st);
