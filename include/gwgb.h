@@ -241,6 +241,28 @@ gw_status gw_polarization_vjp(gw_ctx* ctx, const double* Pbar, double* Gbar);
  * [nq][ntau][naux][naux] are overwritten.  Device pointers; fp64. */
 gw_status gw_selfenergy_vjp(gw_ctx* ctx, const double* Sbar, double* Gbar, double* Pbar);
 
+/* Tangent (Jacobian-vector product) of gw_polarization's P~0(tau) (Eq.
+ * tilde_P0_tau, symmetrised) along dG at the context's current G.  P~0 is a
+ * quadratic form in G, so dP~0 = P(dG(tau), G(-tau)) + P(G(tau), dG(-tau)).
+ * dG [ntau][nk][nao][nao] in, dP0 [nq][ntau][naux][naux] out (overwritten);
+ * device pointers; fp64 whatever contract_prec is.  Shares the adjoint chain
+ * buffers (allocated on first use). */
+gw_status gw_polarization_jvp(gw_ctx* ctx, const double* dG, double* dP0);
+
+/* Tangent of the screened block (Eqs. P0t_to_P0w, tilde_P_omega, Piw_to_Pt)
+ * along dP~0(tau): with X = (I - P~0(i Omega))^-1 = I + P~(i Omega) from the
+ * last gw_screened, dP~(i Omega) = X dP~0(i Omega) X, transformed back and
+ * symmetrised.  dP0_tau in, dP_tau out, both [nq][ntau][naux][naux] device
+ * pointers; fp64.  GW_ERR_STATE before gw_screened. */
+gw_status gw_screened_jvp(gw_ctx* ctx, const double* dP0_tau, double* dP_tau);
+
+/* Tangent of gw_selfenergy's Sigma~(tau) (Eq. tilde_sigma2, symmetrised) along
+ * (dG, dP~(tau)) at the context's current G and P~(tau): Sigma~ is bilinear,
+ * dSigma~ = S(dG, P~) + S(G, dP~).  dG [ntau][nk][nao][nao], dP_tau
+ * [nq][ntau][naux][naux] in; dS_tau [ntau][nk][nao][nao] out (overwritten);
+ * device pointers; fp64. */
+gw_status gw_selfenergy_jvp(gw_ctx* ctx, const double* dG, const double* dP_tau, double* dS_tau);
+
 /* Allocation-free screened solve: P = [I - P0]^{-1} P0 for `count` complex
  * n x n matrices (interleaved (re, im) doubles, row-major, contiguous), the
  * operation of gw_screened without a context.  The paper has no counterpart;

@@ -1029,6 +1029,8 @@ struct View {
 };
 cudaError_t polarization_vjp(const View& v, const double2* Pbar, double2* Gbar, int64_t* launches);
 cudaError_t selfenergy_vjp(const View& v, const double2* Sbar, double2* Gbar, double2* Pbar, int64_t* launches);
+cudaError_t polarization_jvp(const View& v, const double2* dG, double2* dP, int64_t* launches);
+cudaError_t selfenergy_jvp(const View& v, const double2* dG, const double2* dPt, double2* dS, int64_t* launches);
 }  // namespace gwadj
 
 static gw_status adj_view(gw_ctx* c, gwadj::View* v) {
@@ -1075,6 +1077,67 @@ extern "C" gw_status gw_selfenergy_vjp(gw_ctx* c, const double* Sbar, double* Gb
   CK(cudaMemsetAsync(Pbar, 0, (size_t)c->nk * c->ntau * c->na2 * 16, c->st));
   int64_t l = 0;
   CK(gwadj::selfenergy_vjp(v, (const double2*)Sbar, (double2*)Gbar, (double2*)Pbar, &l));
+  count((int)l);
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ tangents (A10)
+
+extern "C" gw_status gw_polarization_jvp(gw_ctx* c, const double* dG, double* dP0) {
+  if (!c || !dG || !dP0) return fail(c, GW_ERR_ARG, "null argument");
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  gwadj::View v;
+  gw_status s = adj_view(c, &v);
+  if (s != GW_OK) return s;
+  int64_t l = 0;
+  CK(gwadj::polarization_jvp(v, (const double2*)dG, (double2*)dP0, &l));
+  count((int)l);
+  return GW_OK;
+}
+
+// dP~(tau) from dP~0(tau) through Eqs. P0t_to_P0w, tilde_P_omega and Piw_to_Pt:
+// with X = (I - P~0(i Omega))^-1 = I + P~(i Omega), dP~(i Omega) = X dP~0(i Omega) X.
+extern "C" gw_status gw_screened_jvp(gw_ctx* c, const double* dP0_tau, double* dP_tau) {
+  if (!c || !dP0_tau || !dP_tau) return fail(c, GW_ERR_ARG, "null argument");
+  if (!c->have_P) return fail(c, GW_ERR_STATE, "no screened interaction yet");
+  gwadj::View v;
+  gw_status s = adj_view(c, &v);
+  if (s != GW_OK) return s;
+  const int naux = c->naux, ntau = c->ntau, nw = c->nw;
+  const int64_t na2 = c->na2;
+  for (int q = 0; q < c->nk; ++q) {
+    const double2* x = (const double2*)dP0_tau + (size_t)q * ntau * na2;
+    const double2* Pw = c->P_iw + (size_t)q * nw * na2;
+    // T1 = TFb dP~0(tau)
+    CK(transform(c, c->TFb, x, v.bufA, nw, na2, 1, 0, 0));
+    // T2 = T1 + P~ T1   (per Omega)
+    CK(cudaMemcpyAsync(v.bufB, v.bufA, (size_t)nw * na2 * 16, cudaMemcpyDeviceToDevice, c->st));
+    GettDesc d = base_desc(naux, naux, naux, nw);
+    d.am = I1(naux); d.ak = I1(1); d.az = I1(na2);
+    d.bk = I1(naux); d.bn = I1(1); d.bz = I1(na2);
+    d.cm = I1(naux); d.cn = I1(1); d.cz = I1(na2);
+    d.beta = make_double2(1, 0);
+    CK(run_gett(d, Pw, Ty::C128, v.bufA, Ty::C128, v.bufB, Ty::C128, Ty::C128, c));
+    // T3 = T2 + T2 P~
+    CK(cudaMemcpyAsync(v.bufA, v.bufB, (size_t)nw * na2 * 16, cudaMemcpyDeviceToDevice, c->st));
+    CK(run_gett(d, v.bufB, Ty::C128, Pw, Ty::C128, v.bufA, Ty::C128, Ty::C128, c));
+    // dP~(tau) = TBb T3
+    CK(transform(c, c->TBb, v.bufA, (double2*)dP_tau + (size_t)q * ntau * na2, ntau, na2, 1, 0, 0));
+  }
+  CK(herm_batched((double2*)dP_tau, naux, (int64_t)c->nk * ntau, na2, c->st));
+  count(1);
+  return GW_OK;
+}
+
+extern "C" gw_status gw_selfenergy_jvp(gw_ctx* c, const double* dG, const double* dP_tau, double* dS_tau) {
+  if (!c || !dG || !dP_tau || !dS_tau) return fail(c, GW_ERR_ARG, "null argument");
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  if (!c->have_P) return fail(c, GW_ERR_STATE, "no screened interaction yet");
+  gwadj::View v;
+  gw_status s = adj_view(c, &v);
+  if (s != GW_OK) return s;
+  int64_t l = 0;
+  CK(gwadj::selfenergy_jvp(v, (const double2*)dG, (const double2*)dP_tau, (double2*)dS_tau, &l));
   count((int)l);
   return GW_OK;
 }

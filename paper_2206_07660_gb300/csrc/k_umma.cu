@@ -29,6 +29,9 @@
 #include <cudaTypedefs.h>
 #include "gw_internal.cuh"
 
+#include <map>
+#include <mutex>
+
 namespace gwk {
 
 constexpr int UM_BM = 128;
@@ -762,6 +765,87 @@ static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch,
   return cudaGetLastError();
 }
 
+// Builds the tensor maps for an N tile of `bn` columns and launches.
+static cudaError_t umma_launch(int bn, const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int nseg,
+                               const UmmaArgs& a, int batch, cudaStream_t st) {
+  CUtensorMap maps[4];
+  if (!make_map(&maps[0], A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
+      !make_map(&maps[1], nseg > 1 ? A.lo : A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
+      !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn) ||
+      !make_map(&maps[3], nseg > 1 ? B.lo : B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn))
+    return cudaErrorInvalidValue;
+  switch (bn) {
+    case 128: return launch_bn<128>(maps, a, batch, st);
+    case 112: return launch_bn<112>(maps, a, batch, st);
+    case 96: return launch_bn<96>(maps, a, batch, st);
+    case 80: return launch_bn<80>(maps, a, batch, st);
+    case 64: return launch_bn<64>(maps, a, batch, st);
+    case 48: return launch_bn<48>(maps, a, batch, st);
+    default: return launch_bn<32>(maps, a, batch, st);
+  }
+}
+
+// ---- tile autotuner: the N tile of each GEMM shape is picked once per process by
+// timing every candidate on the call's own operands.  A candidate run either
+// writes the same values the real call writes (stored outputs) or adds
+// 0 * (A B^T) (accumulating outputs), so tuning leaves the result unchanged.
+// Calls made while the stream is being captured use the cached choice or the
+// cost model.
+struct TuneKey {
+  int M, N, batch, nseg, ksplit, flags;
+  int64_t Kpad;
+  bool operator<(const TuneKey& o) const {
+    if (M != o.M) return M < o.M;
+    if (N != o.N) return N < o.N;
+    if (Kpad != o.Kpad) return Kpad < o.Kpad;
+    if (batch != o.batch) return batch < o.batch;
+    if (nseg != o.nseg) return nseg < o.nseg;
+    if (ksplit != o.ksplit) return ksplit < o.ksplit;
+    return flags < o.flags;
+  }
+};
+static std::map<TuneKey, int> g_tuned;
+static std::mutex g_tune_mu;
+static int g_autotune = 1;
+static const int kBnCand[] = {128, 112, 96, 80, 64, 48, 32};
+
+static int cost_model_bn(int N) {
+  // trade the padding of the last tile against the per-tile cost of re-reading
+  // the A tile (modelled as 32 extra columns per tile)
+  int bn = 128;
+  double best = -1.0;
+  for (int cand : kBnCand) {
+    const int64_t nt = (N + cand - 1) / cand;
+    const double eff = (double)N / (double)(nt * cand) * (double)cand / (double)(cand + 32);
+    if (eff > best + 1e-9) { best = eff; bn = cand; }
+  }
+  return bn;
+}
+
+static int tune_bn(const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int nseg, const UmmaArgs& a, int batch,
+                   cudaStream_t st, int fallback) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fallback;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fallback; }
+  UmmaArgs t = a;
+  if (t.accumulate) t.alpha = 0.0;
+  int best = fallback;
+  float best_ms = 1e30f;
+  for (int cand : kBnCand) {
+    if (umma_launch(cand, A, B, Kpad, nseg, t, batch, st) != cudaSuccess) continue;   // warm-up
+    cudaEventRecord(e0, st);
+    cudaError_t r = umma_launch(cand, A, B, Kpad, nseg, t, batch, st);
+    cudaEventRecord(e1, st);
+    if (r != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = cand; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1, int64_t col_inner,
@@ -770,21 +854,6 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   if (ksplit < 1) ksplit = 1;
   if (ksplit > 1 && (!c_fp64 || !accumulate)) return cudaErrorInvalidValue;   // split partials add atomically
   if ((int64_t)batch * ksplit > 65535) return cudaErrorInvalidValue;
-  CUtensorMap maps[4];
-  // N tile: trade the padding of the last tile against the per-tile cost of
-  // re-reading the A tile (modelled as 32 extra columns per tile)
-  int bn = 128;
-  double best = -1.0;
-  for (int cand : {128, 112, 96, 80, 64, 48, 32}) {
-    const int64_t nt = (N + cand - 1) / cand;
-    const double eff = (double)N / (double)(nt * cand) * (double)cand / (double)(cand + 32);
-    if (eff > best + 1e-9) { best = eff; bn = cand; }
-  }
-  if (!make_map(&maps[0], A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
-      !make_map(&maps[1], nseg > 1 ? A.lo : A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
-      !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn) ||
-      !make_map(&maps[3], nseg > 1 ? B.lo : B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn))
-    return cudaErrorInvalidValue;
   UmmaArgs a{};
   a.M = M; a.N = N; a.kblocks = (int)(Kpad / UM_BK); a.nseg = nseg;
   a.a_batched = A.batch > 1; a.b_batched = B.batch > 1;
@@ -802,15 +871,26 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
               (a.row_s1 % 2) == 0 && (col_s1 % 2) == 0 && ((uintptr_t)C % 8) == 0 &&
               ((uintptr_t)C_lo % 8) == 0) ? 1 : 0;
   a.err = err;
-  switch (bn) {
-    case 128: return launch_bn<128>(maps, a, batch, st);
-    case 112: return launch_bn<112>(maps, a, batch, st);
-    case 96: return launch_bn<96>(maps, a, batch, st);
-    case 80: return launch_bn<80>(maps, a, batch, st);
-    case 64: return launch_bn<64>(maps, a, batch, st);
-    case 48: return launch_bn<48>(maps, a, batch, st);
-    default: return launch_bn<32>(maps, a, batch, st);
+  int bn = cost_model_bn(N);
+  if (g_persistent && g_autotune) {
+    const TuneKey key{M, N, batch, nseg, ksplit,
+                      (c_fp64 ? 1 : 0) | (accumulate ? 2 : 0) | (a.direct ? 4 : 0) | (C_lo ? 8 : 0) |
+                          (a.a_batched ? 16 : 0) | (a.b_batched ? 32 : 0),
+                      Kpad};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      bn = it->second;
+    } else {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(st, &cs);
+      if (cs == cudaStreamCaptureStatusNone) {
+        bn = tune_bn(A, B, Kpad, nseg, a, batch, st, bn);
+        g_tuned[key] = bn;
+      }
+    }
   }
+  return umma_launch(bn, A, B, Kpad, nseg, a, batch, st);
 }
 
 // ------------------------------------------------------------------ operand preparation
@@ -990,6 +1070,24 @@ cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float*
 // Internal entry points for unit tests of the tensor-core GEMM (not part of the
 // public header).  All pointers are device pointers; the scratch is allocated
 // here with cudaMalloc.  Returns 0 on success, else a CUDA error or kernel code.
+
+// Turns the N-tile autotuner of the persistent kernel on (1, the default) or off
+// (0: cost model only); returns the previous setting.  Cached choices are kept.
+extern "C" int gwdbg_umma_set_autotune(int on) {
+  const int old = gwk::g_autotune;
+  gwk::g_autotune = on ? 1 : 0;
+  return old;
+}
+
+// Number of GEMM shapes tuned so far; the choice of entry i (in key order) in *bn.
+extern "C" int gwdbg_umma_tuned(int i, int* M, int* N, int* bn) {
+  std::lock_guard<std::mutex> lk(gwk::g_tune_mu);
+  int j = 0;
+  for (const auto& kv : gwk::g_tuned) {
+    if (j++ == i) { if (M) *M = kv.first.M; if (N) *N = kv.first.N; if (bn) *bn = kv.second; }
+  }
+  return (int)gwk::g_tuned.size();
+}
 
 // Selects the kernel variant used by every later tensor-core GEMM of this
 // process: 1 = persistent tile loop (the default), 0 = one output tile per block.

@@ -76,13 +76,17 @@ def load():
     lib.gw_batch_iterate.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32]
     lib.gw_polarization_vjp.argtypes = [P, P, P]
     lib.gw_selfenergy_vjp.argtypes = [P, P, P, P]
+    lib.gw_polarization_jvp.argtypes = [P, P, P]
+    lib.gw_screened_jvp.argtypes = [P, P, P]
+    lib.gw_selfenergy_jvp.argtypes = [P, P, P, P]
     lib.gw_profile.argtypes = [P, ctypes.c_int]
     lib.gw_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.gw_kernel_launches.argtypes = [P]
     lib.gw_kernel_launches.restype = ctypes.c_int64
     for name in ("gw_init", "gw_destroy", "gw_set", "gw_get", "gw_hf", "gw_polarization", "gw_screened",
                  "gw_selfenergy", "gw_dyson", "gw_iterate", "gw_reset_sigma", "gw_profile", "gw_profile_read",
-                 "gw_polarization_vjp", "gw_selfenergy_vjp", "gw_iterate_graph", "gw_batch_iterate"):
+                 "gw_polarization_vjp", "gw_selfenergy_vjp", "gw_iterate_graph", "gw_batch_iterate",
+                 "gw_polarization_jvp", "gw_screened_jvp", "gw_selfenergy_jvp"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -276,6 +280,30 @@ class GW:
         Pbar = torch.empty(self.shape_of("P_tau"), dtype=torch.complex128, device=Sbar.device)
         self._check(self.lib.gw_selfenergy_vjp(self.ctx, Sbar.data_ptr(), Gbar.data_ptr(), Pbar.data_ptr()))
         return Gbar, Pbar
+
+    def polarization_jvp(self, dG):
+        """dP~0(tau) = tangent of the symmetrised P~0(tau) along dG (device complex128)."""
+        torch = self.torch
+        dG = dG.contiguous()
+        dP = torch.empty(self.shape_of("P0_tau"), dtype=torch.complex128, device=dG.device)
+        self._check(self.lib.gw_polarization_jvp(self.ctx, dG.data_ptr(), dP.data_ptr()))
+        return dP
+
+    def screened_jvp(self, dP0):
+        """dP~(tau) = tangent of the screened block (transform, solve, transform back) along dP~0(tau)."""
+        torch = self.torch
+        dP0 = dP0.contiguous()
+        dP = torch.empty(self.shape_of("P_tau"), dtype=torch.complex128, device=dP0.device)
+        self._check(self.lib.gw_screened_jvp(self.ctx, dP0.data_ptr(), dP.data_ptr()))
+        return dP
+
+    def selfenergy_jvp(self, dG, dP):
+        """dSigma~(tau) = tangent of the symmetrised Sigma~(tau) along (dG, dP~(tau))."""
+        torch = self.torch
+        dG, dP = dG.contiguous(), dP.contiguous()
+        dS = torch.empty(self.shape_of("Sigma_tau"), dtype=torch.complex128, device=dG.device)
+        self._check(self.lib.gw_selfenergy_jvp(self.ctx, dG.data_ptr(), dP.data_ptr(), dS.data_ptr()))
+        return dS
 
     def profile(self, enable=True):
         self._check(self.lib.gw_profile(self.ctx, int(bool(enable))))

@@ -70,3 +70,41 @@ def test_split_tf32_gemm(persistent, M, N, K, conjB, nseg, ksplit):
     err = np.abs(C - ref).max() / scale
     tol = 3e-6 if nseg == 3 else 3e-3
     assert err < tol, err
+
+
+def test_autotuned_tiles_match_cost_model():
+    """The N-tile autotuner changes only the tiling: results agree with the
+    cost-model tile, and accumulating outputs are not disturbed by the trial runs."""
+    import torch
+    lib = _lib()
+    lib.gwdbg_umma_set_autotune.argtypes = [ctypes.c_int]
+    lib.gwdbg_umma_set_autotune.restype = ctypes.c_int
+    lib.gwdbg_umma_tuned.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    lib.gwdbg_umma_tuned.restype = ctypes.c_int
+    M, N, K = 700, 300, 400
+    rng = np.random.default_rng(77)
+    A = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K))
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    out = {}
+    for tune in (0, 1):
+        for ks in (1, 3):   # ks > 1: accumulating output (split K range)
+            old = lib.gwdbg_umma_set_autotune(tune)
+            dC = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+            try:
+                st = lib.gwdbg_umma_cgemm_split(dA.data_ptr(), dB.data_ptr(), M, N, K, 1, 3, ks, dC.data_ptr())
+            finally:
+                lib.gwdbg_umma_set_autotune(old)
+            assert st == 0
+            out[(tune, ks)] = dC.cpu().numpy()
+    ref = A @ np.conj(B).T
+    scale = np.sqrt(2.0 * K) * 2.0
+    for v in out.values():
+        assert np.abs(v - ref).max() / scale < 3e-6
+    assert np.abs(out[(1, 1)] - out[(0, 1)]).max() / scale < 1e-6
+    assert np.abs(out[(1, 3)] - out[(0, 3)]).max() / scale < 1e-6
+    n = lib.gwdbg_umma_tuned(0, None, None, None)
+    assert n >= 1
+    bn = ctypes.c_int()
+    lib.gwdbg_umma_tuned(0, None, None, ctypes.byref(bn))
+    assert bn.value in (32, 48, 64, 80, 96, 112, 128)
