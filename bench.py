@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--impl", default="gw", choices=["gw", "reference"])
     p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4"])
     p.add_argument("--precision", default="split_tf32", choices=["split_tf32", "fp32", "fp64"])
+    p.add_argument("--fp64-gemm", default="tensor", choices=["tensor", "native"],
+                   help="FP64 tau<->i nu transforms: digit-split tensor-core products or the FP64 SIMT kernel")
     p.add_argument("--small-steps", default="auto", choices=["auto", "tensor", "simt"],
                    help="placement of the nao-sized chain steps in the split_tf32 path")
     p.add_argument("--fp64-steps", type=int, default=1, help="timed fp64-path iterations for the comparison")
@@ -340,12 +342,12 @@ def run_gw(args):
         H0d, Sd = torch.from_numpy(sysd["H0"]).cuda(), torch.from_numpy(sysd["S"]).cuda()
         g = GW(H0d, Sd, Vd, sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"], sysd["bose_m"],
                n_elec=sysd["n_elec"], damping=0.5, precision=args.precision, borrow_V=True,
-               small_steps=args.small_steps)
+               small_steps=args.small_steps, fp64_gemm=args.fp64_gemm)
     else:
         Vd = None
         g = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
                sysd["bose_m"], n_elec=sysd["n_elec"], damping=0.5, precision=args.precision,
-               small_steps=args.small_steps)
+               small_steps=args.small_steps, fp64_gemm=args.fp64_gemm)
     g.dyson()
     G0 = g.get("G_tau")
     mu0 = g.get("mu")
@@ -485,7 +487,7 @@ def run_batch(args):
     from paper_2206_07660_gb300.gw import batch_iterate
     from synth import batch_configs, make_batch_system
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    prec = args.precision if args.precision != "split_tf32" else "fp32"
+    prec = args.precision
     cfgs = batch_configs()
     systems, gws = [], []
     for cfg in cfgs:
@@ -523,7 +525,8 @@ def run_batch(args):
     seq = time.perf_counter() - t0
     line = {"metric": METRIC, "value": dt, "unit": "s/batch-iteration (16 systems)", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "c64", "fp64": "c128"}[prec],
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "c64", "fp64": "c128", "split_tf32": "tf32x3/c64"}[prec],
             "data": "synthetic",
             "config": {"workload": "C4: 16 systems, nao in {8,12,16,26,40}, naux = 8 nao, k-meshes 2^3..4^3, "
                                    "ntau = nw = 64, beta = 100, %s contractions, captured graphs on per-system "

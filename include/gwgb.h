@@ -74,8 +74,11 @@ enum {
   GW_SKIP_CHECKS  = 1u << 2, /* skip the Hermiticity / pairing checks of gw_init  */
   GW_SMALL_TENSOR = 1u << 3, /* GW_SPLIT_TF32, nao <= 64: the nao-sized steps of the
                                 P~0 / Sigma~ chains also on tensor cores (split TF32)  */
-  GW_SMALL_SIMT   = 1u << 4  /* GW_SPLIT_TF32, nao <= 64: those steps on the FP32
+  GW_SMALL_SIMT   = 1u << 4, /* GW_SPLIT_TF32, nao <= 64: those steps on the FP32
                                 SIMT small-product kernel.  Neither flag: library default */
+  GW_FP64_NATIVE  = 1u << 5  /* tau <-> i nu transforms on the FP64 SIMT contraction
+                                kernel instead of FP64-accurate digit-split products on
+                                the tensor cores (the default)                        */
 };
 
 typedef void* (*gw_alloc_fn)(void* user, size_t bytes);
@@ -100,7 +103,7 @@ typedef struct {
   gw_free_fn dev_free;
   void* alloc_user;
   uint64_t flags;         /* GW_INPUT_DEVICE | GW_BORROW_V | GW_SKIP_CHECKS |
-                             GW_SMALL_TENSOR | GW_SMALL_SIMT                        */
+                             GW_SMALL_TENSOR | GW_SMALL_SIMT | GW_FP64_NATIVE       */
 } gw_config;
 
 /* Quantities readable with gw_get / writable with gw_set.  Sizes in bytes. */

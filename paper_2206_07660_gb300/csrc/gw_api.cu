@@ -30,6 +30,14 @@ struct gw_ctx {
   // grid
   double *tau = nullptr, *lb = nullptr, *l0 = nullptr, *wn = nullptr;
   double2 *TFf = nullptr, *TBf = nullptr, *TFb = nullptr, *TBb = nullptr, *r = nullptr;
+  // transforms on tensor cores by exact digit splitting: digits/exponents of TFf, TBf,
+  // TFb, TBb and the workspace for the transposed data operand
+  bool emul = false;
+  float* Tdig[4] = {nullptr, nullptr, nullptr, nullptr};
+  int* Texp[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* emA = nullptr;
+  int* emAe = nullptr;
+  size_t emA_bytes = 0;
   int *d_fn = nullptr, *d_bm = nullptr;
   // state
   double2 *G_tau = nullptr, *G_iw = nullptr, *G_prev = nullptr, *gamma = nullptr, *tQ = nullptr;
@@ -218,9 +226,24 @@ static GettDesc base_desc(int64_t M, int64_t N, int64_t K, int64_t Z) {
   return d;
 }
 
-// Y[z] = T (nrow x ntau) * X[z] (ntau x ncol): transforms along the tau axis.
+// Y[z] = T (nrow x ntau) * X[z] (ntau x ncol): transforms along the tau axis, FP64 either
+// way: digit-split products on the tensor cores (k_emul.cu) or the FP64 contraction kernel.
 static cudaError_t transform(gw_ctx* c, const double2* T, const double2* X, double2* Y, int64_t nrow, int64_t ncol,
                              int64_t batch, int64_t xstride, int64_t ystride) {
+  if (c->emul) {
+    const double2* Ts[4] = {c->TFf, c->TBf, c->TFb, c->TBb};
+    int idx = -1;
+    for (int i = 0; i < 4; ++i) if (Ts[i] == T) idx = i;
+    if (idx >= 0 && emul_digit_bytes(ncol, c->ntau) <= c->emA_bytes) {
+      for (int64_t z = 0; z < batch; ++z) {
+        cudaError_t e = emul_transform(c->Tdig[idx], c->Texp[idx], nrow, X + z * xstride, c->ntau, ncol, ncol,
+                                       Y + z * ystride, ncol, c->emA, c->emAe, c->info + 1, c->st);
+        if (e != cudaSuccess) return e;
+      }
+      count((int)(batch * 13));
+      return cudaSuccess;
+    }
+  }
   GettDesc d = base_desc(nrow, ncol, c->ntau, batch);
   d.am = I1(c->ntau); d.ak = I1(1);
   d.bk = I1(ncol); d.bn = I1(1); d.bz = I1(xstride);
@@ -290,6 +313,17 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   c->wn = (double*)need(A(ntau * 8));
   c->TFf = (double2*)need(A((size_t)ntau * ntau * cb)); c->TBf = (double2*)need(A((size_t)ntau * ntau * cb));
   c->TFb = (double2*)need(A((size_t)ntau * ntau * cb)); c->TBb = (double2*)need(A((size_t)ntau * ntau * cb));
+  c->emul = !(cfg->flags & GW_FP64_NATIVE);
+  if (c->emul) {
+    const int64_t ncmax = (int64_t)na2 > (int64_t)nk * n2 ? (int64_t)na2 : (int64_t)nk * n2;
+    c->emA_bytes = emul_digit_bytes(ncmax, ntau);
+    c->emA = (float*)need(A(c->emA_bytes));
+    c->emAe = (int*)need(A((size_t)ncmax * 4));
+    for (int i = 0; i < 4; ++i) {
+      c->Tdig[i] = (float*)need(A(emul_digit_bytes(2 * (int64_t)ntau, ntau)));
+      c->Texp[i] = (int*)need(A((size_t)ntau * 4));
+    }
+  }
   c->r = (double2*)need(A(ntau * cb));
   c->d_fn = (int*)need(A(ntau * 4)); c->d_bm = (int*)need(A(ntau * 4));
   const size_t gsz = (size_t)ntau * nk * n2 * cb;
@@ -395,6 +429,11 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   chk(invert_small_gj(c->TBf, ntau, c->info, st), "TBf");
   chk(invert_small_gj(c->TBb, ntau, c->info, st), "TBb");
   chk(density_weights(ntau, c->lb, c->TBf, c->r, st), "weights");
+  if (c->emul) {
+    chk(cudaMemsetAsync(c->emA, 0, c->emA_bytes, st), "memset");
+    const double2* Ts[4] = {c->TFf, c->TBf, c->TFb, c->TBb};
+    for (int i = 0; i < 4; ++i) chk(emul_split_b(Ts[i], ntau, ntau, ntau, c->Tdig[i], c->Texp[i], st), "digits");
+  }
   chk(fermi_freqs(ntau, cfg->beta, c->d_fn, c->wn, st), "freqs");
   count(4);
   if (lowp) { chk(to_c64(c->V, c->V32, vbytes / cb, st), "V32"); count(1); }

@@ -121,10 +121,26 @@ struct UmmaOperand {
 // o * row_inner + i is written at o * row_s1 + i * c_ld (real elements); col_inner
 // > 0: column n = o * col_inner + i at o * col_s1 + i.  C_lo != null: fp32 output
 // written as TF32 hi (C) / lo (C_lo) planes.
+// scale != null (fp64 output, persistent kernel only): D[m][n] is multiplied by
+// 2^(eA[z*ea_zs + m] + eB[z*eb_zs + n/2] + eshift) before it is added or stored.
+struct UmmaScale {
+  const int* eA;
+  const int* eB;
+  int64_t ea_zs, eb_zs;
+  int eshift;
+};
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
-                      int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr);
+                      int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr,
+                      const UmmaScale* scale = nullptr);
+// FP64 complex products on tensor cores by exact digit splitting (k_emul.cu)
+int64_t emul_kpad(int64_t K);
+size_t emul_digit_bytes(int64_t rows, int64_t K);
+cudaError_t emul_split_b(const double2* B, int64_t rows, int64_t K, int64_t ldb, float* dig, int* ex, cudaStream_t st);
+cudaError_t emul_transform(const float* Bd, const int* Be, int64_t nrow, const double2* X, int64_t K, int64_t ncol,
+                           int64_t ldx, double2* Y, int64_t ldy, float* Ad, int* Ae, int* err, cudaStream_t st);
+
 cudaError_t split_rows(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, float* hi,
                        float* lo, int64_t Kpad, cudaStream_t st);
 cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, float* hi, float* lo, int64_t Kpad,

@@ -60,6 +60,12 @@ struct UmmaArgs {
   float* C_lo;         // non-null: fp32 output split into TF32 hi (C) and lo (C_lo) planes
   int ksplit;          // K range split over blockIdx.z; partial results are added atomically
   int direct;          // persistent kernel: transposed complex output stored lane-per-row (see umma_gemm)
+  int chunk_len;       // persistent kernel: k-blocks accumulated in TMEM before the FP32 register sums
+  // fp64 output only: D[m][n] is scaled by 2^(eA[m] + eB[n/2] + eshift) (emulated FP64 products)
+  const int* eA;
+  const int* eB;
+  int64_t ea_zs, eb_zs;
+  int eshift;
   int* err;
 };
 
@@ -312,9 +318,11 @@ struct UpCfg {
   static constexpr int STAGES = STAGES_FIT > 4 ? 4 : STAGES_FIT;
   static_assert(STAGES >= 2, "pipeline depth");
 };
-// k-blocks per tensor-pipe accumulation chunk in the persistent kernel: 12 MMAs
-// with three products, 16 with one (as in the one-tile-per-block kernel)
-__device__ __forceinline__ int up_chunk_len(int nseg) { return nseg == 3 ? 1 : UM_FLUSH; }
+// k-blocks (stages) per tensor-pipe accumulation chunk in the persistent kernel
+// (UmmaArgs::chunk_len, set from g_chunk_len: 12 MMAs per stage with three products;
+// two stages measured 8% faster than one at the same 7e-7 relative error, four
+// stages 11% faster at 1.1e-6)
+static int g_chunk_len = 2;
 
 // Writes one 32 x 32 block of a finished tile: lane l holds the row sums of
 // output row r0 + l in stg[l * 33 + j] (j = column - c0).  Rows are written
@@ -335,11 +343,17 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
   const int nrow = a.M - r0 < 32 ? a.M - r0 : 32;
   if (a.c_fp64) {
     double* C = (double*)a.C;
-    const double al = a.alpha;
+    double al = a.alpha;
+    int myexp = 0;   // row exponent of row r0 + lane (scaled mode)
+    if (a.eA) {
+      if (lane < nrow) myexp = a.eA[(int64_t)z * a.ea_zs + r0 + lane];
+      if (colok) al = ldexp(al, a.eB[(int64_t)z * a.eb_zs + (n >> 1)] + a.eshift);
+    }
     if (a.ksplit > 1) {
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
-        if (r < nrow && colok) atomicAdd(C + base + n, al * (double)stg[r * 33 + lane]);
+        const int re_ = __shfl_sync(0xffffffffu, myexp, r);
+        if (r < nrow && colok) atomicAdd(C + base + n, ldexp(al * (double)stg[r * 33 + lane], re_));
       }
     } else if (a.accumulate) {
       for (int h = 0; h < 32; h += 16) {
@@ -352,14 +366,16 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
           const int64_t base = __shfl_sync(0xffffffffu, myoff, h + r);
-          if (h + r < nrow && colok) C[base + n] = old[r] + al * (double)stg[(h + r) * 33 + lane];
+          const int re_ = __shfl_sync(0xffffffffu, myexp, h + r);
+          if (h + r < nrow && colok) C[base + n] = old[r] + ldexp(al * (double)stg[(h + r) * 33 + lane], re_);
         }
       }
     } else {
 #pragma unroll 8
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
-        if (r < nrow && colok) C[base + n] = al * (double)stg[r * 33 + lane];
+        const int re_ = __shfl_sync(0xffffffffu, myexp, r);
+        if (r < nrow && colok) C[base + n] = ldexp(al * (double)stg[r * 33 + lane], re_);
       }
     }
   } else {
@@ -467,19 +483,31 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         decode(t, n0, m0, z, kb0, nkb);
         const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
         const bool three = a.nseg == 3;
+        // three products: one k-block per stage (hi and lo planes); one product: two k-blocks
+        const int nst = three ? nkb : (nkb + 1) / 2;
         bool ok = true;
-        for (int it = 0; it < nkb; ++it, ++g) {
+        for (int it = 0; it < nst; ++it, ++g) {
           const int s = (int)(g % NS);
           const uint32_t ph = (g / NS) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); ok = false; break; }
-          const int kb = kb0 + it;
           uint8_t* st = sStage + s * Cf::STAGE;
-          mbar_expect_tx(&full[s], three ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES);
-          tma_load_3d(st, &tA0, &full[s], kb * UM_BK, m0, za);
-          tma_load_3d(st + 2 * A_BYTES, &tB0, &full[s], kb * UM_BK, n0, zb);
           if (three) {
+            const int kb = kb0 + it;
+            mbar_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
+            tma_load_3d(st, &tA0, &full[s], kb * UM_BK, m0, za);
+            tma_load_3d(st + 2 * A_BYTES, &tB0, &full[s], kb * UM_BK, n0, zb);
             tma_load_3d(st + A_BYTES, &tA1, &full[s], kb * UM_BK, m0, za);
             tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tB1, &full[s], kb * UM_BK, n0, zb);
+          } else {
+            const int kb = kb0 + 2 * it;
+            const bool two = 2 * it + 1 < nkb;
+            mbar_expect_tx(&full[s], two ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES);
+            tma_load_3d(st, &tA0, &full[s], kb * UM_BK, m0, za);
+            tma_load_3d(st + 2 * A_BYTES, &tB0, &full[s], kb * UM_BK, n0, zb);
+            if (two) {
+              tma_load_3d(st + A_BYTES, &tA0, &full[s], (kb + 1) * UM_BK, m0, za);
+              tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tB0, &full[s], (kb + 1) * UM_BK, n0, zb);
+            }
           }
         }
         if (!ok) break;
@@ -499,9 +527,10 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         decode(t, n0, m0, z, kb0, nkb);
         const int grp = li & 1;
         const bool three = a.nseg == 3;
-        const int CL = up_chunk_len(a.nseg);
+        const int CL = a.chunk_len;
+        const int nst = three ? nkb : (nkb + 1) / 2;
         bool ok = true;
-        for (int it = 0; it < nkb; ++it, ++g) {
+        for (int it = 0; it < nst; ++it, ++g) {
           const int s = (int)(g % NS);
           const uint32_t ph = (g / NS) & 1u;
           const uint32_t chunk = cg[grp] + (uint32_t)(it / CL);
@@ -520,17 +549,24 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < UM_BK / 8; ++kk) {
             const uint64_t o = (uint64_t)(kk * 2);
-            umma_tf32(d, ah + o, bh + o, idesc, (!chunk_first || kk > 0) ? 1u : 0u);   // hi * hi
+            umma_tf32(d, ah + o, bh + o, idesc, (!chunk_first || kk > 0) ? 1u : 0u);   // hi * hi (first k-block)
             if (three) {
               umma_tf32(d, ah + o, bl + o, idesc, 1u);                                   // hi * lo
               umma_tf32(d, al + o, bh + o, idesc, 1u);                                   // lo * hi
             }
           }
+          if (!three && 2 * it + 1 < nkb) {
+#pragma unroll
+            for (int kk = 0; kk < UM_BK / 8; ++kk) {
+              const uint64_t o = (uint64_t)(kk * 2);
+              umma_tf32(d, al + o, bl + o, idesc, 1u);                                   // second k-block
+            }
+          }
           umma_commit(&empty[s]);
-          if ((it % CL) == CL - 1 || it == nkb - 1) umma_commit(&accf[grp * 2 + b]);
+          if ((it % CL) == CL - 1 || it == nst - 1) umma_commit(&accf[grp * 2 + b]);
         }
         if (!ok) break;
-        cg[grp] += (uint32_t)((nkb + CL - 1) / CL);
+        cg[grp] += (uint32_t)((nst + CL - 1) / CL);
       }
     }
   } else {
@@ -544,8 +580,9 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
       if (*(volatile int*)&s_fail) break;
       int n0, m0, z, kb0, nkb;
       decode(t, n0, m0, z, kb0, nkb);
-      const int CL = up_chunk_len(a.nseg);
-      const int nch = (nkb + CL - 1) / CL;
+      const int CL = a.chunk_len;
+      const int nst = a.nseg == 3 ? nkb : (nkb + 1) / 2;
+      const int nch = (nst + CL - 1) / CL;
       float acc[BN];
 #pragma unroll
       for (int j = 0; j < BN; ++j) acc[j] = 0.f;
@@ -638,7 +675,27 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
                 : "r"(tbase + (uint32_t)(cb + 16)));
           }
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (rok) {
+          if (rok && a.c_fp64) {
+            double* Cd = (double*)a.C;
+            const int rexp = a.eA ? a.eA[(int64_t)z * a.ea_zs + row] + a.eshift : 0;
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const int n = n0 + cb + j;
+              if (cb + j < BN && n < a.N) {
+                const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
+                const int ex = a.eB ? rexp + a.eB[(int64_t)z * a.eb_zs + (n >> 1)] : rexp;
+                const double sre = ldexp(a.alpha * (double)__uint_as_float(v[j]), ex);
+                const double sim = ldexp(a.alpha * (double)__uint_as_float(v[j + 1]), ex);
+                double2* p2 = (double2*)(Cd + off);
+                if (a.accumulate) {
+                  const double2 o = *p2;
+                  *p2 = make_double2(o.x + sre, o.y + sim);
+                } else {
+                  *p2 = make_double2(sre, sim);
+                }
+              }
+            }
+          } else if (rok) {
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const int n = n0 + cb + j;
@@ -849,7 +906,7 @@ static int tune_bn(const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1, int64_t col_inner,
-                      int64_t col_s1, float* C_lo) {
+                      int64_t col_s1, float* C_lo, const UmmaScale* scale) {
   if (Kpad % UM_BK) return cudaErrorInvalidValue;
   if (ksplit < 1) ksplit = 1;
   if (ksplit > 1 && (!c_fp64 || !accumulate)) return cudaErrorInvalidValue;   // split partials add atomically
@@ -867,15 +924,20 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   if (C_lo && (c_fp64 || accumulate)) return cudaErrorInvalidValue;
   // (re, im) column pairs of a complex output that land next to each other while
   // consecutive rows are 2 floats apart: stored row by row from the tile lanes
-  a.direct = (!c_fp64 && !accumulate && col_inner == 2 && c_ld == 2 && (N % 2) == 0 && (c_zs % 2) == 0 &&
-              (a.row_s1 % 2) == 0 && (col_s1 % 2) == 0 && ((uintptr_t)C % 8) == 0 &&
-              ((uintptr_t)C_lo % 8) == 0) ? 1 : 0;
+  a.direct = (((!c_fp64 && !accumulate) || (c_fp64 && ksplit == 1)) && col_inner == 2 && c_ld == 2 &&
+              (N % 2) == 0 && (c_zs % 2) == 0 && (a.row_s1 % 2) == 0 && (col_s1 % 2) == 0 &&
+              ((uintptr_t)C % (c_fp64 ? 16 : 8)) == 0 && ((uintptr_t)C_lo % 8) == 0) ? 1 : 0;
   a.err = err;
+  a.chunk_len = nseg == 3 ? g_chunk_len : UM_FLUSH;
+  if (scale) {
+    if (!c_fp64 || !g_persistent) return cudaErrorInvalidValue;
+    a.eA = scale->eA; a.eB = scale->eB; a.ea_zs = scale->ea_zs; a.eb_zs = scale->eb_zs; a.eshift = scale->eshift;
+  }
   int bn = cost_model_bn(N);
   if (g_persistent && g_autotune) {
     const TuneKey key{M, N, batch, nseg, ksplit,
                       (c_fp64 ? 1 : 0) | (accumulate ? 2 : 0) | (a.direct ? 4 : 0) | (C_lo ? 8 : 0) |
-                          (a.a_batched ? 16 : 0) | (a.b_batched ? 32 : 0),
+                          (a.a_batched ? 16 : 0) | (a.b_batched ? 32 : 0) | (scale ? 64 : 0),
                       Kpad};
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -1070,6 +1132,14 @@ cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float*
 // Internal entry points for unit tests of the tensor-core GEMM (not part of the
 // public header).  All pointers are device pointers; the scratch is allocated
 // here with cudaMalloc.  Returns 0 on success, else a CUDA error or kernel code.
+
+// Sets the number of k-blocks the persistent kernel accumulates in TMEM before
+// adding into its FP32 register sums (three-product GEMMs); returns the old value.
+extern "C" int gwdbg_umma_set_chunk(int k) {
+  const int old = gwk::g_chunk_len;
+  if (k >= 1 && k <= 16) gwk::g_chunk_len = k;
+  return old;
+}
 
 // Turns the N-tile autotuner of the persistent kernel on (1, the default) or off
 // (0: cost model only); returns the previous setting.  Cached choices are kept.

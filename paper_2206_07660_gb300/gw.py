@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libgwgb.so")
 GW_OK, GW_ERR_ARG, GW_ERR_CUDA, GW_ERR_OOM, GW_ERR_NOT_CONVERGED, GW_ERR_SINGULAR, GW_ERR_TIMEOUT, \
     GW_ERR_STATE, GW_ERR_INTERNAL = range(9)
 PRECISIONS = {"fp64": 0, "fp32": 1, "split_bf16": 2, "split_tf32": 3}
-GW_INPUT_DEVICE, GW_BORROW_V, GW_SKIP_CHECKS, GW_SMALL_TENSOR, GW_SMALL_SIMT = 1, 2, 4, 8, 16
+GW_INPUT_DEVICE, GW_BORROW_V, GW_SKIP_CHECKS, GW_SMALL_TENSOR, GW_SMALL_SIMT, GW_FP64_NATIVE = 1, 2, 4, 8, 16, 32
 
 QUANTITIES = {
     "G_tau": 0, "G_iw": 1, "Sigma_inf": 2, "Sigma_tau": 3, "Sigma_iw": 4, "P0_tau": 5, "P0_iw": 6,
@@ -126,7 +126,7 @@ class GW:
 
     def __init__(self, H0, S, V, kmesh, ntau, beta, fermi_n, bose_m, n_elec=None, damping=0.5,
                  mu_tol=1e-9, mu_maxit=400, precision="fp64", spin=2, borrow_V=False,
-                 skip_checks=False, torch_alloc=True, small_steps="auto"):
+                 skip_checks=False, torch_alloc=True, small_steps="auto", fp64_gemm="tensor"):
         import torch
         self.lib = load()
         self.torch = torch
@@ -174,6 +174,7 @@ class GW:
         if skip_checks:
             flags |= GW_SKIP_CHECKS
         flags |= {"auto": 0, "tensor": GW_SMALL_TENSOR, "simt": GW_SMALL_SIMT}[small_steps]
+        flags |= {"tensor": 0, "native": GW_FP64_NATIVE}[fp64_gemm]
         cfg.flags = flags
         self._cfg = cfg
         ctx = ctypes.c_void_p()

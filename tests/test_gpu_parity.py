@@ -198,3 +198,17 @@ def test_lowp_stages(nao, naux, kmesh, ntau, precision, small):
     g.selfenergy()
     S = ogw.selfenergy_tau(st.V, G, P, st.km)
     assert rel(g.get("Sigma_tau"), S) < 2e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_tf32"])
+def test_transforms_tensor_vs_native_fp64(precision):
+    # the tau <-> i nu transforms as digit-split tensor-core products agree with the
+    # FP64 SIMT kernel to FP64 roundoff over full iterations
+    sysd = make_config_system("C1")
+    a = gpu(sysd, precision=precision, fp64_gemm="tensor")
+    b = gpu(sysd, precision=precision, fp64_gemm="native")
+    a.iterate(2)
+    b.iterate(2)
+    for q in ("G_tau", "Sigma_iw", "P_tau"):
+        x, y = a.get(q), b.get(q)
+        assert np.abs(x - y).max() <= 1e-11 * max(1.0, np.abs(y).max()), q
