@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gw", choices=["gw", "reference"])
-    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4"])
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4", "C5"])
+    p.add_argument("--c5-vjp", action="store_true", help="C5: also time the FP64 adjoint chains")
     p.add_argument("--precision", default="split_tf32", choices=["split_tf32", "fp32", "fp64"])
     p.add_argument("--fp64-gemm", default="tensor", choices=["tensor", "native"],
                    help="FP64 tau<->i nu transforms: digit-split tensor-core products or the FP64 SIMT kernel")
@@ -547,6 +548,97 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_differentiation(args):
+    """C5 (C2 sizes): the tangent of the whole self-consistency map and Newton-Krylov
+    self-consistency built on it, against damped iterations from the same start."""
+    import numpy as np
+    import torch
+    from paper_2206_07660_gb300 import GW
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg, sysd = make_inputs("C2", kmesh=args.kmesh)
+    prec = args.precision
+
+    def ctx(damping):
+        return GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
+                  sysd["bose_m"], n_elec=sysd["n_elec"], damping=damping, precision=prec, mu_tol=1e-10)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # damped reference: residual ||F(x) - x|| per iteration (one extra unmixed map per step)
+    g = ctx(1.0)
+    g.iterate(2)
+    start_i, start_w = g.get("Sigma_inf"), g.get("Sigma_iw")
+    # tangent timing at the start point
+    g.polarization()
+    g.screened()
+    vi = torch.randn(*g.shape_of("Sigma_inf"), dtype=torch.complex128, device="cuda")
+    vw = torch.randn(*g.shape_of("Sigma_iw"), dtype=torch.complex128, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        g.sc_jvp(vi, vw)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    for _ in range(args.steps):
+        g.sc_jvp(vi, vw)
+    e1.record()
+    torch.cuda.synchronize()
+    jvp_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    e0, e1 = ev(), ev()
+    e0.record()
+    g.iterate(1)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_s = e0.elapsed_time(e1) / 1e3
+    g.close()
+    # Newton-Krylov from the start point
+    n_outer, m = 4, 6
+    gn = ctx(1.0)
+    gn.set("Sigma_inf", start_i)
+    gn.set("Sigma_iw", start_w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_nk = gn.iterate_newton(n_outer, m=m, tol=1e-10)
+    torch.cuda.synchronize()
+    nk_s = time.perf_counter() - t0
+    gn.close()
+    # damped iterations (mixing 0.5) from the same start, for the same wall time
+    gd = ctx(0.5)
+    gd.set("Sigma_inf", start_i)
+    gd.set("Sigma_iw", start_w)
+    res_d, t0 = [], time.perf_counter()
+    while time.perf_counter() - t0 < nk_s and len(res_d) < 200:
+        st = gd.iterate(1)
+        res_d.append(float(st["max_dSigma"]))
+    torch.cuda.synchronize()
+    gd.close()
+    line = {"metric": METRIC, "value": nk_s / n_outer, "unit": "s/Newton-Krylov step (GMRES(%d), %s)" % (m, prec),
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": nk_s / n_outer * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "c64", "fp64": "c128", "split_tf32": "tf32x3/c64"}[prec], "data": "synthetic",
+            "config": dict(workload_config(cfg, "C5", prec),
+                           workload="C5: C2 sizes, tangent of the self-consistency map and Newton-Krylov "
+                                    "self-consistency (GMRES(%d)) vs damped (0.5) iterations" % m),
+            "sc_jvp_s": jvp_s, "forward_iteration_s": fwd_s,
+            "newton_residual_l2": res_nk, "newton_wall_s": nk_s,
+            "damped_max_dSigma_same_wall_time": res_d[-3:], "damped_iterations_same_wall_time": len(res_d)}
+    if args.c5_vjp:
+        import numpy as np
+        g = GW(sysd["H0"], sysd["S"], sysd["V"], sysd["kmesh"], sysd["ntau"], sysd["beta"], sysd["fermi_n"],
+               sysd["bose_m"], n_elec=sysd["n_elec"], precision=prec)
+        g.iterate(1)
+        Pbar = torch.randn(*g.shape_of("P_tau"), dtype=torch.complex128, device="cuda")
+        Sbar = torch.randn(*g.shape_of("Sigma_tau"), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.polarization_vjp(Pbar)
+        g.selfenergy_vjp(Sbar)
+        torch.cuda.synchronize()
+        line["fp64_vjp_pair_s"] = time.perf_counter() - t0
+        g.close()
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.peaks:
@@ -555,6 +647,8 @@ def main():
         return run_reference(args)
     if args.workload == "C4":
         return run_batch(args)
+    if args.workload == "C5":
+        return run_differentiation(args)
     return run_gw(args)
 
 

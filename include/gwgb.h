@@ -248,8 +248,9 @@ gw_status gw_selfenergy_vjp(gw_ctx* ctx, const double* Sbar, double* Gbar, doubl
  * tilde_P0_tau, symmetrised) along dG at the context's current G.  P~0 is a
  * quadratic form in G, so dP~0 = P(dG(tau), G(-tau)) + P(G(tau), dG(-tau)).
  * dG [ntau][nk][nao][nao] in, dP0 [nq][ntau][naux][naux] out (overwritten);
- * device pointers; fp64 whatever contract_prec is.  Shares the adjoint chain
- * buffers (allocated on first use). */
+ * device pointers.  Runs the forward chain of contract_prec (FP64, complex64
+ * SIMT or split-TF32 tensor cores) twice; with complex64 contractions a second
+ * c64 copy of G is allocated on first use. */
 gw_status gw_polarization_jvp(gw_ctx* ctx, const double* dG, double* dP0);
 
 /* Tangent of the screened block (Eqs. P0t_to_P0w, tilde_P_omega, Piw_to_Pt)
@@ -263,8 +264,27 @@ gw_status gw_screened_jvp(gw_ctx* ctx, const double* dP0_tau, double* dP_tau);
  * (dG, dP~(tau)) at the context's current G and P~(tau): Sigma~ is bilinear,
  * dSigma~ = S(dG, P~) + S(G, dP~).  dG [ntau][nk][nao][nao], dP_tau
  * [nq][ntau][naux][naux] in; dS_tau [ntau][nk][nao][nao] out (overwritten);
- * device pointers; fp64. */
+ * device pointers; runs the forward chain of contract_prec twice. */
 gw_status gw_selfenergy_jvp(gw_ctx* ctx, const double* dG, const double* dP_tau, double* dS_tau);
+
+/* Tangent of the self-consistency map F: (Sigma_inf, Sigma(i w)) -> (Sigma_inf',
+ * Sigma'(i w)) (one pass of Eqs. Dyson, iw_to_tau, HF_J/HF_K, tilde_P0_tau,
+ * tilde_P_omega, tilde_sigma2, tau_to_iw, with mu held at N(mu) = n_elec) along
+ * (dSinf [nk][nao][nao], dSiw [nw][nk][nao][nao]), at the context's state: G
+ * from gw_dyson at the current Sigma and P~ from gw_polarization + gw_screened
+ * at that G (GW_ERR_STATE otherwise).  Outputs oSinf, oSiw (same shapes) are
+ * overwritten; all device pointers.  The Dyson and mu tangents
+ * (dG = G D G - dmu G S G, dmu from dN = 0) and the transforms run in FP64, the
+ * contraction tangents at contract_prec.  Allocates its buffers on first use. */
+gw_status gw_sc_jvp(gw_ctx* ctx, const double* dSinf, const double* dSiw, double* oSinf, double* oSiw);
+
+/* Newton-Krylov self-consistency: n_outer steps x <- x + delta on x =
+ * (Sigma_inf, Sigma(i w)), with (J - I) delta = -(F(x) - x) solved by GMRES(m)
+ * (1 <= m <= 64) whose products J v are gw_sc_jvp calls.  Stops early when
+ * ||F(x) - x||_2 <= tol; res_out (host, n_outer doubles, may be NULL) receives
+ * the residual norm of each step.  The context ends with G from gw_dyson at the
+ * final Sigma (no damping is applied). */
+gw_status gw_iterate_newton(gw_ctx* ctx, int32_t n_outer, int32_t m, double tol, double* res_out);
 
 /* Allocation-free screened solve: P = [I - P0]^{-1} P0 for `count` complex
  * n x n matrices (interleaved (re, im) doubles, row-major, contiguous), the

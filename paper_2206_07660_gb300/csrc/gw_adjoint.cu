@@ -171,101 +171,3 @@ cudaError_t selfenergy_vjp(const View& v, const double2* Sbar, double2* Gbar, do
 }
 
 }  // namespace gwadj
-
-// ---------------------------------------------------------------- tangents (JVPs)
-// P~0 is a quadratic form in G and Sigma~ is bilinear in (G, P~), so their
-// tangents are the forward chains with one factor replaced by its tangent:
-//   dP_QQ' = (s/Nk) sum_k [V1 dG' V2 Gm + V1 G' V2 dGm]     (then symmetrised)
-//   dS_ij  = -(1/Nk) sum_q [V1 dG P V2 + V1 G dP V2]        (then symmetrised)
-// with the factors of the comment at the top of this file.
-namespace gwadj {
-
-// dP (nq,ntau,naux,naux) = tangent of the symmetrised P~0(tau) along dG (ntau,nk,nao,nao).
-cudaError_t polarization_jvp(const View& v, const double2* dG, double2* dP, int64_t* launches) {
-  const int nk = v.nk, nao = v.nao, naux = v.naux, ntau = v.ntau;
-  const int64_t n2 = (int64_t)nao * nao, na2 = (int64_t)naux * naux, slab = (int64_t)naux * n2,
-                gstep = (int64_t)nk * n2;
-  const double f = v.spin / nk;
-  cudaError_t e;
-  for (int q = 0; q < nk; ++q) {
-    double2* Pq = dP + (size_t)q * ntau * na2;
-    for (int k = 0; k < nk; ++k) {
-      const int kq = v.kplus[(size_t)q * nk + k];
-      const double2* V1 = v.V + ((size_t)k * nk + kq) * slab;
-      // Y1 = V1 dG^{k+q}(t),  Y2 = V1 G^{k+q}(t):  Y[t][(Q,d)][b] = sum_a V1[Q][d][a] X[t][a][b]
-      GettDesc d1 = desc((int64_t)naux * nao, nao, nao, ntau);
-      d1.am = I1(nao); d1.ak = I1(1); d1.az = I1(0);
-      d1.bk = I1(nao); d1.bn = I1(1); d1.bz = I1(gstep);
-      d1.cm = I1(nao); d1.cn = I1(1); d1.cz = I1(slab);
-      if ((e = run(v, d1, V1, dG + (size_t)kq * n2, v.bufA))) return e;
-      if ((e = run(v, d1, V1, v.G_tau + (size_t)kq * n2, v.bufB))) return e;
-      // Z[t][Q][c][b] = -sum_d G^k(t_{n-1-j})[c][d] Y1[t][Q][d][b] - sum_d dG^k(t_{n-1-j})[c][d] Y2[t][Q][d][b]
-      GettDesc d2 = desc(nao, (int64_t)naux * nao, nao, ntau);
-      d2.am = I1(nao); d2.ak = I1(1); d2.az = I1(-gstep);
-      d2.bk = I1(nao); d2.bn = I2(nao, n2, 1); d2.bz = I1(slab);
-      d2.cm = I1(nao); d2.cn = I2(nao, n2, 1); d2.cz = I1(slab);
-      d2.alpha = make_double2(-1, 0);
-      const size_t rev = (size_t)(ntau - 1) * gstep + (size_t)k * n2;
-      if ((e = run(v, d2, v.G_tau + rev, v.bufA, v.bufC))) return e;
-      d2.beta = make_double2(1, 0);
-      if ((e = run(v, d2, dG + rev, v.bufB, v.bufC))) return e;
-      // dP[t][Q][Q'] += f sum_{(c,b)} Z[t][Q][(c,b)] conj(V1[Q'][(c,b)])   (V^{k+q,k}_bc = conj V^{k,k+q}_cb)
-      GettDesc d3 = desc((int64_t)ntau * naux, naux, n2, 1);
-      d3.am = I1(n2); d3.ak = I1(1);
-      d3.bk = I1(1); d3.bn = I1(n2); d3.conjB = true;
-      d3.cm = I1(naux); d3.cn = I1(1);
-      d3.alpha = make_double2(f, 0);
-      d3.beta = make_double2(k == 0 ? 0.0 : 1.0, 0);
-      if ((e = run(v, d3, v.bufC, V1, Pq))) return e;
-      *launches += 5;
-    }
-  }
-  if ((e = herm_batched(dP, naux, (int64_t)nk * ntau, na2, v.st))) return e;
-  *launches += 1;
-  return cudaSuccess;
-}
-
-// dS (ntau,nk,nao,nao) = tangent of the symmetrised Sigma~(tau) along (dG, dP).
-cudaError_t selfenergy_jvp(const View& v, const double2* dG, const double2* dPt, double2* dS, int64_t* launches) {
-  const int nk = v.nk, nao = v.nao, naux = v.naux, ntau = v.ntau;
-  const int64_t n2 = (int64_t)nao * nao, na2 = (int64_t)naux * naux, slab = (int64_t)naux * n2,
-                gstep = (int64_t)nk * n2;
-  cudaError_t e;
-  for (int q = 0; q < nk; ++q) {
-    for (int k = 0; k < nk; ++k) {
-      const int kmq = v.kminus[(size_t)q * nk + k];
-      const double2* V1 = v.V + ((size_t)k * nk + kmq) * slab;
-      const double2* V2 = v.V + ((size_t)kmq * nk + k) * slab;
-      // X[t][Q'][(i,a)] = sum_Q P[t][Q][Q'] V1[Q][(i,a)]   (with dP into bufA, with P into bufC)
-      GettDesc d1 = desc(naux, n2, naux, ntau);
-      d1.am = I1(1); d1.ak = I1(naux); d1.az = I1(na2);
-      d1.bk = I1(n2); d1.bn = I1(1); d1.bz = I1(0);
-      d1.cm = I1(n2); d1.cn = I1(1); d1.cz = I1(slab);
-      if ((e = run(v, d1, dPt + (size_t)q * ntau * na2, V1, v.bufA))) return e;
-      if ((e = run(v, d1, v.P_tau + (size_t)q * ntau * na2, V1, v.bufC))) return e;
-      // Y[t][i][Q'][b] = sum_a X_dP[t][Q'][i][a] G[t][a][b] + sum_a X_P[t][Q'][i][a] dG[t][a][b]
-      GettDesc d2 = desc((int64_t)naux * nao, nao, nao, ntau);
-      d2.am = I1(nao); d2.ak = I1(1); d2.az = I1(slab);
-      d2.bk = I1(nao); d2.bn = I1(1); d2.bz = I1(gstep);
-      d2.cm = I2(nao, nao, (int64_t)naux * nao); d2.cn = I1(1); d2.cz = I1(slab);
-      if ((e = run(v, d2, v.bufA, v.G_tau + (size_t)kmq * n2, v.bufB))) return e;
-      d2.beta = make_double2(1, 0);
-      if ((e = run(v, d2, v.bufC, dG + (size_t)kmq * n2, v.bufB))) return e;
-      // dS[t][k][i][j] += -(1/Nk) sum_{(Q',b)} Y[t][i][(Q',b)] V2[Q'][b][j]
-      GettDesc d3 = desc(nao, nao, (int64_t)naux * nao, ntau);
-      d3.am = I1((int64_t)naux * nao); d3.ak = I1(1); d3.az = I1(slab);
-      d3.bk = I1(nao); d3.bn = I1(1); d3.bz = I1(0);
-      d3.cm = I1(nao); d3.cn = I1(1); d3.cz = I1(gstep);
-      d3.alpha = make_double2(-1.0 / nk, 0);
-      d3.beta = make_double2(q == 0 ? 0.0 : 1.0, 0);
-      d3.ksplit = 8;
-      if ((e = run(v, d3, v.bufB, V2, dS + (size_t)k * n2))) return e;
-      *launches += 6;
-    }
-  }
-  if ((e = herm_batched(dS, nao, (int64_t)ntau * nk, n2, v.st))) return e;
-  *launches += 1;
-  return cudaSuccess;
-}
-
-}  // namespace gwadj

@@ -47,6 +47,12 @@ struct gw_ctx {
   void *chA = nullptr, *chB = nullptr;
   size_t ch_bytes = 0;
   float2 *G32 = nullptr, *P32 = nullptr, *gam32 = nullptr;
+  float2* G32m = nullptr;   // c64 copy of the G(-tau) factor when it differs from G(tau) (tangents)
+  // tangent of the self-consistency map: dG(i w), dG(tau), dSigma~(tau), dgamma, dP~, reductions
+  double2 *tGiw = nullptr, *tGtau = nullptr, *tS = nullptr, *tgam = nullptr, *tP = nullptr;
+  double* tpart = nullptr;
+  std::vector<double2*> kry;   // Newton-Krylov basis (owned through `owned`)
+  int nvec = 0;
   // split-TF32 tensor-core operands (hi / lo planes, rows padded to 32 fp32)
   float *Zhi = nullptr, *Zlo = nullptr, *Vhi = nullptr, *Vlo = nullptr;
   float *Pchi = nullptr, *Pclo = nullptr, *VThi = nullptr, *VTlo = nullptr;
@@ -200,17 +206,17 @@ static cudaError_t run_bsm(gw_ctx* c, BsmDesc d) {
 // Ge[k][t] = doubled operand of conj(G^k(t)) for C = A conj(Ge)^T (TF32 hi/lo); with a
 // Hermitian G(t) that product is A G(t).  Gp (polarization only) holds the reversed
 // plain operands G^k(t_{ntau-1-j}).
-static cudaError_t build_gemb(gw_ctx* c) {
+static cudaError_t build_gemb(gw_ctx* c, const double2* Gplus, const double2* Gminus) {
   const int64_t n2 = c->n2, gstep = (int64_t)c->nk * n2, per = 2 * (int64_t)c->nao * c->kpadA;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < c->nk && !e; ++k)
-    e = embed_conj_batched(c->G_tau + (size_t)k * n2, c->ntau, gstep, c->nao, c->nao, c->Ge_hi + (size_t)k * c->ntau * per,
+    e = embed_conj_batched(Gplus + (size_t)k * n2, c->ntau, gstep, c->nao, c->nao, c->Ge_hi + (size_t)k * c->ntau * per,
                            c->Ge_lo + (size_t)k * c->ntau * per, c->kpadA, per, c->st);
   count(c->nk);
-  if (!c->Gp_hi) return e;
+  if (!c->Gp_hi || !Gminus) return e;
   // Gp[k][j] = doubled operand of G^k(t_{ntau-1-j}) for C = A Gp^T (the G(-t) factor up to its sign)
   for (int k = 0; k < c->nk && !e; ++k)
-    e = embed_plain_batched(c->G_tau + (size_t)(c->ntau - 1) * gstep + (size_t)k * n2, c->ntau, -gstep, c->nao, c->nao,
+    e = embed_plain_batched(Gminus + (size_t)(c->ntau - 1) * gstep + (size_t)k * n2, c->ntau, -gstep, c->nao, c->nao,
                             c->Gp_hi + (size_t)k * c->ntau * per, c->Gp_lo + (size_t)k * c->ntau * per, c->kpadA, per,
                             c->st);
   count(c->nk);
@@ -544,16 +550,16 @@ extern "C" gw_status gw_reset_sigma(gw_ctx* c) {
 
 // ------------------------------------------------------------------ A1: gamma, J, K
 
-static gw_status exchange(gw_ctx* c) {
+static gw_status exchange(gw_ctx* c, const double2* gamma, double2* out) {
   // K^k_ij = -(1/Nk) sum_{k',Q,a,b} V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q)    (Eq. HF_K)
   const int nk = c->nk, nao = c->nao, naux = c->naux;
   const int64_t n2 = c->n2, slab = (int64_t)naux * n2;
   const bool f32 = c->cfg.contract_prec != GW_FP64;
   const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = f32 ? Ty::C64 : Ty::C128;
   const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
-  const void* gp = c->gamma;
+  const void* gp = gamma;
   Ty tg = Ty::C128;
-  if (f32) { CK(to_c64(c->gamma, c->gam32, nk * n2, c->st)); count(1); gp = c->gam32; tg = Ty::C64; }
+  if (f32) { CK(to_c64(gamma, c->gam32, nk * n2, c->st)); count(1); gp = c->gam32; tg = Ty::C64; }
   const size_t es = f32 ? 8 : 16;
   for (int kp = 0; kp < nk; ++kp) {
     // Y[k][i][Q][b] = sum_a V^{k k'}[Q][i][a] gamma^{k'}[a][b]    (batch over k)
@@ -581,45 +587,64 @@ static gw_status exchange(gw_ctx* c) {
     e.alpha = make_double2(-1.0 / nk, 0); e.beta = make_double2(1, 0);
     e.ksplit = 16;
     const char* Vk = (const char*)Vp + (size_t)kp * nk * slab * es;
-    CK(run_gett(e, c->chA, tv, Vk, tv, c->Sinf_new, Ty::C128, acc, c));
+    CK(run_gett(e, c->chA, tv, Vk, tv, out, Ty::C128, acc, c));
   }
   return GW_OK;
+}
+
+// Sigma_inf = J[gamma] + K[gamma] with gamma = -G(beta^-) from Gsrc (linear in G, so the
+// same routine gives the tangent from a tangent of G).
+static gw_status hf_core(gw_ctx* c, const double2* Gsrc, double2* gamma, double2* out) {
+  const int nk = c->nk, nao = c->nao, naux = c->naux;
+  CK(density_gamma(Gsrc, c->lb, gamma, c->ntau, (int64_t)nk * c->n2, c->st));
+  CK(hartree_t(c->V, gamma, c->tQ, nk, naux, nao, c->st));
+  CK(hartree_j(c->V, c->tQ, out, nk, naux, nao, c->spin / nk, c->st));   // Eq. HF_J
+  count(3);
+  return exchange(c, gamma, out);
 }
 
 extern "C" gw_status gw_hf(gw_ctx* c) {
   if (!c) return GW_ERR_ARG;
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
-  const int nk = c->nk, nao = c->nao, naux = c->naux;
-  CK(density_gamma(c->G_tau, c->lb, c->gamma, c->ntau, (int64_t)nk * c->n2, c->st));
-  CK(hartree_t(c->V, c->gamma, c->tQ, nk, naux, nao, c->st));
-  CK(hartree_j(c->V, c->tQ, c->Sinf_new, nk, naux, nao, c->spin / nk, c->st));   // Eq. HF_J
-  count(3);
-  return exchange(c);
+  return hf_core(c, c->G_tau, c->gamma, c->Sinf_new);
 }
 
 // ------------------------------------------------------------------ A2/A3: polarization
 
-extern "C" gw_status gw_polarization(gw_ctx* c) {
-  if (!c) return GW_ERR_ARG;
-  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+// The P~0 chain of Eq. tilde_P0_tau with its two G factors taken from separate
+// tensors: Gplus supplies G^{k+q}(t), Gminus supplies G^k(-t) (= -Gminus^k(t_{ntau-1-j})).
+// out (nq, ntau, naux, naux) receives the unsymmetrised sum, added to its contents
+// when accumulate.  The forward map uses G_tau for both; its tangent runs the chain
+// twice with the tangent in one slot.
+static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gminus, double2* out, bool accumulate) {
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
   const bool f32 = c->cfg.contract_prec != GW_FP64;
   const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
   const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = tv;
   const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
-  const void* Gp = c->G_tau;
+  const void* Gp = Gplus;
+  const void* Gmp = Gminus;
   const size_t es = f32 ? 8 : 16;
-  if (f32) { CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st)); count(1); Gp = c->G32; }
+  if (f32) {
+    CK(to_c64(Gplus, c->G32, (int64_t)ntau * gstep, c->st)); count(1); Gp = c->G32; Gmp = c->G32;
+    if (Gminus != Gplus) {
+      if (!c->G32m) {
+        c->G32m = (float2*)dalloc(c, (size_t)ntau * gstep * 8);
+        if (!c->G32m) return fail(c, GW_ERR_OOM, "tangent buffer");
+      }
+      CK(to_c64(Gminus, c->G32m, (int64_t)ntau * gstep, c->st)); count(1); Gmp = c->G32m;
+    }
+  }
   if (!c->deferred) CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
-  const bool tca = tc && c->Vs_hi != nullptr;   // nao-sized first step on tensor cores
-  if (tca) CK(build_gemb(c));
+  const bool tca = tc && c->Vs_hi != nullptr;   // nao-sized steps on tensor cores
+  if (tca) CK(build_gemb(c, Gplus, Gminus));
   for (int q = 0; q < nk; ++q) {
-    double2* Pq = c->P0_tau + (size_t)q * ntau * na2;
+    double2* Pq = out + (size_t)q * ntau * na2;
     for (int k = 0; k < nk; ++k) {
       const int kq = c->kplus[(size_t)q * nk + k];
       const char* Vkq = (const char*)Vp + ((size_t)k * nk + kq) * slab * es;
-      const char* Gm = (const char*)Gp + ((size_t)(ntau - 1) * gstep + (size_t)k * n2) * es;
+      const char* Gm = (const char*)Gmp + ((size_t)(ntau - 1) * gstep + (size_t)k * n2) * es;
       if (tca) {
         // Y[t][Q][d][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b] on tensor cores (G Hermitian), written
         // transposed per Q as TF32 hi/lo rows (t, Q, b) of (d, re/im): the A operand of the next step
@@ -688,7 +713,7 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
         UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, kp, 0};
         UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, kp, 0};
         CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, kp, 1, Pq, true,
-                    c->spin / nk, k > 0, 2 * (int64_t)naux, 0));
+                    c->spin / nk, accumulate || k > 0, 2 * (int64_t)naux, 0));
         count(1);
         continue;
       }
@@ -697,10 +722,21 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
       d3.bk = I1(1); d3.bn = I1(n2); d3.conjB = true;
       d3.cm = I1(naux); d3.cn = I1(1);
       d3.alpha = make_double2(c->spin / nk, 0);
-      d3.beta = make_double2(k == 0 ? 0.0 : 1.0, 0);
+      d3.beta = make_double2(accumulate || k > 0 ? 1.0 : 0.0, 0);
       CK(run_gett(d3, c->chB, tv, Vkq, tv, Pq, Ty::C128, acc, c));
     }
   }
+  return GW_OK;
+}
+
+extern "C" gw_status gw_polarization(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  const int nk = c->nk, naux = c->naux, ntau = c->ntau;
+  const int64_t na2 = c->na2;
+  const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
+  gw_status s = polar_chain(c, c->G_tau, c->G_tau, c->P0_tau, false);
+  if (s != GW_OK) return s;
   if (tc && !c->deferred) {
     int h = 0;
     CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
@@ -748,24 +784,28 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
 
 // ------------------------------------------------------------------ A6: self-energy
 
-static gw_status sigma_dynamic(gw_ctx* c) {
+// The Sigma~ chain of Eq. tilde_sigma2 with G^{k-q}(t) from Gsrc and P~^q(t) from
+// Psrc; out (ntau, nk, nao, nao) receives the unsymmetrised sum (added to its
+// contents when accumulate).  The forward map uses G_tau and P_tau; the tangent runs
+// it with the tangent in either slot.
+static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc, double2* out, bool accumulate) {
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
   const bool f32 = c->cfg.contract_prec != GW_FP64;
   const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
   const Ty tv = f32 ? Ty::C64 : Ty::C128, acc = tv;
   const void* Vp = f32 ? (const void*)c->V32 : (const void*)c->V;
-  const void* Gp = c->G_tau;
-  const void* Pp = c->P_tau;
+  const void* Gp = Gsrc;
+  const void* Pp = Psrc;
   if (!c->deferred) CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
   const bool tc3 = tc && c->Y3hi != nullptr;   // last step on tensor cores (atomic fp64 accumulation)
-  if (tc3) CK(cudaMemsetAsync(c->Stau, 0, (size_t)ntau * gstep * 16, c->st));
+  if (tc3 && !accumulate) CK(cudaMemsetAsync(out, 0, (size_t)ntau * gstep * 16, c->st));
   const bool tc2 = tc3 && c->Xs_hi != nullptr;   // middle step on tensor cores too
-  if (tc2) CK(build_gemb(c));
+  if (tc2) CK(build_gemb(c, Gsrc, nullptr));
   const size_t es = f32 ? 8 : 16;
   if (f32) {
-    CK(to_c64(c->G_tau, c->G32, (int64_t)ntau * gstep, c->st));
-    CK(to_c64(c->P_tau, c->P32, (int64_t)nk * ntau * na2, c->st));
+    CK(to_c64(Gsrc, c->G32, (int64_t)ntau * gstep, c->st));
+    CK(to_c64(Psrc, c->P32, (int64_t)nk * ntau * na2, c->st));
     count(2);
     Gp = c->G32; Pp = c->P32;
   }
@@ -773,7 +813,7 @@ static gw_status sigma_dynamic(gw_ctx* c) {
     const char* Pq = (const char*)Pp + (size_t)q * ntau * na2 * es;
     if (tc) {
       // A operand of the tensor-core stage: conj P~^q(t) = P~^q(t)^T (Hermitian), split hi/lo
-      CK(split_rows(c->P_tau + (size_t)q * ntau * na2, true, (int64_t)ntau * naux, naux, naux, true, c->Pchi,
+      CK(split_rows(Psrc + (size_t)q * ntau * na2, true, (int64_t)ntau * naux, naux, naux, true, c->Pchi,
                     c->Pclo, c->kpadS, c->st));
       count(1);
     }
@@ -848,7 +888,7 @@ static gw_status sigma_dynamic(gw_ctx* c) {
         if (ks > kp / 32) ks = kp / 32;
         if (ks < 1) ks = 1;
         CK(run_umma(c, 8.0 * ntau * nao * (double)nao * naux * nao, oa, ob, ntau * nao, 2 * nao, kp, 1,
-                    (double*)(c->Stau + (size_t)k * n2), true, -1.0 / nk, true, 2 * (int64_t)nao, 0, (int)ks, nao,
+                    (double*)(out + (size_t)k * n2), true, -1.0 / nk, true, 2 * (int64_t)nao, 0, (int)ks, nao,
                     2 * gstep));
         count(1);
         continue;
@@ -858,12 +898,21 @@ static gw_status sigma_dynamic(gw_ctx* c) {
       d3.bk = I1(nao); d3.bn = I1(1); d3.bz = I1(0);
       d3.cm = I1(nao); d3.cn = I1(1); d3.cz = I1(gstep);
       d3.alpha = make_double2(-1.0 / nk, 0);
-      d3.beta = make_double2(q == 0 ? 0.0 : 1.0, 0);
+      d3.beta = make_double2(accumulate || q > 0 ? 1.0 : 0.0, 0);
       d3.ksplit = 8;
       const char* Vk2 = (const char*)Vp + ((size_t)kmq * nk + k) * slab * es;
-      CK(run_gett(d3, c->chB, tv, Vk2, tv, c->Stau + (size_t)k * n2, Ty::C128, acc, c));
+      CK(run_gett(d3, c->chB, tv, Vk2, tv, out + (size_t)k * n2, Ty::C128, acc, c));
     }
   }
+  return GW_OK;
+}
+
+static gw_status sigma_dynamic(gw_ctx* c) {
+  const int nk = c->nk, nao = c->nao, ntau = c->ntau;
+  const int64_t n2 = c->n2, gstep = (int64_t)nk * n2;
+  const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
+  gw_status s = sigma_chain(c, c->G_tau, c->P_tau, c->Stau, false);
+  if (s != GW_OK) return s;
   if (tc && !c->deferred) {
     int h = 0;
     CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
@@ -1068,8 +1117,7 @@ struct View {
 };
 cudaError_t polarization_vjp(const View& v, const double2* Pbar, double2* Gbar, int64_t* launches);
 cudaError_t selfenergy_vjp(const View& v, const double2* Sbar, double2* Gbar, double2* Pbar, int64_t* launches);
-cudaError_t polarization_jvp(const View& v, const double2* dG, double2* dP, int64_t* launches);
-cudaError_t selfenergy_jvp(const View& v, const double2* dG, const double2* dPt, double2* dS, int64_t* launches);
+
 }  // namespace gwadj
 
 static gw_status adj_view(gw_ctx* c, gwadj::View* v) {
@@ -1122,15 +1170,30 @@ extern "C" gw_status gw_selfenergy_vjp(gw_ctx* c, const double* Sbar, double* Gb
 
 // ------------------------------------------------------------------ tangents (A10)
 
+// Tangents of the contraction chains at the context's precision: the forward chains
+// with the tangent in one G (or P~) slot at a time (P~0 is quadratic in G, Sigma~
+// bilinear in (G, P~)), then the symmetrisation.
+static gw_status tc_check(gw_ctx* c) {
+  if (c->cfg.contract_prec != GW_SPLIT_TF32 || c->deferred) return GW_OK;
+  int h = 0;
+  CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  memcpy(&h, c->h_scr, 4);
+  if (h) return fail(c, GW_ERR_TIMEOUT, "tensor-core contraction gave up waiting (code " + std::to_string(h) + ")");
+  return GW_OK;
+}
+
 extern "C" gw_status gw_polarization_jvp(gw_ctx* c, const double* dG, double* dP0) {
   if (!c || !dG || !dP0) return fail(c, GW_ERR_ARG, "null argument");
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
-  gwadj::View v;
-  gw_status s = adj_view(c, &v);
+  const double2* g = (const double2*)dG;
+  double2* out = (double2*)dP0;
+  gw_status s = polar_chain(c, g, c->G_tau, out, false);
+  if (s == GW_OK) s = polar_chain(c, c->G_tau, g, out, true);
+  if (s == GW_OK) s = tc_check(c);
   if (s != GW_OK) return s;
-  int64_t l = 0;
-  CK(gwadj::polarization_jvp(v, (const double2*)dG, (double2*)dP0, &l));
-  count((int)l);
+  CK(herm_batched(out, c->naux, (int64_t)c->nk * c->ntau, c->na2, c->st));
+  count(1);
   return GW_OK;
 }
 
@@ -1172,12 +1235,198 @@ extern "C" gw_status gw_selfenergy_jvp(gw_ctx* c, const double* dG, const double
   if (!c || !dG || !dP_tau || !dS_tau) return fail(c, GW_ERR_ARG, "null argument");
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
   if (!c->have_P) return fail(c, GW_ERR_STATE, "no screened interaction yet");
+  double2* out = (double2*)dS_tau;
+  gw_status s = sigma_chain(c, (const double2*)dG, c->P_tau, out, false);
+  if (s == GW_OK) s = sigma_chain(c, c->G_tau, (const double2*)dP_tau, out, true);
+  if (s == GW_OK) s = tc_check(c);
+  if (s != GW_OK) return s;
+  CK(herm_batched(out, c->nao, (int64_t)c->ntau * c->nk, c->n2, c->st));
+  count(1);
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ tangent of the SC map (A10)
+
+static gw_status sc_tangent_buffers(gw_ctx* c) {
+  if (c->tGiw) return GW_OK;
+  const size_t gsz = (size_t)c->ntau * c->nk * c->n2 * 16, psz = (size_t)c->nk * c->ntau * c->na2 * 16;
+  c->tGiw = (double2*)dalloc(c, gsz);
+  c->tGtau = (double2*)dalloc(c, gsz);
+  c->tS = (double2*)dalloc(c, gsz);
+  c->tgam = (double2*)dalloc(c, (size_t)c->nk * c->n2 * 16);
+  c->tP = (double2*)dalloc(c, psz);
+  const size_t np = (size_t)2 * c->nw * c->nk + 8;
+  c->tpart = (double*)dalloc(c, (np > 1224 ? np : 1224) * 8);   // Dyson-tangent traces / inner-product partials
+  if (!c->tGiw || !c->tGtau || !c->tS || !c->tgam || !c->tP || !c->tpart) return fail(c, GW_ERR_OOM, "tangent buffers");
+  return GW_OK;
+}
+
+// One tangent of the self-consistency map F: (Sigma_inf, Sigma(i w)) -> (Sigma_inf', Sigma'(i w))
+// at the context's state (G from gw_dyson at this Sigma, P~ from gw_screened at this G).
+static gw_status sc_jvp(gw_ctx* c, const double2* dSinf, const double2* dSiw, double2* oSinf, double2* oSiw) {
   gwadj::View v;
   gw_status s = adj_view(c, &v);
+  if (s == GW_OK) s = sc_tangent_buffers(c);
   if (s != GW_OK) return s;
-  int64_t l = 0;
-  CK(gwadj::selfenergy_jvp(v, (const double2*)dG, (const double2*)dP_tau, (double2*)dS_tau, &l));
-  count((int)l);
+  const int nao = c->nao, nk = c->nk, nw = c->nw;
+  const int64_t n2 = c->n2, nsys = (int64_t)nw * nk, gstep = (int64_t)nk * n2;
+  // Dyson: dG(i w) = G D G - dmu G S G, D = dSigma_inf + dSigma(i w)
+  CK(dyson_tangent_rhs(dSinf, dSiw, v.bufA, nk, n2, nw, c->st));
+  GettDesc d = base_desc(nao, nao, nao, nsys);
+  d.am = I1(nao); d.ak = I1(1); d.az = I1(n2);
+  d.bk = I1(nao); d.bn = I1(1); d.bz = I1(n2);
+  d.cm = I1(nao); d.cn = I1(1); d.cz = I1(n2);
+  CK(run_gett(d, c->G_iw, Ty::C128, v.bufA, Ty::C128, v.bufB, Ty::C128, Ty::C128, c));   // G D
+  CK(run_gett(d, v.bufB, Ty::C128, c->G_iw, Ty::C128, v.bufA, Ty::C128, Ty::C128, c));   // (G D) G
+  GettDesc ds = d;
+  ds.bz = I2(nk, 0, n2);   // S^k for system (w, k)
+  CK(run_gett(ds, c->G_iw, Ty::C128, c->S, Ty::C128, v.bufB, Ty::C128, Ty::C128, c));    // G S
+  CK(run_gett(d, v.bufB, Ty::C128, c->G_iw, Ty::C128, v.bufC, Ty::C128, Ty::C128, c));   // (G S) G
+  CK(dyson_tangent_finish(v.bufA, v.bufC, c->S, c->r, nao, nk, nw, c->tpart, c->tpart + 2 * nsys, c->tGiw, c->st));
+  count(4);
+  // dG(tau) = TBf dG(i w), symmetrised
+  CK(transform(c, c->TBf, c->tGiw, c->tGtau, c->ntau, gstep, 1, 0, 0));
+  CK(herm_batched(c->tGtau, nao, (int64_t)c->ntau * nk, n2, c->st));
+  count(1);
+  // dSigma_inf' = J[dgamma] + K[dgamma]
+  if ((s = hf_core(c, c->tGtau, c->tgam, oSinf)) != GW_OK) return s;
+  // dP~0, then dP~ through the screened block (in place), then dSigma~
+  if ((s = polar_chain(c, c->tGtau, c->G_tau, c->tP, false)) != GW_OK) return s;
+  if ((s = polar_chain(c, c->G_tau, c->tGtau, c->tP, true)) != GW_OK) return s;
+  CK(herm_batched(c->tP, c->naux, (int64_t)nk * c->ntau, c->na2, c->st));
+  count(1);
+  if ((s = gw_screened_jvp(c, (const double*)c->tP, (double*)c->tP)) != GW_OK) return s;
+  if ((s = sigma_chain(c, c->tGtau, c->P_tau, c->tS, false)) != GW_OK) return s;
+  if ((s = sigma_chain(c, c->G_tau, c->tP, c->tS, true)) != GW_OK) return s;
+  if ((s = tc_check(c)) != GW_OK) return s;
+  CK(herm_batched(c->tS, nao, (int64_t)c->ntau * nk, n2, c->st));
+  count(1);
+  // dSigma'(i w) = TFf dSigma~(tau)
+  CK(transform(c, c->TFf, c->tS, oSiw, nw, gstep, 1, 0, 0));
+  return GW_OK;
+}
+
+extern "C" gw_status gw_sc_jvp(gw_ctx* c, const double* dSinf, const double* dSiw, double* oSinf, double* oSiw) {
+  if (!c || !dSinf || !dSiw || !oSinf || !oSiw) return fail(c, GW_ERR_ARG, "null argument");
+  if (!c->have_G || !c->have_mu) return fail(c, GW_ERR_STATE, "no Dyson solution yet");
+  if (!c->have_P) return fail(c, GW_ERR_STATE, "no screened interaction yet");
+  return sc_jvp(c, (const double2*)dSinf, (const double2*)dSiw, (double2*)oSinf, (double2*)oSiw);
+}
+
+// ------------------------------------------------------------------ Newton-Krylov iterations (A10)
+
+static gw_status rdot(gw_ctx* c, const double2* a, const double2* b, int64_t n, double* out) {
+  const int nb = rdot_blocks(n);
+  CK(rdot_partials(a, b, n, c->tpart, c->st));
+  double acc = 0;
+  std::vector<double> h((size_t)nb);
+  CK(cudaMemcpyAsync(h.data(), c->tpart, (size_t)nb * 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int i = 0; i < nb; ++i) acc += h[(size_t)i];
+  *out = acc;
+  count(1);
+  return GW_OK;
+}
+
+// The forward map at the current Sigma: Dyson (mu search), P~0, screened, Sigma_inf'
+// and Sigma'(i w) (unmixed) into Sinf_new / Siw_new.
+static gw_status sc_forward(gw_ctx* c) {
+  gw_status s;
+  if ((s = gw_dyson(c, nullptr)) != GW_OK) return s;
+  if ((s = gw_polarization(c)) != GW_OK) return s;
+  if ((s = gw_screened(c)) != GW_OK) return s;
+  if ((s = hf_core(c, c->G_tau, c->gamma, c->Sinf_new)) != GW_OK) return s;
+  return sigma_dynamic(c);
+}
+
+extern "C" gw_status gw_iterate_newton(gw_ctx* c, int32_t n_outer, int32_t m, double tol, double* res_out) {
+  if (!c || n_outer < 0 || m < 1 || m > 64) return fail(c, GW_ERR_ARG, "bad Newton-Krylov arguments");
+  gw_status s = sc_tangent_buffers(c);
+  if (s != GW_OK) return s;
+  gwadj::View v;
+  if ((s = adj_view(c, &v)) != GW_OK) return s;
+  const int64_t ki = (int64_t)c->nk * c->n2, nx = ki + (int64_t)c->nw * ki;
+  if (c->nvec < m + 2) {
+    c->kry.clear();
+    for (int i = 0; i < m + 2; ++i) {
+      double2* p = (double2*)dalloc(c, (size_t)nx * 16);
+      if (!p) return fail(c, GW_ERR_OOM, "Krylov basis");
+      c->kry.push_back(p);
+    }
+    c->nvec = m + 2;
+  }
+  double2* R = c->kry[(size_t)m + 1];   // residual F(x) - x
+  for (int it = 0; it < n_outer; ++it) {
+    if ((s = sc_forward(c)) != GW_OK) return s;
+    // R = F(x) - x
+    CK(cudaMemcpyAsync(R, c->Sinf_new, (size_t)ki * 16, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(R + ki, c->Siw_new, (size_t)(nx - ki) * 16, cudaMemcpyDeviceToDevice, c->st));
+    CK(axpby(R, c->Sinf, -1.0, 1.0, ki, c->st));
+    CK(axpby(R + ki, c->Siw, -1.0, 1.0, nx - ki, c->st));
+    count(2);
+    double rr = 0;
+    if ((s = rdot(c, R, R, nx, &rr)) != GW_OK) return s;
+    const double beta = std::sqrt(rr);
+    if (res_out) res_out[it] = beta;
+    if (beta <= tol) { for (int j = it + 1; j < n_outer; ++j) if (res_out) res_out[j] = beta; break; }
+    // GMRES on (J - I) delta = -R: v0 = -R / beta
+    std::vector<double> H((size_t)(m + 1) * m, 0.0);
+    CK(cudaMemsetAsync(c->kry[0], 0, (size_t)nx * 16, c->st));
+    CK(axpby(c->kry[0], R, -1.0 / beta, 0.0, nx, c->st));
+    int used = 0;
+    for (int j = 0; j < m; ++j) {
+      double2* w = c->kry[(size_t)j + 1];
+      if ((s = sc_jvp(c, c->kry[(size_t)j], c->kry[(size_t)j] + ki, w, w + ki)) != GW_OK) return s;
+      CK(axpby(w, c->kry[(size_t)j], -1.0, 1.0, nx, c->st));   // (J - I) v_j
+      for (int i = 0; i <= j; ++i) {   // modified Gram-Schmidt
+        double h = 0;
+        if ((s = rdot(c, w, c->kry[(size_t)i], nx, &h)) != GW_OK) return s;
+        H[(size_t)i * m + j] = h;
+        CK(axpby(w, c->kry[(size_t)i], -h, 1.0, nx, c->st));
+      }
+      double hn = 0;
+      if ((s = rdot(c, w, w, nx, &hn)) != GW_OK) return s;
+      hn = std::sqrt(hn);
+      H[(size_t)(j + 1) * m + j] = hn;
+      used = j + 1;
+      if (hn <= 1e-14 * beta) break;
+      CK(axpby(w, w, 0.0, 1.0 / hn, nx, c->st));
+    }
+    // least squares min || beta e1 - H y || by Givens rotations (host, used <= 64)
+    std::vector<double> g((size_t)used + 1, 0.0), y((size_t)used, 0.0);
+    g[0] = beta;
+    std::vector<double> Hc = H;
+    for (int j = 0; j < used; ++j) {
+      const double a = Hc[(size_t)j * m + j], b = Hc[(size_t)(j + 1) * m + j];
+      const double rho = std::sqrt(a * a + b * b);
+      const double cs = rho > 0 ? a / rho : 1.0, sn = rho > 0 ? b / rho : 0.0;
+      for (int k = j; k < used; ++k) {
+        const double u = Hc[(size_t)j * m + k], t = Hc[(size_t)(j + 1) * m + k];
+        Hc[(size_t)j * m + k] = cs * u + sn * t;
+        Hc[(size_t)(j + 1) * m + k] = -sn * u + cs * t;
+      }
+      const double gj = g[(size_t)j];
+      g[(size_t)j] = cs * gj;
+      g[(size_t)j + 1] = -sn * gj;
+    }
+    for (int j = used - 1; j >= 0; --j) {
+      double t = g[(size_t)j];
+      for (int k = j + 1; k < used; ++k) t -= Hc[(size_t)j * m + k] * y[(size_t)k];
+      const double dgl = Hc[(size_t)j * m + j];
+      y[(size_t)j] = dgl != 0.0 ? t / dgl : 0.0;
+    }
+    // x <- x + sum y_j v_j  (x lives in Sinf / Siw)
+    for (int j = 0; j < used; ++j) {
+      CK(axpby(c->Sinf, c->kry[(size_t)j], y[(size_t)j], 1.0, ki, c->st));
+      CK(axpby(c->Siw, c->kry[(size_t)j] + ki, y[(size_t)j], 1.0, nx - ki, c->st));
+    }
+    count(2 * used);
+    c->have_sigma = true;
+  }
+  // leave the context at a consistent state: G from the final Sigma
+  if ((s = gw_dyson(c, nullptr)) != GW_OK) return s;
+  c->have_P0 = false;
+  c->have_P = false;
   return GW_OK;
 }
 

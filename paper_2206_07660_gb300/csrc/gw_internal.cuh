@@ -77,6 +77,12 @@ struct MuState {
   int phase, iter, maxit, done, status;
 };
 cudaError_t mu_step(MuState* s, const double* partial, int64_t count, double scale, cudaStream_t st);
+cudaError_t dyson_tangent_rhs(const double2* dSinf, const double2* dSiw, double2* D, int64_t nk, int64_t n2,
+                              int64_t nw, cudaStream_t st);
+cudaError_t dyson_tangent_finish(const double2* X, const double2* Y, const double2* S, const double2* r, int nao,
+                                 int nk, int nw, double* part, double* dmu, double2* dG, cudaStream_t st);
+int rdot_blocks(int64_t n);
+cudaError_t rdot_partials(const double2* a, const double2* b, int64_t n, double* part, cudaStream_t st);
 size_t dyson_smem(int nao, int nt);
 cudaError_t mu_init_device(MuState* s, double target, double tol, double width, int maxit, cudaStream_t st);
 

@@ -151,4 +151,123 @@ cudaError_t mu_step(MuState* s, const double* partial, int64_t count, double sca
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Dyson tangent
+// G = [(i w + mu) S - H0 - Sigma_inf - Sigma(i w)]^-1 at the electron count N(mu) = N_e:
+//   dG = G (dSigma_inf + dSigma(i w)) G - dmu G S G,
+//   dmu = Re sum r_n tr[G D G S] / Re sum r_n tr[G S G S]   (so that dN = 0).
+// The products run on the contraction kernel; these kernels form D, the weighted
+// traces, dmu and the combination.
+
+// D[w][k] = dSinf[k] + dSiw[w][k]
+__global__ void dyson_tangent_rhs_kernel(const double2* __restrict__ dSinf, const double2* __restrict__ dSiw,
+                                         double2* __restrict__ D, int64_t nk, int64_t n2, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = (e / n2) % nk, i = e % n2;
+    const double2 a = dSinf[k * n2 + i], b = dSiw[e];
+    D[e] = make_double2(a.x + b.x, a.y + b.y);
+  }
+}
+
+// part[sys] = Re(r_w tr(X_sys S_k)), part[nsys + sys] = Re(r_w tr(Y_sys S_k)); one block per system
+__global__ void __launch_bounds__(256) dyson_tangent_trace_kernel(const double2* __restrict__ X,
+                                                                  const double2* __restrict__ Y,
+                                                                  const double2* __restrict__ S,
+                                                                  const double2* __restrict__ r, int nao, int nk,
+                                                                  int64_t nsys, double* part) {
+  __shared__ double red[4][256];
+  const int64_t n2 = (int64_t)nao * nao;
+  for (int64_t sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
+    const int w = (int)(sys / nk), k = (int)(sys - (int64_t)w * nk);
+    const double2* x = X + sys * n2;
+    const double2* y = Y + sys * n2;
+    const double2* s = S + (int64_t)k * n2;
+    double xr = 0, xi = 0, yr = 0, yi = 0;
+    for (int64_t e = threadIdx.x; e < n2; e += blockDim.x) {
+      const int64_t i = e / nao, j = e - i * nao;
+      const double2 sv = s[j * nao + i], a = x[e], b = y[e];
+      xr += a.x * sv.x - a.y * sv.y; xi += a.x * sv.y + a.y * sv.x;
+      yr += b.x * sv.x - b.y * sv.y; yi += b.x * sv.y + b.y * sv.x;
+    }
+    red[0][threadIdx.x] = xr; red[1][threadIdx.x] = xi; red[2][threadIdx.x] = yr; red[3][threadIdx.x] = yi;
+    __syncthreads();
+    for (int t = blockDim.x / 2; t > 0; t >>= 1) {
+      if ((int)threadIdx.x < t)
+        for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + t];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double2 rw = r[w];
+      part[sys] = rw.x * red[0][0] - rw.y * red[1][0];
+      part[nsys + sys] = rw.x * red[2][0] - rw.y * red[3][0];
+    }
+    __syncthreads();
+  }
+}
+
+// dmu = sum part[0:nsys] / sum part[nsys:2 nsys], in a fixed order
+__global__ void __launch_bounds__(1024) dyson_tangent_dmu_kernel(const double* part, int64_t nsys, double* dmu) {
+  __shared__ double ra[1024], rb[1024];
+  double a = 0, b = 0;
+  for (int64_t i = threadIdx.x; i < nsys; i += blockDim.x) { a += part[i]; b += part[nsys + i]; }
+  ra[threadIdx.x] = a; rb[threadIdx.x] = b;
+  __syncthreads();
+  for (int t = blockDim.x / 2; t > 0; t >>= 1) {
+    if ((int)threadIdx.x < t) { ra[threadIdx.x] += ra[threadIdx.x + t]; rb[threadIdx.x] += rb[threadIdx.x + t]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *dmu = rb[0] != 0.0 ? ra[0] / rb[0] : 0.0;
+}
+
+// dG = X - dmu Y
+__global__ void dyson_tangent_combine_kernel(const double2* __restrict__ X, const double2* __restrict__ Y,
+                                             const double* dmu, double2* __restrict__ dG, int64_t total) {
+  const double m = *dmu;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 x = X[e], y = Y[e];
+    dG[e] = make_double2(x.x - m * y.x, x.y - m * y.y);
+  }
+}
+
+static inline int nblk_(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 152 * 16 ? b : 152 * 16); }
+
+cudaError_t dyson_tangent_rhs(const double2* dSinf, const double2* dSiw, double2* D, int64_t nk, int64_t n2,
+                              int64_t nw, cudaStream_t st) {
+  const int64_t total = nw * nk * n2;
+  dyson_tangent_rhs_kernel<<<nblk_(total), 256, 0, st>>>(dSinf, dSiw, D, nk, n2, total);
+  return cudaGetLastError();
+}
+
+cudaError_t dyson_tangent_finish(const double2* X, const double2* Y, const double2* S, const double2* r, int nao,
+                                 int nk, int nw, double* part, double* dmu, double2* dG, cudaStream_t st) {
+  const int64_t nsys = (int64_t)nw * nk, total = nsys * nao * nao;
+  dyson_tangent_trace_kernel<<<(int)(nsys < 152 * 8 ? nsys : 152 * 8), 256, 0, st>>>(X, Y, S, r, nao, nk, nsys, part);
+  dyson_tangent_dmu_kernel<<<1, 1024, 0, st>>>(part, nsys, dmu);
+  dyson_tangent_combine_kernel<<<nblk_(total), 256, 0, st>>>(X, Y, dmu, dG, total);
+  return cudaGetLastError();
+}
+
+// Real inner product sum_e (a_e.x b_e.x + a_e.y b_e.y) as per-block partials (count
+// <= 1216 blocks); the host adds them in order.
+__global__ void __launch_bounds__(256) rdot_kernel(const double2* __restrict__ a, const double2* __restrict__ b,
+                                                   int64_t n, double* part) {
+  __shared__ double red[256];
+  double s = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s += a[e].x * b[e].x + a[e].y * b[e].y;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int t = blockDim.x / 2; t > 0; t >>= 1) {
+    if ((int)threadIdx.x < t) red[threadIdx.x] += red[threadIdx.x + t];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+int rdot_blocks(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1216 ? b : 1216); }
+
+cudaError_t rdot_partials(const double2* a, const double2* b, int64_t n, double* part, cudaStream_t st) {
+  rdot_kernel<<<rdot_blocks(n), 256, 0, st>>>(a, b, n, part);
+  return cudaGetLastError();
+}
+
 }  // namespace gwk

@@ -47,12 +47,11 @@ __device__ __forceinline__ int em_exponent(double m) {
   return e;
 }
 
-// Operand digits from a transposed source: row n of the operand is column n of a
-// K x ncol complex matrix (element (n, k) at src[z*zs + k*ld + n]).  A style: one
-// real row (re, im interleaved along 2k + c); B style (B_STYLE): rows 2n = (Br, -Bi)
-// and 2n+1 = (Bi, Br) of the real 2x2 blocks of C = A B^T, digit planes in reverse
-// order.  Padding columns [2K, Kp) are written as zeros.  Block: 32 rows x all K.
-template <bool B_STYLE>
+// A-operand digits from a transposed source: row n of the operand is column n of a
+// K x ncol complex matrix (element (n, k) at src[z*zs + k*ld + n]), real K index
+// 2k + c (re, im).  Padding columns [2K, Kp) are written as zeros.  Block: 32 rows x
+// all K; the source tile goes through shared memory so both the reads (along n)
+// and the digit writes (along k) are coalesced.
 __global__ void __launch_bounds__(256) em_split_t_kernel(const double2* __restrict__ src, int64_t K, int64_t ncol,
                                                          int64_t ld, int64_t zs, float* __restrict__ dig,
                                                          int* __restrict__ ex, int64_t Kp) {
@@ -62,8 +61,7 @@ __global__ void __launch_bounds__(256) em_split_t_kernel(const double2* __restri
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t z = blockIdx.y;
   const double2* X = src + z * zs;
-  const int64_t rows_out = B_STYLE ? 2 * ncol : ncol;
-  float* D = dig + z * rows_out * (int64_t)EM_S * Kp;
+  float* D = dig + z * ncol * (int64_t)EM_S * Kp;
   int* E = ex + z * ncol;
   const int64_t n0 = (int64_t)blockIdx.x * 32;
   const int64_t n = n0 + tx;
@@ -98,20 +96,9 @@ __global__ void __launch_bounds__(256) em_split_t_kernel(const double2* __restri
         float dr[EM_S], di[EM_S];
         em_digits(v.x, es[rr], dr);
         em_digits(v.y, es[rr], di);
-        if (!B_STYLE) {
-          float* o = D + row * rowlen + 2 * j;
+        float* o = D + row * rowlen + 2 * j;
 #pragma unroll
-          for (int i = 0; i < EM_S; ++i) *(float2*)(o + (int64_t)i * Kp) = make_float2(dr[i], di[i]);
-        } else {
-          float* r0 = D + (2 * row) * rowlen + 2 * j;
-          float* r1 = D + (2 * row + 1) * rowlen + 2 * j;
-#pragma unroll
-          for (int i = 0; i < EM_S; ++i) {
-            const int64_t p = (int64_t)(EM_S - 1 - i) * Kp;
-            *(float2*)(r0 + p) = make_float2(dr[i], -di[i]);
-            *(float2*)(r1 + p) = make_float2(di[i], dr[i]);
-          }
-        }
+        for (int i = 0; i < EM_S; ++i) *(float2*)(o + (int64_t)i * Kp) = make_float2(dr[i], di[i]);
       }
     }
     __syncthreads();
@@ -175,7 +162,7 @@ cudaError_t emul_transform(const float* Bd, const int* Be, int64_t nrow, const d
                            int64_t ldx, double2* Y, int64_t ldy, float* Ad, int* Ae, int* err, cudaStream_t st) {
   if (ldy != ncol) return cudaErrorInvalidValue;   // transposed lane-per-row stores assume packed rows
   const int64_t Kp = emul_kpad(K);
-  em_split_t_kernel<false><<<dim3((unsigned)((ncol + 31) / 32), 1), 256, 0, st>>>(X, K, ncol, ldx, 0, Ad, Ae, Kp);
+  em_split_t_kernel<<<dim3((unsigned)((ncol + 31) / 32), 1), 256, 0, st>>>(X, K, ncol, ldx, 0, Ad, Ae, Kp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t ld = (int64_t)EM_S * Kp;

@@ -79,6 +79,9 @@ def load():
     lib.gw_polarization_jvp.argtypes = [P, P, P]
     lib.gw_screened_jvp.argtypes = [P, P, P]
     lib.gw_selfenergy_jvp.argtypes = [P, P, P, P]
+    lib.gw_sc_jvp.argtypes = [P, P, P, P, P]
+    lib.gw_iterate_newton.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_double)]
     lib.gw_profile.argtypes = [P, ctypes.c_int]
     lib.gw_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.gw_kernel_launches.argtypes = [P]
@@ -86,7 +89,8 @@ def load():
     for name in ("gw_init", "gw_destroy", "gw_set", "gw_get", "gw_hf", "gw_polarization", "gw_screened",
                  "gw_selfenergy", "gw_dyson", "gw_iterate", "gw_reset_sigma", "gw_profile", "gw_profile_read",
                  "gw_polarization_vjp", "gw_selfenergy_vjp", "gw_iterate_graph", "gw_batch_iterate",
-                 "gw_polarization_jvp", "gw_screened_jvp", "gw_selfenergy_jvp"):
+                 "gw_polarization_jvp", "gw_screened_jvp", "gw_selfenergy_jvp", "gw_sc_jvp",
+                 "gw_iterate_newton"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -305,6 +309,21 @@ class GW:
         dS = torch.empty(self.shape_of("Sigma_tau"), dtype=torch.complex128, device=dG.device)
         self._check(self.lib.gw_selfenergy_jvp(self.ctx, dG.data_ptr(), dP.data_ptr(), dS.data_ptr()))
         return dS
+
+    def sc_jvp(self, dSinf, dSiw):
+        """Tangent of the self-consistency map (Sigma_inf, Sigma(i w)) -> (Sigma_inf', Sigma'(i w))."""
+        torch = self.torch
+        dSinf, dSiw = dSinf.contiguous(), dSiw.contiguous()
+        oi = torch.empty(self.shape_of("Sigma_inf"), dtype=torch.complex128, device=dSiw.device)
+        ow = torch.empty(self.shape_of("Sigma_iw"), dtype=torch.complex128, device=dSiw.device)
+        self._check(self.lib.gw_sc_jvp(self.ctx, dSinf.data_ptr(), dSiw.data_ptr(), oi.data_ptr(), ow.data_ptr()))
+        return oi, ow
+
+    def iterate_newton(self, n_outer, m=8, tol=1e-10):
+        """Newton-Krylov self-consistency; returns the residual norm of each step."""
+        res = (ctypes.c_double * max(1, int(n_outer)))()
+        self._check(self.lib.gw_iterate_newton(self.ctx, int(n_outer), int(m), float(tol), res))
+        return [float(x) for x in res][:int(n_outer)]
 
     def profile(self, enable=True):
         self._check(self.lib.gw_profile(self.ctx, int(bool(enable))))

@@ -52,3 +52,12 @@ def test_header_entry_points_documented():
         # every entry point is preceded by a comment block
         i = txt.rindex(n + "(")
         assert "*/" in txt[max(0, i - 2000):i], n
+
+
+def test_library_resolves_every_symbol_at_load():
+    """Loading with immediate binding fails on any undefined internal symbol
+    (a function declared in a header but defined outside its namespace)."""
+    import ctypes
+    import os
+    from paper_2206_07660_gb300.gw import LIB_PATH
+    ctypes.CDLL(LIB_PATH, mode=os.RTLD_NOW)

@@ -81,3 +81,27 @@ def test_screened_jvp(nao, naux, kmesh, ntau):
     got = g.screened_jvp(torch.from_numpy(dP0).cuda()).cpu().numpy()
     scale = np.abs(fd[5e-5]).max()
     assert np.abs(got - fd[5e-5]).max() <= 4 * err_fd + 1e-10 * scale
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_tf32"])
+def test_mixed_precision_tangents(precision):
+    # the tangents run the forward chains of the context's precision: complex64-level
+    # agreement with the oracle's central differences
+    import torch
+    nao, naux, kmesh, ntau = 6, 20, (2, 2, 1), 10
+    sysd = system(nao, naux, kmesh, ntau, 40.0, 53)
+    km = ogw.KMesh(kmesh)
+    G = hermitian_noise((ntau, km.nk, nao, nao), 0.2, 8)
+    P = hermitian_noise((km.nk, ntau, naux, naux), 0.2, 9)
+    dG, dP = _noise(G.shape, 10), _noise(P.shape, 11)
+    h = 1e-3
+    V = sysd["V"]
+    refP = (ogw.polarization_tau(V, G + h * dG, km) - ogw.polarization_tau(V, G - h * dG, km)) / (2 * h)
+    refS = (ogw.selfenergy_tau(V, G + h * dG, P + h * dP, km) - ogw.selfenergy_tau(V, G - h * dG, P - h * dP, km)) / (2 * h)
+    g = gpu(sysd, precision=precision)
+    g.set("G_tau", G)
+    g.set("P_tau", P)
+    gotP = g.polarization_jvp(torch.from_numpy(dG).cuda()).cpu().numpy()
+    gotS = g.selfenergy_jvp(torch.from_numpy(dG).cuda(), torch.from_numpy(dP).cuda()).cpu().numpy()
+    assert rel(gotP, refP) < 2e-5
+    assert rel(gotS, refS) < 2e-5
