@@ -61,6 +61,7 @@ struct UmmaArgs {
   int ksplit;          // K range split over blockIdx.z; partial results are added atomically
   int direct;          // persistent kernel: transposed complex output stored lane-per-row (see umma_gemm)
   int chunk_len;       // persistent kernel: k-blocks accumulated in TMEM before the FP32 register sums
+  int prefetch;        // persistent kernel: stages ahead of the pipeline whose tiles are prefetched into L2
   // fp64 output only: D[m][n] is scaled by 2^(eA[m] + eB[n/2] + eshift) (emulated FP64 products)
   const int* eA;
   const int* eB;
@@ -98,6 +99,12 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
       ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
+}
+// L2 prefetch of one tile (no shared-memory destination, no barrier)
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)map), "r"(c0),
+               "r"(c1), "r"(c2)
+               : "memory");
 }
 __device__ __forceinline__ uint64_t sw128_desc(const void* p) {
   uint64_t a = smem_u32(p);
@@ -323,6 +330,7 @@ struct UpCfg {
 // two stages measured 8% faster than one at the same 7e-7 relative error, four
 // stages 11% faster at 1.1e-6)
 static int g_chunk_len = 2;
+static int g_prefetch = 0;   // L2 prefetch distance in stages (0: off)
 
 // Writes one 32 x 32 block of a finished tile: lane l holds the row sums of
 // output row r0 + l in stg[l * 33 + j] (j = column - c0).  Rows are written
@@ -491,6 +499,21 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           const uint32_t ph = (g / NS) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); ok = false; break; }
           uint8_t* st = sStage + s * Cf::STAGE;
+          if (a.prefetch > 0) {   // warm L2 with the operand tiles a few stages ahead
+            const int itp = it + a.prefetch;
+            if (itp < nst) {
+              const int kbp = three ? kb0 + itp : kb0 + 2 * itp;
+              tma_prefetch_3d(&tA0, kbp * UM_BK, m0, za);
+              tma_prefetch_3d(&tB0, kbp * UM_BK, n0, zb);
+              if (three) {
+                tma_prefetch_3d(&tA1, kbp * UM_BK, m0, za);
+                tma_prefetch_3d(&tB1, kbp * UM_BK, n0, zb);
+              } else if (2 * itp + 1 < nkb) {
+                tma_prefetch_3d(&tA0, (kbp + 1) * UM_BK, m0, za);
+                tma_prefetch_3d(&tB0, (kbp + 1) * UM_BK, n0, zb);
+              }
+            }
+          }
           if (three) {
             const int kb = kb0 + it;
             mbar_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
@@ -929,6 +952,7 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
               ((uintptr_t)C % (c_fp64 ? 16 : 8)) == 0 && ((uintptr_t)C_lo % 8) == 0) ? 1 : 0;
   a.err = err;
   a.chunk_len = nseg == 3 ? g_chunk_len : UM_FLUSH;
+  a.prefetch = g_prefetch;
   if (scale) {
     if (!c_fp64 || !g_persistent) return cudaErrorInvalidValue;
     a.eA = scale->eA; a.eB = scale->eB; a.ea_zs = scale->ea_zs; a.eb_zs = scale->eb_zs; a.eshift = scale->eshift;
@@ -1141,6 +1165,13 @@ extern "C" int gwdbg_umma_set_chunk(int k) {
   return old;
 }
 
+// Sets the L2 prefetch distance (stages) of the persistent kernel; returns the old value.
+extern "C" int gwdbg_umma_set_prefetch(int k) {
+  const int old = gwk::g_prefetch;
+  if (k >= 0 && k <= 32) gwk::g_prefetch = k;
+  return old;
+}
+
 // Turns the N-tile autotuner of the persistent kernel on (1, the default) or off
 // (0: cost model only); returns the previous setting.  Cached choices are kept.
 extern "C" int gwdbg_umma_set_autotune(int on) {
@@ -1204,8 +1235,17 @@ extern "C" int gwdbg_umma_cgemm_split(const double2* A, const double2* B, int M,
   return e ? (int)e : herr;
 }
 
+// pseudo-random TF32-valued fill in [-1, 1) (integer hash of the index)
+__global__ void gwdbg_fill_kernel(float* x, int64_t n, uint32_t seed) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)e * 2654435761u ^ seed;
+    h ^= h >> 15; h *= 2246822519u; h ^= h >> 13; h *= 3266489917u; h ^= h >> 16;
+    x[e] = __uint_as_float(__float_as_uint((float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f) & 0xffffe000u);
+  }
+}
+
 // Times `iters` launches of the split-TF32 GEMM on operands of the given shape
-// (contents arbitrary); *ms receives the mean device time per launch.
+// (pseudo-random contents); *ms receives the mean device time per launch.
 extern "C" int gwdbg_umma_bench(int M, int N, int Kpad, int batch, int c_fp64, int iters, double* ms) {
   using namespace gwk;
   float *ah, *bh;
@@ -1214,7 +1254,9 @@ extern "C" int gwdbg_umma_bench(int M, int N, int Kpad, int batch, int c_fp64, i
   size_t asz = (size_t)M * Kpad * 4 * batch, bsz = (size_t)N * Kpad * 4;
   if (cudaMalloc(&ah, asz) || cudaMalloc(&bh, bsz) || cudaMalloc(&C, (size_t)M * N * 8 * batch) || cudaMalloc(&err, 4))
     return -1;
-  cudaMemset(ah, 0, asz); cudaMemset(bh, 0, bsz); cudaMemset(C, 0, (size_t)M * N * 8 * batch); cudaMemset(err, 0, 4);
+  gwdbg_fill_kernel<<<1216, 256>>>(ah, (int64_t)(asz / 4), 12345u);
+  gwdbg_fill_kernel<<<1216, 256>>>(bh, (int64_t)(bsz / 4), 67890u);
+  cudaMemset(C, 0, (size_t)M * N * 8 * batch); cudaMemset(err, 0, 4);
   UmmaOperand oa{ah, ah, M, batch, Kpad, (int64_t)M * Kpad}, ob{bh, bh, N, 1, Kpad, 0};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0); cudaEventCreate(&e1);
