@@ -30,6 +30,7 @@
 #include "gw_internal.cuh"
 
 #include <map>
+#include <vector>
 #include <mutex>
 
 namespace gwk {
@@ -331,6 +332,8 @@ struct UpCfg {
 // stages 11% faster at 1.1e-6)
 static int g_chunk_len = 2;
 static int g_prefetch = 0;   // L2 prefetch distance in stages (0: off)
+static int g_wide = 1;       // autotuner may pick N tiles of 192..256 (one epilogue group of 8 warps)
+static int g_force_bn = 0;   // test hook: nonzero forces this N tile (no tuning)
 
 // Writes one 32 x 32 block of a finished tile: lane l holds the row sums of
 // output row r0 + l in stg[l * 33 + j] (j = column - c0).  Rows are written
@@ -434,11 +437,19 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
     umma_pkernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                  const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, UmmaArgs a,
                  int ntn, int ntm, int ntiles) {
-  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "N tile");
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "N tile");
+  // BN <= 128: two epilogue groups of 4 warps take alternate tiles (ping-pong).
+  // BN > 128 ("wide"): one group of 8 warps, two per TMEM lane quarter, each owning
+  // half of the tile's columns; TMEM holds its two chunk buffers.
+  constexpr bool WIDE = BN > 128;
+  static_assert(!WIDE || (BN / 2) % 16 == 0, "wide tiles split into 16-column halves");
+  constexpr int NGRP = WIDE ? 1 : 2;
+  constexpr int BW = WIDE ? BN / 2 : BN;   // columns per epilogue warp
+  constexpr uint32_t ACCE_COUNT = WIDE ? 8 : 4;
   using Cf = UpCfg<BN>;
   constexpr uint32_t A_BYTES = Cf::A_BYTES, B_BYTES = Cf::B_BYTES;
   constexpr int NS = Cf::STAGES;
-  constexpr uint32_t NEED = 4 * BN;   // 2 groups x 2 chunk buffers
+  constexpr uint32_t NEED = NGRP * 2 * BN;   // groups x 2 chunk buffers
   constexpr uint32_t TMEM_COLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -458,7 +469,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 4; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
+    for (int b = 0; b < 4; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], ACCE_COUNT); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         if (*(volatile int*)&s_fail) break;
         int n0, m0, z, kb0, nkb;
         decode(t, n0, m0, z, kb0, nkb);
-        const int grp = li & 1;
+        const int grp = WIDE ? 0 : (li & 1);
         const bool three = a.nseg == 3;
         const int CL = a.chunk_len;
         const int nst = three ? nkb : (nkb + 1) / 2;
@@ -593,22 +604,23 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
       }
     }
   } else {
-    // epilogue group grp = 0 (warps 2..5) or 1 (warps 6..9) takes local tiles grp, grp+2, ...
-    const int grp = (warp - 2) >> 2;
+    // narrow: epilogue group grp = 0 (warps 2..5) or 1 (warps 6..9) takes local tiles
+    // grp, grp+2, ...;  wide: all 8 warps take every tile, warps 6..9 the upper columns
+    const int grp = WIDE ? 0 : (warp - 2) >> 2;
+    const int cbase = WIDE ? ((warp - 2) >> 2) * BW : 0;
     const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31 = tile rows
     float* stg = stage_all + (warp - 2) * 32 * 33;
     uint32_t cg = 0;
-    int li = grp;
-    for (int t = blockIdx.x + grp * gridDim.x; t < ntiles; t += 2 * gridDim.x, li += 2) {
+    for (int t = blockIdx.x + grp * gridDim.x; t < ntiles; t += NGRP * gridDim.x) {
       if (*(volatile int*)&s_fail) break;
       int n0, m0, z, kb0, nkb;
       decode(t, n0, m0, z, kb0, nkb);
       const int CL = a.chunk_len;
       const int nst = a.nseg == 3 ? nkb : (nkb + 1) / 2;
       const int nch = (nst + CL - 1) / CL;
-      float acc[BN];
+      float acc[BW];
 #pragma unroll
-      for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+      for (int j = 0; j < BW; ++j) acc[j] = 0.f;
       bool ok = true;
       int blast = 0;
       for (int c = 0; c < nch; ++c) {
@@ -618,14 +630,15 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         if (!mbar_wait(&accf[grp * 2 + b], u & 1u)) { atomicCAS(&s_fail, 0, 3); ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // GRP columns in flight per wait (fewer load round trips, within the register budget)
-        constexpr int GRP = BN >= 112 ? 16 : BN > 80 ? 32 : 64;
+        constexpr int GRP = BW >= 112 ? 16 : BW > 80 ? 32 : 64;
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += GRP) {
+        for (int c0 = 0; c0 < BW; c0 += GRP) {
           uint32_t r[GRP];
 #pragma unroll
           for (int q = 0; q < GRP; q += 16) {
-            if (c0 + q < BN) {
-              const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((grp * 2 + b) * BN + c0 + q);
+            if (c0 + q < BW) {
+              const uint32_t taddr =
+                  tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((grp * 2 + b) * BN + cbase + c0 + q);
               asm volatile(
                   "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                   : "=r"(r[q + 0]), "=r"(r[q + 1]), "=r"(r[q + 2]), "=r"(r[q + 3]), "=r"(r[q + 4]), "=r"(r[q + 5]),
@@ -637,7 +650,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int j = 0; j < GRP; ++j)
-            if (c0 + j < BN) acc[c0 + j] += __uint_as_float(r[j]);
+            if (c0 + j < BW) acc[c0 + j] += __uint_as_float(r[j]);
         }
         if (c + 1 < nch) {
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -654,9 +667,9 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
       // The finished row sums go back into the last chunk's TMEM buffer (released to
       // the MMA thread only after the write-out below), so that the register sums
       // are not live during the write-out.
-      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((grp * 2 + blast) * BN);
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((grp * 2 + blast) * BN + cbase);
 #pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      for (int c0 = 0; c0 < BW; c0 += 16) {
         asm volatile(
             "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
             ::"r"(tbase + (uint32_t)c0), "r"(__float_as_uint(acc[c0 + 0])), "r"(__float_as_uint(acc[c0 + 1])),
@@ -682,14 +695,14 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         const bool rok = row < a.M;
         float* C = (float*)a.C;
         const float al = (float)a.alpha;
-        for (int cb = 0; cb < BN; cb += 32) {
+        for (int cb = 0; cb < BW; cb += 32) {
           uint32_t v[32];
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
               : "r"(tbase + (uint32_t)cb));
-          if (cb + 16 < BN) {
+          if (cb + 16 < BW) {
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
@@ -703,8 +716,8 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
             const int rexp = a.eA ? a.eA[(int64_t)z * a.ea_zs + row] + a.eshift : 0;
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
-              const int n = n0 + cb + j;
-              if (cb + j < BN && n < a.N) {
+              const int n = n0 + cbase + cb + j;
+              if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
                 const int ex = a.eB ? rexp + a.eB[(int64_t)z * a.eb_zs + (n >> 1)] : rexp;
                 const double sre = ldexp(a.alpha * (double)__uint_as_float(v[j]), ex);
@@ -721,8 +734,8 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           } else if (rok) {
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
-              const int n = n0 + cb + j;
-              if (cb + j < BN && n < a.N) {
+              const int n = n0 + cbase + cb + j;
+              if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
                 const float re = al * __uint_as_float(v[j]), im = al * __uint_as_float(v[j + 1]);
                 if (a.C_lo) {
@@ -737,14 +750,14 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           }
         }
       } else if (m0 + quarter * 32 < a.M) {
-        for (int cb = 0; cb < BN; cb += 32) {
+        for (int cb = 0; cb < BW; cb += 32) {
           uint32_t v[32];
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
               : "r"(tbase + (uint32_t)cb));
-          if (cb + 16 < BN) {
+          if (cb + 16 < BW) {
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
@@ -756,7 +769,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
           __syncwarp();
-          umma_write_block(a, z, m0 + quarter * 32, n0 + cb, BN - cb, stg, lane);
+          umma_write_block(a, z, m0 + quarter * 32, n0 + cbase + cb, BW - cb, stg, lane);
           __syncwarp();
         }
       }
@@ -820,7 +833,7 @@ static int g_num_sms = 0;
 
 template <int BN>
 static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch, cudaStream_t st) {
-  if (g_persistent) {
+  if (g_persistent || BN > 128) {
     if (!g_num_sms) {
       int dev = 0;
       cudaGetDevice(&dev);
@@ -837,12 +850,15 @@ static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch,
     umma_pkernel<BN><<<grid, UP_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a, ntn, ntm, (int)ntiles);
     return cudaGetLastError();
   }
-  size_t sm = umma_smem<BN>();
-  cudaError_t e = cudaFuncSetAttribute(umma_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  dim3 grid((a.N + BN - 1) / BN, (a.M + UM_BM - 1) / UM_BM, batch * a.ksplit);
-  umma_kernel<BN><<<grid, UM_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a);
-  return cudaGetLastError();
+  if constexpr (BN <= 128) {
+    size_t sm = umma_smem<BN>();
+    cudaError_t e = cudaFuncSetAttribute(umma_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.N + BN - 1) / BN, (a.M + UM_BM - 1) / UM_BM, batch * a.ksplit);
+    umma_kernel<BN><<<grid, UM_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
 }
 
 // Builds the tensor maps for an N tile of `bn` columns and launches.
@@ -855,6 +871,9 @@ static cudaError_t umma_launch(int bn, const UmmaOperand& A, const UmmaOperand& 
       !make_map(&maps[3], nseg > 1 ? B.lo : B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn))
     return cudaErrorInvalidValue;
   switch (bn) {
+    case 256: return launch_bn<256>(maps, a, batch, st);
+    case 224: return launch_bn<224>(maps, a, batch, st);
+    case 192: return launch_bn<192>(maps, a, batch, st);
     case 128: return launch_bn<128>(maps, a, batch, st);
     case 112: return launch_bn<112>(maps, a, batch, st);
     case 96: return launch_bn<96>(maps, a, batch, st);
@@ -888,6 +907,7 @@ static std::map<TuneKey, int> g_tuned;
 static std::mutex g_tune_mu;
 static int g_autotune = 1;
 static const int kBnCand[] = {128, 112, 96, 80, 64, 48, 32};
+static const int kBnWide[] = {256, 224, 192};   // persistent kernel only, tried when N >= 192
 
 static int cost_model_bn(int N) {
   // trade the padding of the last tile against the per-tile cost of re-reading
@@ -911,7 +931,9 @@ static int tune_bn(const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int
   if (t.accumulate) t.alpha = 0.0;
   int best = fallback;
   float best_ms = 1e30f;
-  for (int cand : kBnCand) {
+  std::vector<int> cands(kBnCand, kBnCand + sizeof(kBnCand) / sizeof(int));
+  if (a.N >= 192 && g_wide) cands.insert(cands.begin(), kBnWide, kBnWide + sizeof(kBnWide) / sizeof(int));
+  for (int cand : cands) {
     if (umma_launch(cand, A, B, Kpad, nseg, t, batch, st) != cudaSuccess) continue;   // warm-up
     cudaEventRecord(e0, st);
     cudaError_t r = umma_launch(cand, A, B, Kpad, nseg, t, batch, st);
@@ -958,6 +980,7 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
     a.eA = scale->eA; a.eB = scale->eB; a.ea_zs = scale->ea_zs; a.eb_zs = scale->eb_zs; a.eshift = scale->eshift;
   }
   int bn = cost_model_bn(N);
+  if (g_force_bn) return umma_launch(g_force_bn, A, B, Kpad, nseg, a, batch, st);
   if (g_persistent && g_autotune) {
     const TuneKey key{M, N, batch, nseg, ksplit,
                       (c_fp64 ? 1 : 0) | (accumulate ? 2 : 0) | (a.direct ? 4 : 0) | (C_lo ? 8 : 0) |
@@ -1163,6 +1186,27 @@ extern "C" int gwdbg_umma_set_chunk(int k) {
   const int old = gwk::g_chunk_len;
   if (k >= 1 && k <= 16) gwk::g_chunk_len = k;
   return old;
+}
+
+// Allows (1) or forbids (0) the wide N tiles (192..256 columns) in the autotuner;
+// returns the old value.  Cached choices are kept.
+extern "C" int gwdbg_umma_set_wide(int on) {
+  const int old = gwk::g_wide;
+  gwk::g_wide = on ? 1 : 0;
+  return old;
+}
+
+// Forces the N tile of every later GEMM (0: back to the autotuner); returns the old value.
+extern "C" int gwdbg_umma_force_bn(int bn) {
+  const int old = gwk::g_force_bn;
+  gwk::g_force_bn = bn;
+  return old;
+}
+
+// Clears the autotuner's cached choices.
+extern "C" void gwdbg_umma_clear_tuning(void) {
+  std::lock_guard<std::mutex> lk(gwk::g_tune_mu);
+  gwk::g_tuned.clear();
 }
 
 // Sets the L2 prefetch distance (stages) of the persistent kernel; returns the old value.

@@ -108,3 +108,29 @@ def test_autotuned_tiles_match_cost_model():
     bn = ctypes.c_int()
     lib.gwdbg_umma_tuned(0, None, None, ctypes.byref(bn))
     assert bn.value in (32, 48, 64, 80, 96, 112, 128)
+
+
+@pytest.mark.parametrize("bn", [256, 224, 192, 128, 80])
+@pytest.mark.parametrize("M,N,K,ksplit", [(300, 200, 100, 1), (257, 130, 700, 3), (700, 260, 45, 1)])
+def test_forced_tiles(bn, M, N, K, ksplit):
+    """Every N tile of the persistent kernel, including the wide ones (one epilogue
+    group of 8 warps over 192..256 columns), on ragged shapes."""
+    import torch
+    lib = _lib()
+    lib.gwdbg_umma_force_bn.argtypes = [ctypes.c_int]
+    lib.gwdbg_umma_force_bn.restype = ctypes.c_int
+    rng = np.random.default_rng(bn + M + N)
+    A = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K))
+    ref = A @ np.conj(B).T
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.full((M, N), np.nan + 0j, dtype=torch.complex128, device="cuda")
+    old = lib.gwdbg_umma_force_bn(bn)
+    try:
+        st = lib.gwdbg_umma_cgemm_split(dA.data_ptr(), dB.data_ptr(), M, N, K, 1, 3, ksplit, dC.data_ptr())
+    finally:
+        lib.gwdbg_umma_force_bn(old)
+    assert st == 0
+    C = dC.cpu().numpy()
+    assert np.all(np.isfinite(C))
+    assert np.abs(C - ref).max() / (np.sqrt(2.0 * K) * 2.0) < 3e-6
