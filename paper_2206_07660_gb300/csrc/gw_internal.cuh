@@ -75,6 +75,8 @@ cudaError_t dyson_eval(const DysonArgs& a, const double* mu_ptr, double2* G_out,
 struct MuState {
   double lo, hi, Nlo, Nhi, x, Nx, target, tol, width;
   int phase, iter, maxit, done, status;
+  double flo, fhi;   // Illinois-weighted N - target at the bracket ends
+  int side;          // which end moved last (-1 lo, +1 hi, 0 none)
 };
 cudaError_t mu_step(MuState* s, const double* partial, int64_t count, double scale, cudaStream_t st);
 cudaError_t dyson_tangent_rhs(const double2* dSinf, const double2* dSiw, double2* D, int64_t nk, int64_t n2,

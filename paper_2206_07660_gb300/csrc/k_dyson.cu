@@ -96,8 +96,10 @@ cudaError_t dyson_eval(const DysonArgs& a, const double* mu_ptr, double2* G_out,
   return cudaGetLastError();
 }
 
-// One step of the bracketing bisection.  state->x is the point evaluated by
-// the preceding dyson_kernel; `scale` turns the summed partials into N(x).
+// One step of the bracketing search (expand until N(lo) <= target <= N(hi), then
+// Illinois steps with a bisection every fourth step, until |N - target| <= tol and
+// hi - lo <= width).  state->x is the point evaluated by the preceding
+// dyson_kernel; `scale` turns the summed partials into N(x).
 __global__ void __launch_bounds__(1024) mu_step_kernel(MuState* s, const double* partial, int64_t count,
                                                        double scale) {
   if (*(volatile int*)&s->done) return;
@@ -120,14 +122,32 @@ __global__ void __launch_bounds__(1024) mu_step_kernel(MuState* s, const double*
   } else if (s->phase == 1) {     // N at hi: must be >= target
     s->Nhi = N;
     if (N < s->target) { double w = s->hi - s->lo; s->hi += 2.0 * w; s->x = s->hi; }
-    else { s->phase = 2; s->x = 0.5 * (s->lo + s->hi); }
-  } else {                        // bisection
+    else {
+      s->phase = 2;
+      s->flo = s->Nlo - s->target; s->fhi = N - s->target; s->side = 0;
+      const double d = s->fhi - s->flo;
+      const double xs = d > 0 ? s->lo - s->flo * (s->hi - s->lo) / d : 0.5 * (s->lo + s->hi);
+      s->x = (xs > s->lo && xs < s->hi) ? xs : 0.5 * (s->lo + s->hi);
+    }
+  } else {                        // Illinois (regula falsi with halved stale end), bisection every 4th step
     s->Nx = N;
-    if (fabs(N - s->target) <= s->tol && (s->hi - s->lo) <= s->width) {
+    const double F = N - s->target;
+    if (fabs(F) <= s->tol && (s->hi - s->lo) <= s->width) {
       s->done = 1; s->status = 0;
     } else {
-      if (N < s->target) s->lo = s->x; else s->hi = s->x;
-      s->x = 0.5 * (s->lo + s->hi);
+      if (F < 0) {
+        s->lo = s->x; s->flo = F;
+        if (s->side == -1) s->fhi *= 0.5;
+        s->side = -1;
+      } else {
+        s->hi = s->x; s->fhi = F;
+        if (s->side == 1) s->flo *= 0.5;
+        s->side = 1;
+      }
+      const double mid = 0.5 * (s->lo + s->hi), d = s->fhi - s->flo;
+      double xs = d > 0 ? s->lo - s->flo * (s->hi - s->lo) / d : mid;
+      if (!(xs > s->lo && xs < s->hi) || (s->iter & 3) == 0) xs = mid;
+      s->x = xs;
     }
   }
   if (!s->done && s->iter >= s->maxit) { s->done = 1; s->status = 1; }
@@ -140,6 +160,7 @@ __global__ void mu_init_kernel(MuState* s, double target, double tol, double wid
   s->Nlo = s->Nhi = s->Nx = 0.0;
   s->target = target; s->tol = tol; s->width = width;
   s->phase = 0; s->iter = 0; s->maxit = maxit; s->done = 0; s->status = 0;
+  s->flo = s->fhi = 0.0; s->side = 0;
 }
 cudaError_t mu_init_device(MuState* s, double target, double tol, double width, int maxit, cudaStream_t st) {
   mu_init_kernel<<<1, 1, 0, st>>>(s, target, tol, width, maxit);

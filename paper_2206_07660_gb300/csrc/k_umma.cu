@@ -332,7 +332,7 @@ struct UpCfg {
 // stages 11% faster at 1.1e-6)
 static int g_chunk_len = 2;
 static int g_prefetch = 0;   // L2 prefetch distance in stages (0: off)
-static int g_wide = 1;       // autotuner may pick N tiles of 192..256 (one epilogue group of 8 warps)
+static int g_wide = 1;       // autotuner may pick 192..256-column tiles (split 8-warp epilogue)
 static int g_force_bn = 0;   // test hook: nonzero forces this N tile (no tuning)
 
 // Writes one 32 x 32 block of a finished tile: lane l holds the row sums of
@@ -432,17 +432,21 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
   }
 }
 
-template <int BN>
+template <int BN, bool SPLIT>
 __global__ void __launch_bounds__(UP_THREADS, 1)
     umma_pkernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                  const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, UmmaArgs a,
                  int ntn, int ntm, int ntiles) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "N tile");
-  // BN <= 128: two epilogue groups of 4 warps take alternate tiles (ping-pong).
-  // BN > 128 ("wide"): one group of 8 warps, two per TMEM lane quarter, each owning
-  // half of the tile's columns; TMEM holds its two chunk buffers.
-  constexpr bool WIDE = BN > 128;
-  static_assert(!WIDE || (BN / 2) % 16 == 0, "wide tiles split into 16-column halves");
+  // !SPLIT (BN <= 128): two epilogue groups of 4 warps take alternate tiles (ping-pong):
+  // one group's write-out overlaps the next tile's MMAs.
+  // SPLIT (BN 192..256): one group of 8 warps, two per TMEM lane quarter, each owning
+  // half of the tile's columns; TMEM holds the group's two chunk buffers.  Wider MMAs
+  // (N = 256: 128 tensor-pipe cycles each) amortise the fixed per-stage cost of the
+  // barrier handshakes (measured: split 128-column tiles are slower than ping-pong ones).
+  constexpr bool WIDE = SPLIT;
+  static_assert(BN <= 128 || SPLIT, "tiles above 128 columns need the split epilogue");
+  static_assert(!WIDE || (BN / 2) % 16 == 0, "split tiles are two halves of 16-column multiples");
   constexpr int NGRP = WIDE ? 1 : 2;
   constexpr int BW = WIDE ? BN / 2 : BN;   // columns per epilogue warp
   constexpr uint32_t ACCE_COUNT = WIDE ? 8 : 4;
@@ -831,9 +835,9 @@ static size_t umma_psmem() {
 
 static int g_num_sms = 0;
 
-template <int BN>
+template <int BN, bool SPLIT = (BN > 128)>
 static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch, cudaStream_t st) {
-  if (g_persistent || BN > 128) {
+  if (g_persistent || BN > 128 || SPLIT) {
     if (!g_num_sms) {
       int dev = 0;
       cudaGetDevice(&dev);
@@ -841,13 +845,14 @@ static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch,
       if (g_num_sms <= 0) g_num_sms = 148;
     }
     size_t sm = umma_psmem<BN>();
-    cudaError_t e = cudaFuncSetAttribute(umma_pkernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(umma_pkernel<BN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int ntn = (a.N + BN - 1) / BN, ntm = (a.M + UM_BM - 1) / UM_BM;
     const int64_t ntiles = (int64_t)ntn * ntm * batch * a.ksplit;
     if (ntiles > INT32_MAX) return cudaErrorInvalidValue;
     const int grid = (int)(ntiles < g_num_sms ? ntiles : g_num_sms);
-    umma_pkernel<BN><<<grid, UP_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a, ntn, ntm, (int)ntiles);
+    umma_pkernel<BN, SPLIT><<<grid, UP_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a, ntn, ntm, (int)ntiles);
     return cudaGetLastError();
   }
   if constexpr (BN <= 128) {
@@ -865,10 +870,11 @@ static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch,
 static cudaError_t umma_launch(int bn, const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int nseg,
                                const UmmaArgs& a, int batch, cudaStream_t st) {
   CUtensorMap maps[4];
+  const uint32_t box = (uint32_t)bn;
   if (!make_map(&maps[0], A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
       !make_map(&maps[1], nseg > 1 ? A.lo : A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
-      !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn) ||
-      !make_map(&maps[3], nseg > 1 ? B.lo : B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, (uint32_t)bn))
+      !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, box) ||
+      !make_map(&maps[3], nseg > 1 ? B.lo : B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, box))
     return cudaErrorInvalidValue;
   switch (bn) {
     case 256: return launch_bn<256>(maps, a, batch, st);
@@ -907,7 +913,8 @@ static std::map<TuneKey, int> g_tuned;
 static std::mutex g_tune_mu;
 static int g_autotune = 1;
 static const int kBnCand[] = {128, 112, 96, 80, 64, 48, 32};
-static const int kBnWide[] = {256, 224, 192};   // persistent kernel only, tried when N >= 192
+static const int kBnWide[] = {256, 224, 192};   // tried when N >= 192
+
 
 static int cost_model_bn(int N) {
   // trade the padding of the last tile against the per-tile cost of re-reading
