@@ -169,7 +169,8 @@ static cudaError_t run_gett(const GettDesc& d, const void* A, Ty ta, const void*
 static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const UmmaOperand& B, int M, int N,
                             int64_t Kpad, int batch, void* C, bool c_fp64, double alpha, bool accumulate, int64_t c_ld,
                             int64_t c_zs, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
-                            int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr) {
+                            int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr,
+                            int64_t kvalid = 0) {
   count(1);
   if (c->prof) {
     while (c->uev.size() < c->uused + 2) {
@@ -181,7 +182,7 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
     cudaEventRecord(c->uev[c->uused], c->st);
   }
   cudaError_t r = umma_gemm(A, B, M, N, Kpad, batch, C, c_fp64, alpha, accumulate, c_ld, c_zs, 3, c->info + 1, c->st,
-                            ksplit, row_inner, row_s1, col_inner, col_s1, C_lo);
+                            ksplit, row_inner, row_s1, col_inner, col_s1, C_lo, nullptr, kvalid);
   if (c->prof) {
     cudaEventRecord(c->uev[c->uused + 1], c->st);
     c->uused += 2; c->uflops += flops; c->ulaunch += 1;
@@ -656,14 +657,15 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
         UmmaOperand ob{c->Ge_hi + (size_t)kq * ntau * per, c->Ge_lo + (size_t)kq * ntau * per, 2 * (int64_t)nao, ntau, ka,
                        per};
         CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, oa, ob, naux * nao, 2 * nao, ka, ntau, c->Xs_hi, false, 1.0,
-                    false, 2, (int64_t)naux * nao * ka, 1, nao, (int64_t)nao * ka, 2, ka, c->Xs_lo));
+                    false, 2, (int64_t)naux * nao * ka, 1, nao, (int64_t)nao * ka, 2, ka, c->Xs_lo, 2 * (int64_t)nao));
         // Z[t][Q][c][b] = -sum_d G^k(t_{ntau-1-j})[c][d] Y[t][Q][d][b] as rows (t, Q, b) of (c, re/im),
         // written into the (c, b) layout of the last step's A operand
         UmmaOperand ya{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka};
         UmmaOperand gb{c->Gp_hi + (size_t)k * ntau * per, c->Gp_lo + (size_t)k * ntau * per, 2 * (int64_t)nao, ntau, ka,
                        per};
         CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, ya, gb, naux * nao, 2 * nao, ka, ntau, c->Zhi, false, -1.0,
-                    false, 2, (int64_t)naux * c->kpadP, 1, nao, c->kpadP, 2, 2 * (int64_t)nao, c->Zlo));
+                    false, 2, (int64_t)naux * c->kpadP, 1, nao, c->kpadP, 2, 2 * (int64_t)nao, c->Zlo,
+                    2 * (int64_t)nao));
       } else if (f32 && nao <= 64) {
         // Y[t][Q][d][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b]   (G shared per t)
         BsmDesc b1{};
@@ -713,7 +715,7 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
         UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, kp, 0};
         UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, kp, 0};
         CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, kp, 1, Pq, true,
-                    c->spin / nk, accumulate || k > 0, 2 * (int64_t)naux, 0));
+                    c->spin / nk, accumulate || k > 0, 2 * (int64_t)naux, 0, 1, 0, 0, 0, 0, nullptr, 2 * n2));
         count(1);
         continue;
       }
@@ -831,10 +833,10 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
           const int64_t ka = c->kpadA;
           CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, naux, (int)(2 * n2), kp, ntau, c->Xs_hi, false,
                       1.0, false, (int64_t)nao * ka, (int64_t)naux * nao * ka, 1, 0, 0, 2 * (int64_t)nao, ka,
-                      c->Xs_lo));
+                      c->Xs_lo, 2 * (int64_t)naux));
         } else {
           CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, naux, (int)(2 * n2), kp, ntau, c->chA, false,
-                      1.0, false, 2 * n2, (int64_t)naux * 2 * n2));
+                      1.0, false, 2 * n2, (int64_t)naux * 2 * n2, 1, 0, 0, 0, 0, nullptr, 2 * (int64_t)naux));
         }
         count(1);
       } else {
@@ -854,7 +856,8 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
         UmmaOperand ob{c->Ge_hi + (size_t)kmq * ntau * per, c->Ge_lo + (size_t)kmq * ntau * per, 2 * (int64_t)nao, ntau,
                        ka, per};
         CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, oa, ob, naux * nao, 2 * nao, ka, ntau, c->Y3hi, false, 1.0,
-                    false, c->kpad3, (int64_t)nao * c->kpad3, 1, nao, 2 * (int64_t)nao, 0, 0, c->Y3lo));
+                    false, c->kpad3, (int64_t)nao * c->kpad3, 1, nao, 2 * (int64_t)nao, 0, 0, c->Y3lo,
+                    2 * (int64_t)nao));
         count(1);
       } else if (f32 && nao <= 64) {
         BsmDesc b{};
@@ -889,7 +892,7 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
         if (ks < 1) ks = 1;
         CK(run_umma(c, 8.0 * ntau * nao * (double)nao * naux * nao, oa, ob, ntau * nao, 2 * nao, kp, 1,
                     (double*)(out + (size_t)k * n2), true, -1.0 / nk, true, 2 * (int64_t)nao, 0, (int)ks, nao,
-                    2 * gstep));
+                    2 * gstep, 0, 0, nullptr, 2 * (int64_t)naux * nao));
         count(1);
         continue;
       }

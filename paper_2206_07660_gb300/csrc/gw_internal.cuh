@@ -129,6 +129,8 @@ struct UmmaOperand {
 // o * row_inner + i is written at o * row_s1 + i * c_ld (real elements); col_inner
 // > 0: column n = o * col_inner + i at o * col_s1 + i.  C_lo != null: fp32 output
 // written as TF32 hi (C) / lo (C_lo) planes.
+// kvalid > 0: real K extent holding data (the rest of Kpad is zero padding in both
+// operands); the persistent kernel skips whole K = 8 steps of that padding.
 // scale != null (fp64 output, persistent kernel only): D[m][n] is multiplied by
 // 2^(eA[z*ea_zs + m] + eB[z*eb_zs + n/2] + eshift) before it is added or stored.
 struct UmmaScale {
@@ -141,7 +143,7 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
                       int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr,
-                      const UmmaScale* scale = nullptr);
+                      const UmmaScale* scale = nullptr, int64_t kvalid = 0);
 // FP64 complex products on tensor cores by exact digit splitting (k_emul.cu)
 int64_t emul_kpad(int64_t K);
 size_t emul_digit_bytes(int64_t rows, int64_t K);

@@ -177,7 +177,7 @@ cudaError_t emul_transform(const float* Bd, const int* Be, int64_t nrow, const d
       UmmaOperand ob{const_cast<float*>(Bd) + (int64_t)(EM_S - g + i0) * Kp, nullptr, 2 * nrow, 1, ld, 0};
       UmmaScale sc{Ae, Be, 0, 0, -EM_BETA * g};
       e = umma_gemm(oa, ob, (int)ncol, (int)(2 * nrow), (int64_t)np * Kp, 1, (void*)Y, true, 1.0, !first, 2, 0, 1,
-                    err, st, 1, 0, 0, 2, 2 * ldy, nullptr, &sc);
+                    err, st, 1, 0, 0, 2, 2 * ldy, nullptr, &sc, (int64_t)(np - 1) * Kp + 2 * K);
       if (e != cudaSuccess) return e;
       first = false;
     }

@@ -63,6 +63,7 @@ struct UmmaArgs {
   int direct;          // persistent kernel: transposed complex output stored lane-per-row (see umma_gemm)
   int chunk_len;       // persistent kernel: k-blocks accumulated in TMEM before the FP32 register sums
   int prefetch;        // persistent kernel: stages ahead of the pipeline whose tiles are prefetched into L2
+  int klast8;          // persistent kernel: K = 8 steps of the last k-block that hold data (1..4)
   // fp64 output only: D[m][n] is scaled by 2^(eA[m] + eB[n/2] + eshift) (emulated FP64 products)
   const int* eA;
   const int* eB;
@@ -584,20 +585,28 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           uint8_t* st = sStage + s * Cf::STAGE;
           const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_BYTES);
           const uint64_t bh = sw128_desc(st + 2 * A_BYTES), bl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
+          // K = 8 per MMA; the zero padding of the last k-block of the K range is skipped
+          const int kb_first = three ? kb0 + it : kb0 + 2 * it;
+          const int nk1 = kb_first == a.kblocks - 1 ? a.klast8 : UM_BK / 8;
 #pragma unroll
           for (int kk = 0; kk < UM_BK / 8; ++kk) {
-            const uint64_t o = (uint64_t)(kk * 2);
-            umma_tf32(d, ah + o, bh + o, idesc, (!chunk_first || kk > 0) ? 1u : 0u);   // hi * hi (first k-block)
-            if (three) {
-              umma_tf32(d, ah + o, bl + o, idesc, 1u);                                   // hi * lo
-              umma_tf32(d, al + o, bh + o, idesc, 1u);                                   // lo * hi
+            if (kk < nk1) {
+              const uint64_t o = (uint64_t)(kk * 2);
+              umma_tf32(d, ah + o, bh + o, idesc, (!chunk_first || kk > 0) ? 1u : 0u);   // hi * hi (first k-block)
+              if (three) {
+                umma_tf32(d, ah + o, bl + o, idesc, 1u);                                   // hi * lo
+                umma_tf32(d, al + o, bh + o, idesc, 1u);                                   // lo * hi
+              }
             }
           }
           if (!three && 2 * it + 1 < nkb) {
+            const int nk2 = kb_first + 1 == a.kblocks - 1 ? a.klast8 : UM_BK / 8;
 #pragma unroll
             for (int kk = 0; kk < UM_BK / 8; ++kk) {
-              const uint64_t o = (uint64_t)(kk * 2);
-              umma_tf32(d, al + o, bl + o, idesc, 1u);                                   // second k-block
+              if (kk < nk2) {
+                const uint64_t o = (uint64_t)(kk * 2);
+                umma_tf32(d, al + o, bl + o, idesc, 1u);                                 // second k-block
+              }
             }
           }
           umma_commit(&empty[s]);
@@ -962,7 +971,7 @@ static int tune_bn(const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1, int64_t col_inner,
-                      int64_t col_s1, float* C_lo, const UmmaScale* scale) {
+                      int64_t col_s1, float* C_lo, const UmmaScale* scale, int64_t kvalid) {
   if (Kpad % UM_BK) return cudaErrorInvalidValue;
   if (ksplit < 1) ksplit = 1;
   if (ksplit > 1 && (!c_fp64 || !accumulate)) return cudaErrorInvalidValue;   // split partials add atomically
@@ -986,6 +995,13 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   a.err = err;
   a.chunk_len = nseg == 3 ? g_chunk_len : UM_FLUSH;
   a.prefetch = g_prefetch;
+  {
+    // columns [kvalid, Kpad) are zero padding in both operands; whole K = 8 steps of
+    // it at the end of the last k-block are skipped
+    const int64_t kv = (kvalid > 0 && kvalid <= Kpad) ? kvalid : Kpad;
+    const int64_t in_last = kv - (int64_t)(a.kblocks - 1) * UM_BK;
+    a.klast8 = in_last <= 0 ? UM_BK / 8 : (int)((in_last + 7) / 8);
+  }
   if (scale) {
     if (!c_fp64 || !g_persistent) return cudaErrorInvalidValue;
     a.eA = scale->eA; a.eB = scale->eB; a.ea_zs = scale->ea_zs; a.eb_zs = scale->eb_zs; a.eshift = scale->eshift;
@@ -1282,7 +1298,8 @@ extern "C" int gwdbg_umma_cgemm_split(const double2* A, const double2* B, int M,
   }
   UmmaOperand oa{ah, al, M, 1, Kpad, 0}, ob{bh, bl, 2 * (int64_t)N, 1, Kpad, 0};
   if (!e && ksplit > 1) e = cudaMemset(C, 0, (size_t)M * 2 * N * 8);
-  if (!e) e = umma_gemm(oa, ob, M, 2 * N, Kpad, 1, C, true, 1.0, ksplit > 1, 2 * N, 0, nseg, err, 0, ksplit);
+  if (!e) e = umma_gemm(oa, ob, M, 2 * N, Kpad, 1, C, true, 1.0, ksplit > 1, 2 * N, 0, nseg, err, 0, ksplit, 0, 0, 0, 0,
+                        nullptr, nullptr, 2 * (int64_t)K);
   int herr = 0;
   if (!e) e = cudaDeviceSynchronize();
   cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
