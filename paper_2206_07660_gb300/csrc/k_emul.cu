@@ -27,17 +27,21 @@ namespace gwk {
 
 constexpr int EM_BETA = 7;
 constexpr int EM_S = 8;
+static_assert(EM_BETA == 7, "the balanced digit masks below are for 7-bit digits");
 
-// digits of x / 2^e (|x| <= 2^e): d[0..S-1]
+// digits of x / 2^e (|x| <= 2^e): d[0..S-1].  x is rounded once to a multiple of
+// 2^(e - 7S) (an exact integer v with |v| <= 2^(7S) = 2^56), whose balanced base-128
+// digits d_S .. d_2 in [-64, 63] are peeled off with integer shifts; the rest is
+// d_1 (|d_1| <= 128).
 __device__ __forceinline__ void em_digits(double x, int e, float* d) {
-  double t = ldexp(x, -e);
+  long long v = __double2ll_rn(ldexp(x, EM_BETA * EM_S - e));
 #pragma unroll
-  for (int i = 0; i < EM_S; ++i) {
-    t *= (double)(1 << EM_BETA);
-    const double r = rint(t);
-    t -= r;
-    d[i] = (float)r;
+  for (int i = EM_S - 1; i >= 1; --i) {
+    const long long di = ((v + 64) & 127) - 64;
+    d[i] = (float)di;
+    v = (v - di) >> EM_BETA;
   }
+  d[0] = (float)v;
 }
 
 __device__ __forceinline__ int em_exponent(double m) {

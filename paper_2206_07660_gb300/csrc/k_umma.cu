@@ -333,7 +333,7 @@ struct UpCfg {
 // stages 11% faster at 1.1e-6)
 static int g_chunk_len = 2;
 static int g_prefetch = 0;   // L2 prefetch distance in stages (0: off)
-static int g_wide = 1;       // autotuner may pick 192..256-column tiles (split 8-warp epilogue)
+static int g_wide = 1;       // autotuner may pick 160..256-column tiles (split 8-warp epilogue)
 static int g_force_bn = 0;   // test hook: nonzero forces this N tile (no tuning)
 
 // Writes one 32 x 32 block of a finished tile: lane l holds the row sums of
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "N tile");
   // !SPLIT (BN <= 128): two epilogue groups of 4 warps take alternate tiles (ping-pong):
   // one group's write-out overlaps the next tile's MMAs.
-  // SPLIT (BN 192..256): one group of 8 warps, two per TMEM lane quarter, each owning
+  // SPLIT (BN 160..256): one group of 8 warps, two per TMEM lane quarter, each owning
   // half of the tile's columns; TMEM holds the group's two chunk buffers.  Wider MMAs
   // (N = 256: 128 tensor-pipe cycles each) amortise the fixed per-stage cost of the
   // barrier handshakes (measured: split 128-column tiles are slower than ping-pong ones).
@@ -889,6 +889,7 @@ static cudaError_t umma_launch(int bn, const UmmaOperand& A, const UmmaOperand& 
     case 256: return launch_bn<256>(maps, a, batch, st);
     case 224: return launch_bn<224>(maps, a, batch, st);
     case 192: return launch_bn<192>(maps, a, batch, st);
+    case 160: return launch_bn<160>(maps, a, batch, st);
     case 128: return launch_bn<128>(maps, a, batch, st);
     case 112: return launch_bn<112>(maps, a, batch, st);
     case 96: return launch_bn<96>(maps, a, batch, st);
@@ -922,7 +923,7 @@ static std::map<TuneKey, int> g_tuned;
 static std::mutex g_tune_mu;
 static int g_autotune = 1;
 static const int kBnCand[] = {128, 112, 96, 80, 64, 48, 32};
-static const int kBnWide[] = {256, 224, 192};   // tried when N >= 192
+static const int kBnWide[] = {256, 224, 192, 160};   // tried when N >= 160
 
 
 static int cost_model_bn(int N) {
@@ -948,7 +949,7 @@ static int tune_bn(const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int
   int best = fallback;
   float best_ms = 1e30f;
   std::vector<int> cands(kBnCand, kBnCand + sizeof(kBnCand) / sizeof(int));
-  if (a.N >= 192 && g_wide) cands.insert(cands.begin(), kBnWide, kBnWide + sizeof(kBnWide) / sizeof(int));
+  if (a.N >= 160 && g_wide) cands.insert(cands.begin(), kBnWide, kBnWide + sizeof(kBnWide) / sizeof(int));
   for (int cand : cands) {
     if (umma_launch(cand, A, B, Kpad, nseg, t, batch, st) != cudaSuccess) continue;   // warm-up
     float cand_ms = 1e30f;

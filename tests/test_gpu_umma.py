@@ -107,14 +107,14 @@ def test_autotuned_tiles_match_cost_model():
     assert n >= 1
     bn = ctypes.c_int()
     lib.gwdbg_umma_tuned(0, None, None, ctypes.byref(bn))
-    assert bn.value in (32, 48, 64, 80, 96, 112, 128, 192, 224, 256)
+    assert bn.value in (32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256)
 
 
-@pytest.mark.parametrize("bn", [256, 224, 192, 128, 80])
+@pytest.mark.parametrize("bn", [256, 224, 192, 160, 128, 80])
 @pytest.mark.parametrize("M,N,K,ksplit", [(300, 200, 100, 1), (257, 130, 700, 3), (700, 260, 45, 1)])
 def test_forced_tiles(bn, M, N, K, ksplit):
     """N tiles of the persistent kernel on ragged shapes: ping-pong epilogues (two
-    groups of 4 warps, up to 128 columns) and the split epilogue of the 192..256-column
+    groups of 4 warps, up to 128 columns) and the split epilogue of the 160..256-column
     tiles (8 warps, each half of the columns)."""
     import torch
     lib = _lib()
