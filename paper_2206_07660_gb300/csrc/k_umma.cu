@@ -64,6 +64,8 @@ struct UmmaArgs {
   int chunk_len;       // persistent kernel: k-blocks accumulated in TMEM before the FP32 register sums
   int prefetch;        // persistent kernel: stages ahead of the pipeline whose tiles are prefetched into L2
   int klast8;          // persistent kernel: K = 8 steps of the last k-block that hold data (1..4)
+  uint32_t spin;       // persistent kernel: iteration limit of the pipeline waits (the teardown waits use
+                       // UM_SPIN_LIMIT)
   // fp64 output only: D[m][n] is scaled by 2^(eA[m] + eB[n/2] + eshift) (emulated FP64 products)
   const int* eA;
   const int* eB;
@@ -83,9 +85,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 // bounded wait; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = UM_SPIN_LIMIT) {
   uint32_t addr = smem_u32(bar);
-  for (uint32_t i = 0; i < UM_SPIN_LIMIT; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -148,8 +150,10 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
   uint64_t* empty = full + UM_STAGES;
   uint64_t* accf = empty + UM_STAGES;    // accumulator buffer b holds a finished chunk
   uint64_t* acce = accf + 2;             // accumulator buffer b has been drained
-  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  uint64_t* mdone = acce + 2;            // the MMA thread's final commit (teardown)
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
   __shared__ int s_fail;
+  __shared__ int s_issued, s_consumed;   // TMA stage fills issued / waited for by the MMA thread
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * UM_BM;
@@ -162,6 +166,9 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
 
   if (threadIdx.x == 0) {
     s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    mbar_init(mdone, 1);
     for (int s = 0; s < UM_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -179,10 +186,11 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
   if (warp == 0) {
     if (lane == 0) {
       const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
-      for (int it = 0; it < total; ++it) {
+      int it = 0;
+      for (; it < total; ++it) {
         const int s = it % UM_STAGES;
         const uint32_t ph = (uint32_t)(it / UM_STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); break; }
+        if (!mbar_wait(&empty[s], ph ^ 1u, a.spin)) { atomicCAS(&s_fail, 0, 1); break; }
         const int seg = it / nkb, kb = kb0 + (it - seg * nkb);
         const CUtensorMap* ma = (seg == 2) ? &tA1 : &tA0;   // A_hi, A_hi, A_lo
         const CUtensorMap* mb = (seg == 1) ? &tB1 : &tB0;   // B_hi, B_lo, B_hi
@@ -190,6 +198,7 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
         tma_load_3d(sA + s * A_BYTES, ma, &full[s], kb * UM_BK, m0, za);
         tma_load_3d(sB + s * B_BYTES, mb, &full[s], kb * UM_BK, n0, zb);
       }
+      s_issued = it;
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -197,15 +206,16 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                              ((uint32_t)(UM_BM >> 4) << 24);
       uint32_t dcur = tmem;
-      for (int it = 0; it < total; ++it) {
+      int it = 0;
+      for (; it < total; ++it) {
         const int s = it % UM_STAGES;
         const uint32_t ph = (uint32_t)(it / UM_STAGES) & 1u;
         const int c = it / UM_FLUSH, b = c & 1;
         const bool chunk_first = (it % UM_FLUSH) == 0;
         if (chunk_first && c >= 2) {   // buffer b must have been drained (its use c/2 - 1)
-          if (!mbar_wait(&acce[b], (uint32_t)((c / 2 - 1) & 1))) { atomicCAS(&s_fail, 0, 4); break; }
+          if (!mbar_wait(&acce[b], (uint32_t)((c / 2 - 1) & 1), a.spin)) { atomicCAS(&s_fail, 0, 4); break; }
         }
-        if (!mbar_wait(&full[s], ph)) { atomicCAS(&s_fail, 0, 2); break; }
+        if (!mbar_wait(&full[s], ph, a.spin)) { atomicCAS(&s_fail, 0, 2); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         dcur = tmem + (uint32_t)(b * BN);
         const uint64_t ad = sw128_desc(sA + s * A_BYTES), bd = sw128_desc(sB + s * B_BYTES);
@@ -216,6 +226,8 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
         umma_commit(&empty[s]);
         if ((it % UM_FLUSH) == UM_FLUSH - 1 || it == total - 1) umma_commit(&accf[b]);
       }
+      s_consumed = it;
+      umma_commit(mdone);   // arrives once every MMA issued above has completed
     }
   } else {
     // Epilogue warps: warp w owns TMEM lanes 32*(w%4) .. +31, i.e. 32 output rows.
@@ -230,7 +242,12 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int b = c & 1;
-      if (!mbar_wait(&accf[b], (uint32_t)((c / 2) & 1))) { atomicCAS(&s_fail, 0, 3); ok = false; break; }
+      // warp-uniform outcome: the TMEM loads below are warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], (uint32_t)((c / 2) & 1), a.spin))) {
+        atomicCAS(&s_fail, 0, 3);
+        ok = false;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -299,6 +316,13 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (threadIdx.x == 0 && s_fail) {
+    // after a timeout: let the stage fills still in flight land and the issued MMAs
+    // finish before the shared memory and TMEM are given back
+    for (int gg = s_consumed; gg < s_issued; ++gg) mbar_wait(&full[gg % UM_STAGES], (uint32_t)(gg / UM_STAGES) & 1u);
+    mbar_wait(mdone, 0);
+  }
+  __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
@@ -333,6 +357,7 @@ struct UpCfg {
 // stages 11% faster at 1.1e-6)
 static int g_chunk_len = 2;
 static int g_prefetch = 0;   // L2 prefetch distance in stages (0: off)
+static uint32_t g_spin = UM_SPIN_LIMIT;   // pipeline wait limit (test hook lowers it)
 static int g_wide = 1;       // autotuner may pick 160..256-column tiles (split 8-warp epilogue)
 static int g_force_bn = 0;   // test hook: nonzero forces this N tile (no tuning)
 
@@ -465,14 +490,19 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
   uint64_t* empty = full + NS;
   uint64_t* accf = empty + NS;          // [group][buffer]: chunk in TMEM is complete
   uint64_t* acce = accf + 4;            // [group][buffer]: chunk drained by the group's 4 warps
-  uint32_t* tmem_slot = (uint32_t*)(acce + 4);
+  uint64_t* mdone = acce + 4;           // the MMA thread's final commit (teardown)
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
   __shared__ int s_fail;
+  __shared__ uint32_t s_issued, s_consumed;   // TMA stage fills issued / waited for by the MMA thread
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kbs = (a.kblocks + a.ksplit - 1) / a.ksplit;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    mbar_init(mdone, 1);
     for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 4; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], ACCE_COUNT); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -513,7 +543,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         for (int it = 0; it < nst; ++it, ++g) {
           const int s = (int)(g % NS);
           const uint32_t ph = (g / NS) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicCAS(&s_fail, 0, 1); ok = false; break; }
+          if (!mbar_wait(&empty[s], ph ^ 1u, a.spin)) { atomicCAS(&s_fail, 0, 1); ok = false; break; }
           uint8_t* st = sStage + s * Cf::STAGE;
           if (a.prefetch > 0) {   // warm L2 with the operand tiles a few stages ahead
             const int itp = it + a.prefetch;
@@ -551,6 +581,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         }
         if (!ok) break;
       }
+      s_issued = g;
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -577,9 +608,9 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           const uint32_t u = chunk >> 1;   // use count of this buffer
           const bool chunk_first = (it % CL) == 0;
           if (chunk_first && u >= 1) {
-            if (!mbar_wait(&acce[grp * 2 + b], (u - 1) & 1u)) { atomicCAS(&s_fail, 0, 4); ok = false; break; }
+            if (!mbar_wait(&acce[grp * 2 + b], (u - 1) & 1u, a.spin)) { atomicCAS(&s_fail, 0, 4); ok = false; break; }
           }
-          if (!mbar_wait(&full[s], ph)) { atomicCAS(&s_fail, 0, 2); ok = false; break; }
+          if (!mbar_wait(&full[s], ph, a.spin)) { atomicCAS(&s_fail, 0, 2); ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t d = tmem + (uint32_t)((grp * 2 + b) * BN);
           uint8_t* st = sStage + s * Cf::STAGE;
@@ -615,6 +646,8 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         if (!ok) break;
         cg[grp] += (uint32_t)((nst + CL - 1) / CL);
       }
+      s_consumed = g;
+      umma_commit(mdone);   // arrives once every MMA issued above has completed
     }
   } else {
     // narrow: epilogue group grp = 0 (warps 2..5) or 1 (warps 6..9) takes local tiles
@@ -640,7 +673,12 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         const uint32_t chunk = cg + (uint32_t)c;
         const int b = (int)(chunk & 1u);
         const uint32_t u = chunk >> 1;
-        if (!mbar_wait(&accf[grp * 2 + b], u & 1u)) { atomicCAS(&s_fail, 0, 3); ok = false; break; }
+        // warp-uniform outcome: the TMEM loads below are warp-collective
+        if (!__all_sync(0xffffffffu, mbar_wait(&accf[grp * 2 + b], u & 1u, a.spin))) {
+          atomicCAS(&s_fail, 0, 3);
+          ok = false;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // GRP columns in flight per wait (fewer load round trips, within the register budget)
         constexpr int GRP = BW >= 112 ? 16 : BW > 80 ? 32 : 64;
@@ -794,6 +832,13 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (threadIdx.x == 0 && s_fail) {
+    // after a timeout: let the stage fills still in flight land and the issued MMAs
+    // finish before the shared memory and TMEM are given back
+    for (uint32_t gg = s_consumed; gg < s_issued; ++gg) mbar_wait(&full[gg % NS], (gg / NS) & 1u);
+    mbar_wait(mdone, 0);
+  }
+  __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
@@ -833,13 +878,13 @@ static bool make_map(CUtensorMap* m, const float* base, int64_t kdim, int64_t ro
 template <int BN>
 static size_t umma_smem() {
   static_assert(UM_BM * (BN + 1) * 4 <= UM_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4), "epilogue tile must fit");
-  return 1024 + (size_t)UM_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + (2 * UM_STAGES + 4) * 8 + 16;
+  return 1024 + (size_t)UM_STAGES * (UM_BM * UM_BK * 4 + BN * UM_BK * 4) + (2 * UM_STAGES + 5) * 8 + 16;
 }
 
 template <int BN>
 static size_t umma_psmem() {
   using Cf = UpCfg<BN>;
-  return 1024 + (size_t)Cf::STAGES * Cf::STAGE + Cf::STAGING + (2 * Cf::STAGES + 8) * 8 + 16;
+  return 1024 + (size_t)Cf::STAGES * Cf::STAGE + Cf::STAGING + (2 * Cf::STAGES + 9) * 8 + 16;
 }
 
 static int g_num_sms = 0;
@@ -996,6 +1041,7 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   a.err = err;
   a.chunk_len = nseg == 3 ? g_chunk_len : UM_FLUSH;
   a.prefetch = g_prefetch;
+  a.spin = g_spin;
   {
     // columns [kvalid, Kpad) are zero padding in both operands; whole K = 8 steps of
     // it at the end of the last k-block are skipped
@@ -1235,6 +1281,16 @@ extern "C" int gwdbg_umma_force_bn(int bn) {
 extern "C" void gwdbg_umma_clear_tuning(void) {
   std::lock_guard<std::mutex> lk(gwk::g_tune_mu);
   gwk::g_tuned.clear();
+}
+
+// Sets the iteration limit of the persistent kernel's pipeline waits (0: the default);
+// returns the old value.  A limit of a few iterations makes the kernel give up at its
+// first wait that is not already satisfied: it drains its TMA loads and MMAs, frees
+// its TMEM and reports the timeout through the error flag (code 100 + role).
+extern "C" unsigned gwdbg_umma_set_spin(unsigned n) {
+  const unsigned old = gwk::g_spin;
+  gwk::g_spin = n ? n : gwk::UM_SPIN_LIMIT;
+  return old;
 }
 
 // Sets the L2 prefetch distance (stages) of the persistent kernel; returns the old value.
