@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 #include <atomic>
+#include <nvtx3/nvToolsExt.h>
 #include "gw_internal.cuh"
 
 using namespace gwk;
@@ -38,6 +39,9 @@ struct gw_ctx {
   float* emA = nullptr;
   int* emAe = nullptr;
   size_t emA_bytes = 0;
+  // screened solve as a complex64 inversion refined to FP64 accuracy (with emul)
+  void* irws = nullptr;
+  size_t irws_bytes = 0;
   int *d_fn = nullptr, *d_bm = nullptr;
   // state
   double2 *G_tau = nullptr, *G_iw = nullptr, *G_prev = nullptr, *gamma = nullptr, *tQ = nullptr;
@@ -102,6 +106,13 @@ static thread_local std::string g_init_err;
 // beat the FP32 SIMT small-product kernel (C3 shapes with a 2x2x2 k-mesh: P~0 stage
 // 327 ms against 530 ms, Sigma~ 244 ms against 331 ms per iteration).
 static constexpr bool kTensorSmallSteps = true;   // GW_SMALL_TENSOR / GW_SMALL_SIMT override
+
+// Screened solve with the tensor cores: complex64 inversion of I - P~0 and two Newton
+// steps with FP64-accurate residuals (relative error ~1e-7 -> ~1e-14 -> FP64
+// rounding); the systems are processed in batches whose workspace (digit planes of
+// P~0 and of the iterate, residual, complex64 panels) stays below kRefineBytes.
+static constexpr int kRefineSteps = 2;
+static constexpr size_t kRefineBytes = (size_t)6 << 30;
 
 #define CK(x)                                                                        \
   do {                                                                               \
@@ -181,8 +192,12 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
     }
     cudaEventRecord(c->uev[c->uused], c->st);
   }
+  // named range around the contraction GEMMs of the P~0 / Sigma~ chains, so that a
+  // profiler can select exactly these launches
+  nvtxRangePushA("contraction");
   cudaError_t r = umma_gemm(A, B, M, N, Kpad, batch, C, c_fp64, alpha, accumulate, c_ld, c_zs, 3, c->info + 1, c->st,
                             ksplit, row_inner, row_s1, col_inner, col_s1, C_lo, nullptr, kvalid);
+  nvtxRangePop();
   if (c->prof) {
     cudaEventRecord(c->uev[c->uused + 1], c->st);
     c->uused += 2; c->uflops += flops; c->ulaunch += 1;
@@ -247,7 +262,7 @@ static cudaError_t transform(gw_ctx* c, const double2* T, const double2* X, doub
                                        Y + z * ystride, ncol, c->emA, c->emAe, c->info + 1, c->st);
         if (e != cudaSuccess) return e;
       }
-      count((int)(batch * 13));
+      count((int)(batch * (1 + emul_launches(c->ntau))));
       return cudaSuccess;
     }
   }
@@ -329,6 +344,16 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     for (int i = 0; i < 4; ++i) {
       c->Tdig[i] = (float*)need(A(emul_digit_bytes(2 * (int64_t)ntau, ntau)));
       c->Texp[i] = (int*)need(A((size_t)ntau * 4));
+    }
+    if (screened_refine_ok(naux)) {
+      // as many (q, Omega) systems per batch as fit in kRefineBytes
+      const int64_t cnt = (int64_t)nk * ntau;
+      const size_t per = screened_refine_bytes(naux, 1);
+      int64_t chunk = (int64_t)(kRefineBytes / per);
+      if (chunk < 1) chunk = 1;
+      if (chunk > cnt) chunk = cnt;
+      c->irws_bytes = screened_refine_bytes(naux, chunk);
+      c->irws = need(A(c->irws_bytes));
     }
   }
   c->r = (double2*)need(A(ntau * cb));
@@ -762,11 +787,19 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
   if (!c->have_P0) return fail(c, GW_ERR_STATE, "no polarization yet");
   const int nk = c->nk, naux = c->naux, ntau = c->ntau;
   const int64_t na2 = c->na2;
-  if (!c->deferred) CK(cudaMemsetAsync(c->info + 2, 0, 4, c->st));
-  CK(screened_inplace(c->P_iw, naux, (int64_t)nk * c->nw, (double2*)c->ws, c->ws_bytes, c->info + 2, c->st));
-  {
+  if (!c->deferred) {
+    CK(cudaMemsetAsync(c->info + 1, 0, 8, c->st));
+  }
+  if (c->irws) {
+    // complex64 inversion refined to FP64 accuracy (P~0 Y on the tensor cores)
+    int64_t nl = 0;
+    CK(screened_refine(c->P_iw, naux, (int64_t)nk * c->nw, c->irws, c->irws_bytes, kRefineSteps, c->info + 2,
+                       c->info + 1, c->st, &nl));
+    count((int)nl);
+  } else {
+    CK(screened_inplace(c->P_iw, naux, (int64_t)nk * c->nw, (double2*)c->ws, c->ws_bytes, c->info + 2, c->st));
     int64_t nbk = (naux + 63) / 64;
-    count((int)(2 + nbk * 6));
+    count((int)(2 + nbk * 7));
   }
   // P~(tau_j) = sum_m TBb[j][m] P~(i Omega_m)   (Eq. Piw_to_Pt), symmetrised
   CK(transform(c, c->TBb, c->P_iw, c->P_tau, ntau, na2, nk, (int64_t)c->nw * na2, (int64_t)ntau * na2));
@@ -774,11 +807,12 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
   count(1);
   c->have_P0 = false;   // P~0(i Omega) was overwritten
   if (!c->deferred) {
-    int h = 0;
-    CK(cudaMemcpyAsync(c->h_scr, c->info + 2, 4, cudaMemcpyDeviceToHost, c->st));
+    int h[2] = {0, 0};
+    CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 8, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    memcpy(&h, c->h_scr, 4);
-    if (h) return fail(c, GW_ERR_SINGULAR, "zero pivot in the screened solve");
+    memcpy(h, c->h_scr, 8);
+    if (h[0]) return fail(c, GW_ERR_TIMEOUT, "tensor-core product gave up waiting (code " + std::to_string(h[0]) + ")");
+    if (h[1]) return fail(c, GW_ERR_SINGULAR, "zero pivot in the screened solve");
   }
   c->have_P = true;
   return GW_OK;

@@ -62,6 +62,11 @@ cudaError_t invert_small_gj(double2* A, int n, int* d_info, cudaStream_t st);
 cudaError_t screened_inplace(double2* P, int64_t n, int64_t count, double2* work, size_t work_bytes,
                              int* d_info, cudaStream_t st);
 size_t screened_work_bytes(int64_t n, int64_t count);
+// complex64 inversion + nsteps Newton steps with FP64-accurate residuals (k_solve.cu)
+size_t screened_refine_bytes(int64_t n, int64_t chunk);
+bool screened_refine_ok(int64_t n);
+cudaError_t screened_refine(double2* X, int64_t n, int64_t count, void* work, size_t work_bytes, int nsteps,
+                            int* d_info, int* d_err, cudaStream_t st, int64_t* nlaunch);
 
 struct DysonArgs {
   int nao, nk, nw;
@@ -150,6 +155,14 @@ size_t emul_digit_bytes(int64_t rows, int64_t K);
 cudaError_t emul_split_b(const double2* B, int64_t rows, int64_t K, int64_t ldb, float* dig, int* ex, cudaStream_t st);
 cudaError_t emul_transform(const float* Bd, const int* Be, int64_t nrow, const double2* X, int64_t K, int64_t ncol,
                            int64_t ldx, double2* Y, int64_t ldy, float* Ad, int* Ae, int* err, cudaStream_t st);
+// tensor-core launches of one product with complex K and nd digits (-1: K too large)
+int emul_launches(int64_t K, int nd = 8);
+cudaError_t emul_split_rows(const double2* A, int64_t count, int64_t M, int64_t K, int64_t lda, int64_t sa,
+                            float* Ad, int* Ae, cudaStream_t st);
+cudaError_t emul_split_cols(const double2* B, int64_t count, int64_t K, int64_t N, int64_t ldb, int64_t sb,
+                            float* Bd, int* Be, cudaStream_t st);
+cudaError_t emul_cgemm_batched(const float* Ad, const int* Ae, const float* Bd, const int* Be, int64_t count,
+                               int64_t M, int64_t N, int64_t K, double2* C, int* err, cudaStream_t st, int nd = 8);
 
 cudaError_t split_rows(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, float* hi,
                        float* lo, int64_t Kpad, cudaStream_t st);
@@ -157,6 +170,8 @@ cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, 
                        cudaStream_t st);
 cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float* hi, float* lo, int64_t Kpad,
                     cudaStream_t st);
+cudaError_t embed_t_batched(const void* src, bool src_c128, int64_t count, int64_t K, int64_t N, int64_t ld,
+                            int64_t zs, float* hi, float* lo, int64_t Kpad, int64_t ds, cudaStream_t st);
 cudaError_t embed_conj_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
                                float* lo, int64_t Kpad, int64_t ds, cudaStream_t st);
 cudaError_t embed_plain_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
