@@ -127,7 +127,8 @@ struct UmmaOperand {
   const float* hi;
   const float* lo;
   int64_t rows, batch;   // rows per batch, batch count (1 = shared by all z)
-  int64_t ld, bs;        // row stride and batch stride in fp32 elements
+  int64_t ld, bs;        // row stride and batch stride in elements
+  int f16 = 0;           // 1: hi/lo hold fp16 pieces (cast pointers), K and strides in fp16 elements
 };
 // ksplit > 1: the K range is split over blocks and partial results are added to
 // an fp64 C with atomics (requires accumulate).  row_inner > 0: output row m =
@@ -136,8 +137,9 @@ struct UmmaOperand {
 // written as TF32 hi (C) / lo (C_lo) planes.
 // kvalid > 0: real K extent holding data (the rest of Kpad is zero padding in both
 // operands); the persistent kernel skips whole K = 8 steps of that padding.
-// scale != null (fp64 output, persistent kernel only): D[m][n] is multiplied by
-// 2^(eA[z*ea_zs + m] + eB[z*eb_zs + n/2] + eshift) before it is added or stored.
+// scale != null (persistent kernel only): D[m][n] is multiplied by
+// 2^(eA[z*ea_zs + m] + eB[z*eb_zs + n/2] + eshift) before it is added or stored; fp16
+// operands require it (their rows are stored with power-of-two scales).
 struct UmmaScale {
   const int* eA;
   const int* eB;
@@ -170,6 +172,11 @@ cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, 
                        cudaStream_t st);
 cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float* hi, float* lo, int64_t Kpad,
                     cudaStream_t st);
+// fp16 pieces with one power-of-two exponent per (complex) row; Kpad a multiple of 64
+cudaError_t split_rows_f16(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, void* hi,
+                           void* lo, int64_t Kpad, int* ex, cudaStream_t st);
+cudaError_t embed_conj_f16(const void* src, bool src_c128, int64_t rows, int64_t K, void* hi, void* lo, int64_t Kpad,
+                           int* ex, cudaStream_t st);
 cudaError_t embed_t_batched(const void* src, bool src_c128, int64_t count, int64_t K, int64_t N, int64_t ld,
                             int64_t zs, float* hi, float* lo, int64_t Kpad, int64_t ds, cudaStream_t st);
 cudaError_t embed_conj_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,

@@ -66,7 +66,10 @@ struct UmmaArgs {
   int klast8;          // persistent kernel: K = 8 steps of the last k-block that hold data (1..4)
   uint32_t spin;       // persistent kernel: iteration limit of the pipeline waits (the teardown waits use
                        // UM_SPIN_LIMIT)
-  // fp64 output only: D[m][n] is scaled by 2^(eA[m] + eB[n/2] + eshift) (emulated FP64 products)
+  int f16;             // persistent kernel: operands are fp16 (kind::f16), else tf32 (kind::tf32)
+  int bke;             // elements per k-block (one 128-byte swizzle row): 32 (tf32) or 64 (fp16)
+  // eA != null: D[m][n] is scaled by 2^(eA[m] + eB[n/2] + eshift) (operands stored with
+  // power-of-two row scales: digit-split FP64 products, fp16 pieces)
   const int* eA;
   const int* eB;
   int64_t ea_zs, eb_zs;
@@ -122,6 +125,20 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
+}
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// one K-step (32 bytes of K: 8 tf32 or 16 fp16) of the chosen kind
+__device__ __forceinline__ void umma_step(bool f16, uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc) {
+  if (f16) umma_f16(tmem_d, adesc, bdesc, idesc, acc);
+  else umma_tf32(tmem_d, adesc, bdesc, idesc, acc);
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -423,12 +440,20 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
     }
     float* C = (float*)a.C;
     const float al = (float)a.alpha;
+    // scaled operands: column exponent here, row exponent per row below
+    int myexp = 0, colexp = 0;
+    if (a.eA) {
+      if (lane < nrow) myexp = a.eA[(int64_t)z * a.ea_zs + r0 + lane];
+      if (colok) colexp = a.eB[(int64_t)z * a.eb_zs + (n >> 1)] + a.eshift;
+    }
+    const bool scaled = a.eA != nullptr;
     if (a.C_lo) {
 #pragma unroll 8
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+        const int re_ = __shfl_sync(0xffffffffu, myexp, r);
         if (r < nrow && colok) {
-          const float v = al * stg[r * 33 + lane];
+          const float v = scaled ? ldexpf(al * stg[r * 33 + lane], re_ + colexp) : al * stg[r * 33 + lane];
           const float h = tf32_rna_dev(v);
           C[base + coff] = h;
           a.C_lo[base + coff] = tf32_rna_dev(v - h);
@@ -445,14 +470,18 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
           const int64_t base = __shfl_sync(0xffffffffu, myoff, h + r);
-          if (h + r < nrow && colok) C[base + coff] = old[r] + al * stg[(h + r) * 33 + lane];
+          const int re_ = __shfl_sync(0xffffffffu, myexp, h + r);
+          const float v = al * stg[(h + r) * 33 + lane];
+          if (h + r < nrow && colok) C[base + coff] = old[r] + (scaled ? ldexpf(v, re_ + colexp) : v);
         }
       }
     } else {
 #pragma unroll 8
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
-        if (r < nrow && colok) C[base + coff] = al * stg[r * 33 + lane];
+        const int re_ = __shfl_sync(0xffffffffu, myexp, r);
+        const float v = al * stg[r * 33 + lane];
+        if (r < nrow && colok) C[base + coff] = scaled ? ldexpf(v, re_ + colexp) : v;
       }
     }
   }
@@ -549,33 +578,33 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
             const int itp = it + a.prefetch;
             if (itp < nst) {
               const int kbp = three ? kb0 + itp : kb0 + 2 * itp;
-              tma_prefetch_3d(&tA0, kbp * UM_BK, m0, za);
-              tma_prefetch_3d(&tB0, kbp * UM_BK, n0, zb);
+              tma_prefetch_3d(&tA0, kbp * a.bke, m0, za);
+              tma_prefetch_3d(&tB0, kbp * a.bke, n0, zb);
               if (three) {
-                tma_prefetch_3d(&tA1, kbp * UM_BK, m0, za);
-                tma_prefetch_3d(&tB1, kbp * UM_BK, n0, zb);
+                tma_prefetch_3d(&tA1, kbp * a.bke, m0, za);
+                tma_prefetch_3d(&tB1, kbp * a.bke, n0, zb);
               } else if (2 * itp + 1 < nkb) {
-                tma_prefetch_3d(&tA0, (kbp + 1) * UM_BK, m0, za);
-                tma_prefetch_3d(&tB0, (kbp + 1) * UM_BK, n0, zb);
+                tma_prefetch_3d(&tA0, (kbp + 1) * a.bke, m0, za);
+                tma_prefetch_3d(&tB0, (kbp + 1) * a.bke, n0, zb);
               }
             }
           }
           if (three) {
             const int kb = kb0 + it;
             mbar_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
-            tma_load_3d(st, &tA0, &full[s], kb * UM_BK, m0, za);
-            tma_load_3d(st + 2 * A_BYTES, &tB0, &full[s], kb * UM_BK, n0, zb);
-            tma_load_3d(st + A_BYTES, &tA1, &full[s], kb * UM_BK, m0, za);
-            tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tB1, &full[s], kb * UM_BK, n0, zb);
+            tma_load_3d(st, &tA0, &full[s], kb * a.bke, m0, za);
+            tma_load_3d(st + 2 * A_BYTES, &tB0, &full[s], kb * a.bke, n0, zb);
+            tma_load_3d(st + A_BYTES, &tA1, &full[s], kb * a.bke, m0, za);
+            tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tB1, &full[s], kb * a.bke, n0, zb);
           } else {
             const int kb = kb0 + 2 * it;
             const bool two = 2 * it + 1 < nkb;
             mbar_expect_tx(&full[s], two ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES);
-            tma_load_3d(st, &tA0, &full[s], kb * UM_BK, m0, za);
-            tma_load_3d(st + 2 * A_BYTES, &tB0, &full[s], kb * UM_BK, n0, zb);
+            tma_load_3d(st, &tA0, &full[s], kb * a.bke, m0, za);
+            tma_load_3d(st + 2 * A_BYTES, &tB0, &full[s], kb * a.bke, n0, zb);
             if (two) {
-              tma_load_3d(st + A_BYTES, &tA0, &full[s], (kb + 1) * UM_BK, m0, za);
-              tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tB0, &full[s], (kb + 1) * UM_BK, n0, zb);
+              tma_load_3d(st + A_BYTES, &tA0, &full[s], (kb + 1) * a.bke, m0, za);
+              tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tB0, &full[s], (kb + 1) * a.bke, n0, zb);
             }
           }
         }
@@ -585,8 +614,11 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // instruction descriptor: D fp32, A/B tf32, both K-major, N = BN, M = 128
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+      // instruction descriptor: D fp32, A/B tf32 (format 2) or fp16 (format 0), both
+      // K-major, N = BN, M = 128
+      const bool f16 = a.f16 != 0;
+      const uint32_t fmt = f16 ? 0u : 2u;
+      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
                              ((uint32_t)(UM_BM >> 4) << 24);
       uint32_t g = 0;
       uint32_t cg[2] = {0u, 0u};   // chunks issued so far into each group's buffers
@@ -616,17 +648,17 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           uint8_t* st = sStage + s * Cf::STAGE;
           const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_BYTES);
           const uint64_t bh = sw128_desc(st + 2 * A_BYTES), bl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
-          // K = 8 per MMA; the zero padding of the last k-block of the K range is skipped
+          // 32 bytes of K per MMA; the zero padding of the last k-block of the K range is skipped
           const int kb_first = three ? kb0 + it : kb0 + 2 * it;
           const int nk1 = kb_first == a.kblocks - 1 ? a.klast8 : UM_BK / 8;
 #pragma unroll
           for (int kk = 0; kk < UM_BK / 8; ++kk) {
             if (kk < nk1) {
               const uint64_t o = (uint64_t)(kk * 2);
-              umma_tf32(d, ah + o, bh + o, idesc, (!chunk_first || kk > 0) ? 1u : 0u);   // hi * hi (first k-block)
+              umma_step(f16, d, ah + o, bh + o, idesc, (!chunk_first || kk > 0) ? 1u : 0u);   // hi * hi
               if (three) {
-                umma_tf32(d, ah + o, bl + o, idesc, 1u);                                   // hi * lo
-                umma_tf32(d, al + o, bh + o, idesc, 1u);                                   // lo * hi
+                umma_step(f16, d, ah + o, bl + o, idesc, 1u);                                   // hi * lo
+                umma_step(f16, d, al + o, bh + o, idesc, 1u);                                   // lo * hi
               }
             }
           }
@@ -636,7 +668,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
             for (int kk = 0; kk < UM_BK / 8; ++kk) {
               if (kk < nk2) {
                 const uint64_t o = (uint64_t)(kk * 2);
-                umma_tf32(d, al + o, bl + o, idesc, 1u);                                 // second k-block
+                umma_step(f16, d, al + o, bl + o, idesc, 1u);                                 // second k-block
               }
             }
           }
@@ -783,12 +815,14 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
               }
             }
           } else if (rok) {
+            const int rexp = a.eA ? a.eA[(int64_t)z * a.ea_zs + row] + a.eshift : 0;
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const float re = al * __uint_as_float(v[j]), im = al * __uint_as_float(v[j + 1]);
+                const float sc = a.eA ? ldexpf(al, rexp + a.eB[(int64_t)z * a.eb_zs + (n >> 1)]) : al;
+                const float re = sc * __uint_as_float(v[j]), im = sc * __uint_as_float(v[j + 1]);
                 if (a.C_lo) {
                   const float hr = tf32_rna_dev(re), hi_ = tf32_rna_dev(im);
                   *(float2*)(C + off) = make_float2(hr, hi_);
@@ -859,17 +893,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D fp32 tensor map {kdim, rows, batch} with row stride ld and batch stride bs (elements)
-static bool make_map(CUtensorMap* m, const float* base, int64_t kdim, int64_t rows, int64_t batch, int64_t ld,
-                     int64_t bs, uint32_t box_rows) {
+// 3-D tensor map {kdim, rows, batch} of fp32 (or fp16) elements with row stride ld and
+// batch stride bs (elements); the box is one 128-byte row of K by box_rows rows
+static bool make_map(CUtensorMap* m, const void* base, int64_t kdim, int64_t rows, int64_t batch, int64_t ld,
+                     int64_t bs, uint32_t box_rows, bool f16) {
   auto fn = encode_fn();
   if (!fn) return false;
-  if (((uintptr_t)base & 15) || (ld * 4) % 16 || (bs * 4) % 16) return false;
+  const int64_t esz = f16 ? 2 : 4;
+  if (((uintptr_t)base & 15) || (ld * esz) % 16 || (bs * esz) % 16) return false;
   cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)(batch > 0 ? batch : 1)};
-  cuuint64_t strides[2] = {(cuuint64_t)(ld * 4), (cuuint64_t)((batch > 1 ? bs : ld * rows) * 4)};
-  cuuint32_t box[3] = {(cuuint32_t)UM_BK, box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * esz), (cuuint64_t)((batch > 1 ? bs : ld * rows) * esz)};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / esz), box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+  CUresult r = fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims,
+                  strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -925,10 +962,11 @@ static cudaError_t umma_launch(int bn, const UmmaOperand& A, const UmmaOperand& 
                                const UmmaArgs& a, int batch, cudaStream_t st) {
   CUtensorMap maps[4];
   const uint32_t box = (uint32_t)bn;
-  if (!make_map(&maps[0], A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
-      !make_map(&maps[1], nseg > 1 ? A.lo : A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM) ||
-      !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, box) ||
-      !make_map(&maps[3], nseg > 1 ? B.lo : B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, box))
+  const bool f16 = a.f16 != 0;
+  if (!make_map(&maps[0], A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM, f16) ||
+      !make_map(&maps[1], nseg > 1 ? A.lo : A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM, f16) ||
+      !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, box, f16) ||
+      !make_map(&maps[3], nseg > 1 ? B.lo : B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, box, f16))
     return cudaErrorInvalidValue;
   switch (bn) {
     case 256: return launch_bn<256>(maps, a, batch, st);
@@ -1018,12 +1056,18 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1, int64_t col_inner,
                       int64_t col_s1, float* C_lo, const UmmaScale* scale, int64_t kvalid) {
-  if (Kpad % UM_BK) return cudaErrorInvalidValue;
+  const bool f16 = A.f16 != 0;
+  const int bke = f16 ? 64 : UM_BK;   // elements per 128-byte k-block
+  if (B.f16 != A.f16) return cudaErrorInvalidValue;   // one MMA kind: both operands fp16 or both tf32
+  if (f16 && (!g_persistent || !scale)) return cudaErrorInvalidValue;   // fp16 pieces carry row scales
+  if (Kpad % bke) return cudaErrorInvalidValue;
   if (ksplit < 1) ksplit = 1;
   if (ksplit > 1 && (!c_fp64 || !accumulate)) return cudaErrorInvalidValue;   // split partials add atomically
   if ((int64_t)batch * ksplit > 65535) return cudaErrorInvalidValue;
   UmmaArgs a{};
-  a.M = M; a.N = N; a.kblocks = (int)(Kpad / UM_BK); a.nseg = nseg;
+  a.M = M; a.N = N; a.kblocks = (int)(Kpad / bke); a.nseg = nseg;
+  a.f16 = f16 ? 1 : 0;
+  a.bke = bke;
   a.a_batched = A.batch > 1; a.b_batched = B.batch > 1;
   a.C = C; a.c_fp64 = c_fp64; a.accumulate = accumulate; a.alpha = alpha; a.c_ld = c_ld; a.c_zs = c_zs;
   a.ksplit = ksplit;
@@ -1043,14 +1087,15 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   a.prefetch = g_prefetch;
   a.spin = g_spin;
   {
-    // columns [kvalid, Kpad) are zero padding in both operands; whole K = 8 steps of
-    // it at the end of the last k-block are skipped
+    // columns [kvalid, Kpad) are zero padding in both operands; whole 32-byte K steps
+    // of it at the end of the last k-block are skipped
+    const int step = bke / 4;
     const int64_t kv = (kvalid > 0 && kvalid <= Kpad) ? kvalid : Kpad;
-    const int64_t in_last = kv - (int64_t)(a.kblocks - 1) * UM_BK;
-    a.klast8 = in_last <= 0 ? UM_BK / 8 : (int)((in_last + 7) / 8);
+    const int64_t in_last = kv - (int64_t)(a.kblocks - 1) * bke;
+    a.klast8 = in_last <= 0 ? 4 : (int)((in_last + step - 1) / step);
   }
   if (scale) {
-    if (!c_fp64 || !g_persistent) return cudaErrorInvalidValue;
+    if (!g_persistent) return cudaErrorInvalidValue;
     a.eA = scale->eA; a.eB = scale->eB; a.ea_zs = scale->ea_zs; a.eb_zs = scale->eb_zs; a.eshift = scale->eshift;
   }
   int bn = cost_model_bn(N);
@@ -1058,7 +1103,7 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   if (g_persistent && g_autotune) {
     const TuneKey key{M, N, batch, nseg, ksplit,
                       (c_fp64 ? 1 : 0) | (accumulate ? 2 : 0) | (a.direct ? 4 : 0) | (C_lo ? 8 : 0) |
-                          (a.a_batched ? 16 : 0) | (a.b_batched ? 32 : 0) | (scale ? 64 : 0),
+                          (a.a_batched ? 16 : 0) | (a.b_batched ? 32 : 0) | (scale ? 64 : 0) | (f16 ? 128 : 0),
                       Kpad};
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
