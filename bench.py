@@ -183,12 +183,20 @@ def device_V(sysd):
     return V
 
 
+def source_sha(precision):
+    """Hash of the sources that decide the contraction launches: the kernel and the
+    chains that call it."""
+    kern = "k_umma.cu" if precision == "split_tf32" else "k_gett.cu"
+    h = hashlib.sha256()
+    for f in (kern, "gw_api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2206_07660_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles(workload, precision):
     """Per-launch DRAM bytes of the contraction kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    kern = "k_umma.cu" if precision == "split_tf32" else "k_gett.cu"
-    src = os.path.join(ROOT, "paper_2206_07660_gb300", "csrc", kern)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    summary, if it was taken on the current sources (else None)."""
+    sha = source_sha(precision)
     path = os.path.join(ROOT, "profiles", "contraction_%s_%s.md" % (workload, precision))
     if not os.path.exists(path):
         return None

@@ -62,6 +62,7 @@ struct gw_ctx {
   float *Pchi = nullptr, *Pclo = nullptr, *VThi = nullptr, *VTlo = nullptr;
   float *Y3hi = nullptr, *Y3lo = nullptr, *W3hi = nullptr, *W3lo = nullptr;   // last Sigma step
   int64_t kpadP = 0, kpadS = 0, kpad3 = 0;
+  int pgroup = 1;   // k-points whose last P~0 step runs as one GEMM (K concatenated over k)
   size_t y3bytes = 0;
   double2 *adjA = nullptr, *adjB = nullptr, *adjC = nullptr;   // fp64 chains of the adjoints (lazy)
   // captured iteration (gw_iterate_graph): status checks are deferred while capturing
@@ -112,6 +113,8 @@ static constexpr bool kTensorSmallSteps = true;   // GW_SMALL_TENSOR / GW_SMALL_
 // rounding); the systems are processed in batches whose workspace (digit planes of
 // P~0 and of the iterate, residual, complex64 panels) stays below kRefineBytes.
 static constexpr int kRefineSteps = 2;
+static constexpr size_t kZGroupBytes = (size_t)8 << 30;
+static int g_pgroup_cap = 0;   // test hook: upper bound on the k-points per group (0: none)
 static constexpr size_t kRefineBytes = (size_t)6 << 30;
 
 #define CK(x)                                                                        \
@@ -376,7 +379,15 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   if (cfg->contract_prec == GW_SPLIT_TF32) {
     c->kpadP = (2 * n2 + 31) / 32 * 32;
     c->kpadS = (2 * (int64_t)naux + 31) / 32 * 32;
-    const size_t zb = (size_t)ntau * naux * c->kpadP * 4, vb = (size_t)2 * naux * c->kpadP * 4;
+    // the last P~0 step of pgroup k-points is one GEMM with their K ranges side by
+    // side (one FP64 read-modify-write of P~0^q per group, long K loops); the group
+    // is as large as kZGroupBytes of Z hi/lo planes allow
+    const size_t zk = (size_t)ntau * naux * c->kpadP * 4;
+    c->pgroup = (int)(kZGroupBytes / (2 * zk));
+    if (c->pgroup > nk) c->pgroup = nk;
+    if (g_pgroup_cap > 0 && c->pgroup > g_pgroup_cap) c->pgroup = g_pgroup_cap;
+    if (c->pgroup < 1) c->pgroup = 1;
+    const size_t zb = zk * c->pgroup, vb = (size_t)2 * naux * c->kpadP * 4 * c->pgroup;
     const size_t pb = (size_t)ntau * naux * c->kpadS * 4, tb = (size_t)2 * n2 * c->kpadS * 4;
     c->Zhi = (float*)need(A(zb)); c->Zlo = (float*)need(A(zb));
     c->Vhi = (float*)need(A(vb)); c->Vlo = (float*)need(A(vb));
@@ -665,10 +676,17 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
   if (!c->deferred) CK(cudaMemsetAsync(c->info + 1, 0, 4, c->st));
   const bool tca = tc && c->Vs_hi != nullptr;   // nao-sized steps on tensor cores
   if (tca) CK(build_gemb(c, Gplus, Gminus));
+  // tensor cores: the last step of G k-points at a time as one GEMM; Z and the
+  // embedded V of k-point j of a group sit at column block j of rows of length G kp
+  const int G = tc ? c->pgroup : 1;
+  const int64_t zld = tc ? G * c->kpadP : 0;
   for (int q = 0; q < nk; ++q) {
     double2* Pq = out + (size_t)q * ntau * na2;
     for (int k = 0; k < nk; ++k) {
       const int kq = c->kplus[(size_t)q * nk + k];
+      const int j = k % G;                      // column block of this k in its group
+      float* Zh = tc ? c->Zhi + j * c->kpadP : nullptr;
+      float* Zl = tc ? c->Zlo + j * c->kpadP : nullptr;
       const char* Vkq = (const char*)Vp + ((size_t)k * nk + kq) * slab * es;
       const char* Gm = (const char*)Gmp + ((size_t)(ntau - 1) * gstep + (size_t)k * n2) * es;
       if (tca) {
@@ -688,9 +706,8 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
         UmmaOperand ya{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka};
         UmmaOperand gb{c->Gp_hi + (size_t)k * ntau * per, c->Gp_lo + (size_t)k * ntau * per, 2 * (int64_t)nao, ntau, ka,
                        per};
-        CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, ya, gb, naux * nao, 2 * nao, ka, ntau, c->Zhi, false, -1.0,
-                    false, 2, (int64_t)naux * c->kpadP, 1, nao, c->kpadP, 2, 2 * (int64_t)nao, c->Zlo,
-                    2 * (int64_t)nao));
+        CK(run_umma(c, 8.0 * ntau * naux * (double)nao * n2, ya, gb, naux * nao, 2 * nao, ka, ntau, Zh, false, -1.0,
+                    false, 2, (int64_t)naux * zld, 1, nao, zld, 2, 2 * (int64_t)nao, Zl, 2 * (int64_t)nao));
       } else if (f32 && nao <= 64) {
         // Y[t][Q][d][b] = sum_a V^{k,k+q}[Q][d][a] G^{k+q}[t][a][b]   (G shared per t)
         BsmDesc b1{};
@@ -705,8 +722,8 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
         b2.A = (const float2*)Gm; b2.a_gs = -gstep; b2.a_rs = nao; b2.a_cs = 1; b2.a_shared = 1;
         b2.B = (const float2*)c->chA; b2.b_gs = slab; b2.b_es = n2; b2.b_rs = nao; b2.b_cs = 1;
         if (tc) {   // straight into the TF32 hi/lo operand of the tensor-core GEMM
-          const int64_t hk = c->kpadP / 2;
-          b2.Chi = c->Zhi; b2.Clo = c->Zlo; b2.c_gs = (int64_t)naux * hk; b2.c_es = hk; b2.c_rs = nao;
+          const int64_t hk = zld / 2;
+          b2.Chi = Zh; b2.Clo = Zl; b2.c_gs = (int64_t)naux * hk; b2.c_es = hk; b2.c_rs = nao;
         } else {
           b2.C = (float2*)c->chB; b2.c_gs = slab; b2.c_es = n2; b2.c_rs = nao;
         }
@@ -729,19 +746,24 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
       // P[t][Q][Q'] += (s/Nk) sum_{(c,b)} Z[t][Q][(c,b)] V^{k+q,k}_{bc}(Q'),
       // with V^{k+q,k}_{bc}(Q') = conj V^{k,k+q}_{cb}(Q') (pairing checked at init)
       if (tc) {
-        // tensor cores: split-TF32 real GEMM on the embedded operands
+        // tensor cores: split-TF32 real GEMM on the embedded operands, once per group
+        // of G k-points (K = their column blocks side by side)
         const int64_t kp = c->kpadP;
         if (nao > 64) {
-          CK(split_rows(c->chB, false, (int64_t)ntau * naux, n2, n2, false, c->Zhi, c->Zlo, kp, c->st));
+          CK(split_rows(c->chB, false, (int64_t)ntau * naux, n2, n2, false, Zh, Zl, kp, c->st, zld));
           count(1);
         }
-        CK(embed_conj((const char*)c->V + ((size_t)k * nk + kq) * slab * 16, true, naux, n2, c->Vhi, c->Vlo, kp,
-                      c->st));
-        UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, kp, 0};
-        UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, kp, 0};
-        CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, kp, 1, Pq, true,
-                    c->spin / nk, accumulate || k > 0, 2 * (int64_t)naux, 0, 1, 0, 0, 0, 0, nullptr, 2 * n2));
+        CK(embed_conj((const char*)c->V + ((size_t)k * nk + kq) * slab * 16, true, naux, n2, c->Vhi + j * kp,
+                      c->Vlo + j * kp, kp, c->st, zld));
         count(1);
+        if (j == G - 1 || k == nk - 1) {
+          const int g = j + 1, k0 = k - j;
+          UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, zld, 0};
+          UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, zld, 0};
+          CK(run_umma(c, 8.0 * g * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, g * kp, 1, Pq,
+                      true, c->spin / nk, accumulate || k0 > 0, 2 * (int64_t)naux, 0, 1, 0, 0, 0, 0, nullptr,
+                      (g - 1) * kp + 2 * n2));
+        }
         continue;
       }
       GettDesc d3 = base_desc((int64_t)ntau * naux, naux, n2, 1);
@@ -1585,4 +1607,12 @@ extern "C" gw_status gw_batch_iterate(gw_ctx* const* ctxs, int32_t n, int32_t n_
     if (s != GW_OK) { g_init_err = "system " + std::to_string(i) + ": " + ctxs[i]->err; return s; }
   }
   return GW_OK;
+}
+
+// Caps the number of k-points whose last P~0 step runs as one GEMM in contexts created
+// afterwards (0: no cap); returns the old cap.
+extern "C" int gwdbg_set_pgroup_cap(int cap) {
+  const int old = g_pgroup_cap;
+  g_pgroup_cap = cap < 0 ? 0 : cap;
+  return old;
 }

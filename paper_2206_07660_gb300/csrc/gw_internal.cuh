@@ -166,10 +166,11 @@ cudaError_t emul_split_cols(const double2* B, int64_t count, int64_t K, int64_t 
 cudaError_t emul_cgemm_batched(const float* Ad, const int* Ae, const float* Bd, const int* Be, int64_t count,
                                int64_t M, int64_t N, int64_t K, double2* C, int* err, cudaStream_t st, int nd = 8);
 
+// ldo: row stride of the output planes (0: Kpad)
 cudaError_t split_rows(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, float* hi,
-                       float* lo, int64_t Kpad, cudaStream_t st);
+                       float* lo, int64_t Kpad, cudaStream_t st, int64_t ldo = 0);
 cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, float* hi, float* lo, int64_t Kpad,
-                       cudaStream_t st);
+                       cudaStream_t st, int64_t ldo = 0);
 cudaError_t embed_t(const void* src, bool src_c128, int64_t K, int64_t N, float* hi, float* lo, int64_t Kpad,
                     cudaStream_t st);
 // fp16 pieces with one power-of-two exponent per (complex) row; Kpad a multiple of 64

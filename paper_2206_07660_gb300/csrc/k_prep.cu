@@ -21,10 +21,11 @@ __device__ __forceinline__ void split2(double x, float& hi, float& lo) {
 }
 
 // Rows of a complex matrix (element (r, k) at src + r*ld + k, complex units) into
-// real hi/lo rows of length Kpad (zero padded): out[r][2k + s] = (re, +-im).
+// real hi/lo rows of length Kpad (zero padded) at row stride ldo: out[r][2k + s] =
+// (re, +-im).
 template <typename T>
 __global__ void split_rows_kernel(const T* __restrict__ src, int64_t rows, int64_t K, int64_t ld, int conj,
-                                  float* hi, float* lo, int64_t Kpad) {
+                                  float* hi, float* lo, int64_t Kpad, int64_t ldo) {
   const int64_t tot = rows * Kpad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / Kpad, c = e - r * Kpad;
@@ -35,16 +36,16 @@ __global__ void split_rows_kernel(const T* __restrict__ src, int64_t rows, int64
     }
     float h, l;
     split2(v, h, l);
-    hi[e] = h;
-    if (lo) lo[e] = l;
+    hi[r * ldo + c] = h;
+    if (lo) lo[r * ldo + c] = l;
   }
 }
 
 // Doubled operand of C = A conj(B)^T from B (rows n, complex K): rows 2n = (re, im),
-// rows 2n+1 = (-im, re).
+// rows 2n+1 = (-im, re), Kpad floats each at row stride ldo.
 template <typename T>
 __global__ void embed_conj_kernel(const T* __restrict__ src, int64_t rows, int64_t K, float* hi, float* lo,
-                                  int64_t Kpad) {
+                                  int64_t Kpad, int64_t ldo) {
   const int64_t tot = 2 * rows * Kpad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r2 = e / Kpad, c = e - r2 * Kpad, n = r2 >> 1;
@@ -56,8 +57,8 @@ __global__ void embed_conj_kernel(const T* __restrict__ src, int64_t rows, int64
     }
     float h, l;
     split2(v, h, l);
-    hi[e] = h;
-    if (lo) lo[e] = l;
+    hi[r2 * ldo + c] = h;
+    if (lo) lo[r2 * ldo + c] = l;
   }
 }
 
@@ -154,15 +155,21 @@ __global__ void embed_t_kernel(const T* __restrict__ src, int64_t K, int64_t N, 
 static inline int nb_(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 152 * 16 ? b : 152 * 16); }
 
 cudaError_t split_rows(const void* src, bool src_c128, int64_t rows, int64_t K, int64_t ld, bool conj, float* hi,
-                       float* lo, int64_t Kpad, cudaStream_t st) {
-  if (src_c128) split_rows_kernel<double2><<<nb_(rows * Kpad), 256, 0, st>>>((const double2*)src, rows, K, ld, conj, hi, lo, Kpad);
-  else split_rows_kernel<float2><<<nb_(rows * Kpad), 256, 0, st>>>((const float2*)src, rows, K, ld, conj, hi, lo, Kpad);
+                       float* lo, int64_t Kpad, cudaStream_t st, int64_t ldo) {
+  if (ldo <= 0) ldo = Kpad;
+  if (src_c128)
+    split_rows_kernel<double2><<<nb_(rows * Kpad), 256, 0, st>>>((const double2*)src, rows, K, ld, conj, hi, lo, Kpad, ldo);
+  else
+    split_rows_kernel<float2><<<nb_(rows * Kpad), 256, 0, st>>>((const float2*)src, rows, K, ld, conj, hi, lo, Kpad, ldo);
   return cudaGetLastError();
 }
 cudaError_t embed_conj(const void* src, bool src_c128, int64_t rows, int64_t K, float* hi, float* lo, int64_t Kpad,
-                       cudaStream_t st) {
-  if (src_c128) embed_conj_kernel<double2><<<nb_(2 * rows * Kpad), 256, 0, st>>>((const double2*)src, rows, K, hi, lo, Kpad);
-  else embed_conj_kernel<float2><<<nb_(2 * rows * Kpad), 256, 0, st>>>((const float2*)src, rows, K, hi, lo, Kpad);
+                       cudaStream_t st, int64_t ldo) {
+  if (ldo <= 0) ldo = Kpad;
+  if (src_c128)
+    embed_conj_kernel<double2><<<nb_(2 * rows * Kpad), 256, 0, st>>>((const double2*)src, rows, K, hi, lo, Kpad, ldo);
+  else
+    embed_conj_kernel<float2><<<nb_(2 * rows * Kpad), 256, 0, st>>>((const float2*)src, rows, K, hi, lo, Kpad, ldo);
   return cudaGetLastError();
 }
 cudaError_t embed_conj_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,

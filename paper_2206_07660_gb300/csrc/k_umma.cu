@@ -446,14 +446,30 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
       if (lane < nrow) myexp = a.eA[(int64_t)z * a.ea_zs + r0 + lane];
       if (colok) colexp = a.eB[(int64_t)z * a.eb_zs + (n >> 1)] + a.eshift;
     }
-    const bool scaled = a.eA != nullptr;
-    if (a.C_lo) {
+    if (a.eA) {
+      // scaled operands: the row factor 2^eA (shuffled per row) times the column
+      // factor 2^(eB + eshift), both exact powers of two
+      const float rsc = ldexpf(1.0f, myexp), csc = ldexpf(al, colexp);
+      for (int r = 0; r < 32; ++r) {
+        const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+        const float rs = __shfl_sync(0xffffffffu, rsc, r);
+        if (r < nrow && colok) {
+          const float v = stg[r * 33 + lane] * csc * rs;
+          if (a.C_lo) {
+            const float h = tf32_rna_dev(v);
+            C[base + coff] = h;
+            a.C_lo[base + coff] = tf32_rna_dev(v - h);
+          } else {
+            C[base + coff] = a.accumulate ? C[base + coff] + v : v;
+          }
+        }
+      }
+    } else if (a.C_lo) {
 #pragma unroll 8
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
-        const int re_ = __shfl_sync(0xffffffffu, myexp, r);
         if (r < nrow && colok) {
-          const float v = scaled ? ldexpf(al * stg[r * 33 + lane], re_ + colexp) : al * stg[r * 33 + lane];
+          const float v = al * stg[r * 33 + lane];
           const float h = tf32_rna_dev(v);
           C[base + coff] = h;
           a.C_lo[base + coff] = tf32_rna_dev(v - h);
@@ -470,18 +486,14 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
           const int64_t base = __shfl_sync(0xffffffffu, myoff, h + r);
-          const int re_ = __shfl_sync(0xffffffffu, myexp, h + r);
-          const float v = al * stg[(h + r) * 33 + lane];
-          if (h + r < nrow && colok) C[base + coff] = old[r] + (scaled ? ldexpf(v, re_ + colexp) : v);
+          if (h + r < nrow && colok) C[base + coff] = old[r] + al * stg[(h + r) * 33 + lane];
         }
       }
     } else {
 #pragma unroll 8
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
-        const int re_ = __shfl_sync(0xffffffffu, myexp, r);
-        const float v = al * stg[r * 33 + lane];
-        if (r < nrow && colok) C[base + coff] = scaled ? ldexpf(v, re_ + colexp) : v;
+        if (r < nrow && colok) C[base + coff] = al * stg[r * 33 + lane];
       }
     }
   }
@@ -814,15 +826,32 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
                 }
               }
             }
-          } else if (rok) {
-            const int rexp = a.eA ? a.eA[(int64_t)z * a.ea_zs + row] + a.eshift : 0;
+          } else if (rok && a.eA) {
+            // scaled operands: 2^(eA[row] + eB[column pair] + eshift), exact powers of two
+            const float rsc = ldexpf(al, a.eA[(int64_t)z * a.ea_zs + row] + a.eshift);
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const float sc = a.eA ? ldexpf(al, rexp + a.eB[(int64_t)z * a.eb_zs + (n >> 1)]) : al;
+                const float sc = rsc * ldexpf(1.0f, a.eB[(int64_t)z * a.eb_zs + (n >> 1)]);
                 const float re = sc * __uint_as_float(v[j]), im = sc * __uint_as_float(v[j + 1]);
+                if (a.C_lo) {
+                  const float hr = tf32_rna_dev(re), hi_ = tf32_rna_dev(im);
+                  *(float2*)(C + off) = make_float2(hr, hi_);
+                  *(float2*)(a.C_lo + off) = make_float2(tf32_rna_dev(re - hr), tf32_rna_dev(im - hi_));
+                } else {
+                  *(float2*)(C + off) = make_float2(re, im);
+                }
+              }
+            }
+          } else if (rok) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const int n = n0 + cbase + cb + j;
+              if (cb + j < BW && n < a.N) {
+                const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
+                const float re = al * __uint_as_float(v[j]), im = al * __uint_as_float(v[j + 1]);
                 if (a.C_lo) {
                   const float hr = tf32_rna_dev(re), hi_ = tf32_rna_dev(im);
                   *(float2*)(C + off) = make_float2(hr, hi_);
