@@ -882,17 +882,18 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
         const int64_t kp = c->kpadS;
         CK(embed_t((const char*)c->V + ((size_t)k * nk + kmq) * slab * 16, true, naux, n2, c->VThi, c->VTlo, kp,
                    c->st));
-        UmmaOperand oa{c->Pchi, c->Pclo, naux, ntau, kp, (int64_t)naux * kp};
+        // V is shared by all t: the rows (t, Q') of every t form one M = ntau naux
+        UmmaOperand oa{c->Pchi, c->Pclo, (int64_t)ntau * naux, 1, kp, 0};
         UmmaOperand ob{c->VThi, c->VTlo, 2 * n2, 1, kp, 0};
         if (tc2) {
           // X written as TF32 hi/lo rows (t, Q', i) of length kpadA: the A operand of the next step
           const int64_t ka = c->kpadA;
-          CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, naux, (int)(2 * n2), kp, ntau, c->Xs_hi, false,
-                      1.0, false, (int64_t)nao * ka, (int64_t)naux * nao * ka, 1, 0, 0, 2 * (int64_t)nao, ka,
-                      c->Xs_lo, 2 * (int64_t)naux));
+          CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, (int)(2 * n2), kp, 1, c->Xs_hi,
+                      false, 1.0, false, (int64_t)nao * ka, 0, 1, 0, 0, 2 * (int64_t)nao, ka, c->Xs_lo,
+                      2 * (int64_t)naux));
         } else {
-          CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, naux, (int)(2 * n2), kp, ntau, c->chA, false,
-                      1.0, false, 2 * n2, (int64_t)naux * 2 * n2, 1, 0, 0, 0, 0, nullptr, 2 * (int64_t)naux));
+          CK(run_umma(c, 8.0 * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, (int)(2 * n2), kp, 1, c->chA,
+                      false, 1.0, false, 2 * n2, 0, 1, 0, 0, 0, 0, nullptr, 2 * (int64_t)naux));
         }
         count(1);
       } else {
