@@ -154,16 +154,17 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
 // FP64 complex products on tensor cores by exact digit splitting (k_emul.cu)
 int64_t emul_kpad(int64_t K);
 size_t emul_digit_bytes(int64_t rows, int64_t K);
-cudaError_t emul_split_b(const double2* B, int64_t rows, int64_t K, int64_t ldb, float* dig, int* ex, cudaStream_t st);
-cudaError_t emul_transform(const float* Bd, const int* Be, int64_t nrow, const double2* X, int64_t K, int64_t ncol,
-                           int64_t ldx, double2* Y, int64_t ldy, float* Ad, int* Ae, int* err, cudaStream_t st);
+// digit planes are fp16 arrays (emul_digit_bytes), passed as untyped pointers
+cudaError_t emul_split_b(const double2* B, int64_t rows, int64_t K, int64_t ldb, void* dig, int* ex, cudaStream_t st);
+cudaError_t emul_transform(const void* Bd, const int* Be, int64_t nrow, const double2* X, int64_t K, int64_t ncol,
+                           int64_t ldx, double2* Y, int64_t ldy, void* Ad, int* Ae, int* err, cudaStream_t st);
 // tensor-core launches of one product with complex K and nd digits (-1: K too large)
 int emul_launches(int64_t K, int nd = 8);
 cudaError_t emul_split_rows(const double2* A, int64_t count, int64_t M, int64_t K, int64_t lda, int64_t sa,
-                            float* Ad, int* Ae, cudaStream_t st);
+                            void* Ad, int* Ae, cudaStream_t st);
 cudaError_t emul_split_cols(const double2* B, int64_t count, int64_t K, int64_t N, int64_t ldb, int64_t sb,
-                            float* Bd, int* Be, cudaStream_t st);
-cudaError_t emul_cgemm_batched(const float* Ad, const int* Ae, const float* Bd, const int* Be, int64_t count,
+                            void* Bd, int* Be, cudaStream_t st);
+cudaError_t emul_cgemm_batched(const void* Ad, const int* Ae, const void* Bd, const int* Be, int64_t count,
                                int64_t M, int64_t N, int64_t K, double2* C, int* err, cudaStream_t st, int nd = 8);
 
 // ldo: row stride of the output planes (0: Kpad)

@@ -17,6 +17,9 @@
 //
 // Operand layout: digit planes of a row are stored one after another,
 // [row][S][Kp] (Kp = padded real K), so the K range of a launch is contiguous.
+// The digits are stored as fp16 (exact for |d| <= 2048) and multiplied with
+// tcgen05 kind::f16 (FP32 accumulation): half the bytes of TF32 storage and twice
+// the tensor rate, with the same exact sums.
 // B's planes are stored in reverse digit order so that the B slices that pair
 // with A slices i0..i1 of a launch are contiguous as well.
 //
@@ -25,9 +28,12 @@
 // output written transposed into Y (lane-per-row FP64 stores); and for the batched
 // square products C[z] = A[z] B[z] of the screened solve's refinement (A split from
 // its rows, B from its columns, output row-major).
+#include <cuda_fp16.h>
 #include "gw_internal.cuh"
 
 namespace gwk {
+
+using dig_t = __half;   // storage of one digit
 
 constexpr int EM_BETA = 7;
 constexpr int EM_S = 8;
@@ -61,7 +67,7 @@ __device__ __forceinline__ int em_exponent(double m) {
 // all K; the source tile goes through shared memory so both the reads (along n)
 // and the digit writes (along k) are coalesced.
 __global__ void __launch_bounds__(256) em_split_t_kernel(const double2* __restrict__ src, int64_t K, int64_t ncol,
-                                                         int64_t ld, int64_t zs, float* __restrict__ dig,
+                                                         int64_t ld, int64_t zs, dig_t* __restrict__ dig,
                                                          int* __restrict__ ex, int64_t Kp) {
   __shared__ double2 tile[32][33];
   __shared__ double red[8][32];
@@ -69,7 +75,7 @@ __global__ void __launch_bounds__(256) em_split_t_kernel(const double2* __restri
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t z = blockIdx.y;
   const double2* X = src + z * zs;
-  float* D = dig + z * ncol * (int64_t)EM_S * Kp;
+  dig_t* D = dig + z * ncol * (int64_t)EM_S * Kp;
   int* E = ex + z * ncol;
   const int64_t n0 = (int64_t)blockIdx.x * 32;
   const int64_t n = n0 + tx;
@@ -104,9 +110,9 @@ __global__ void __launch_bounds__(256) em_split_t_kernel(const double2* __restri
         float dr[EM_S], di[EM_S];
         em_digits(v.x, es[rr], dr);
         em_digits(v.y, es[rr], di);
-        float* o = D + row * rowlen + 2 * j;
+        dig_t* o = D + row * rowlen + 2 * j;
 #pragma unroll
-        for (int i = 0; i < EM_S; ++i) *(float2*)(o + (int64_t)i * Kp) = make_float2(dr[i], di[i]);
+        for (int i = 0; i < EM_S; ++i) *(__half2*)(o + (int64_t)i * Kp) = __floats2half2_rn(dr[i], di[i]);
       }
     }
     __syncthreads();
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(256) em_split_t_kernel(const double2* __restri
 // ldb): rows 2m = (Br, -Bi), 2m+1 = (Bi, Br) along the real K index 2j + c;
 // digit planes in reverse order; one exponent per complex row m.
 __global__ void em_split_b_kernel(const double2* __restrict__ B, int64_t rows, int64_t K, int64_t ldb,
-                                  float* __restrict__ dig, int* __restrict__ ex, int64_t Kp) {
+                                  dig_t* __restrict__ dig, int* __restrict__ ex, int64_t Kp) {
   const int64_t m = blockIdx.x;
   __shared__ double red[256];
   double mx = 0.0;
@@ -139,13 +145,13 @@ __global__ void em_split_b_kernel(const double2* __restrict__ B, int64_t rows, i
     float dr[EM_S], di[EM_S];
     em_digits(v.x, e, dr);
     em_digits(v.y, e, di);
-    float* r0 = dig + (2 * m) * rowlen + 2 * j;
-    float* r1 = dig + (2 * m + 1) * rowlen + 2 * j;
+    dig_t* r0 = dig + (2 * m) * rowlen + 2 * j;
+    dig_t* r1 = dig + (2 * m + 1) * rowlen + 2 * j;
 #pragma unroll
     for (int i = 0; i < EM_S; ++i) {
       const int64_t p = (int64_t)(EM_S - 1 - i) * Kp;   // reverse digit order
-      *(float2*)(r0 + p) = make_float2(dr[i], -di[i]);
-      *(float2*)(r1 + p) = make_float2(di[i], dr[i]);
+      *(__half2*)(r0 + p) = __floats2half2_rn(dr[i], -di[i]);
+      *(__half2*)(r1 + p) = __floats2half2_rn(di[i], dr[i]);
     }
   }
 }
@@ -155,7 +161,7 @@ __global__ void em_split_b_kernel(const double2* __restrict__ B, int64_t rows, i
 // written as zeros.
 __global__ void __launch_bounds__(256) em_split_r_kernel(const double2* __restrict__ src, int64_t rows, int64_t K,
                                                          int64_t ld, int64_t zs, int64_t count,
-                                                         float* __restrict__ dig, int* __restrict__ ex, int64_t Kp) {
+                                                         dig_t* __restrict__ dig, int* __restrict__ ex, int64_t Kp) {
   const int lane = threadIdx.x & 31;
   const int64_t gr = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (gr >= rows * count) return;
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(256) em_split_r_kernel(const double2* __restri
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   const int e = em_exponent(m);
   if (lane == 0) ex[gr] = e;
-  float* o = dig + gr * (int64_t)EM_S * Kp;
+  dig_t* o = dig + gr * (int64_t)EM_S * Kp;
   for (int64_t k = lane; 2 * k < Kp; k += 32) {
     float dr[EM_S], di[EM_S];
     if (k < K) {
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(256) em_split_r_kernel(const double2* __restri
       for (int i = 0; i < EM_S; ++i) dr[i] = di[i] = 0.f;
     }
 #pragma unroll
-    for (int i = 0; i < EM_S; ++i) *(float2*)(o + (int64_t)i * Kp + 2 * k) = make_float2(dr[i], di[i]);
+    for (int i = 0; i < EM_S; ++i) *(__half2*)(o + (int64_t)i * Kp + 2 * k) = __floats2half2_rn(dr[i], di[i]);
   }
 }
 
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(256) em_split_r_kernel(const double2* __restri
 // column j.  Block: 32 columns x all K through a shared-memory tile (reads along j,
 // digit writes along k); padding columns [2K, Kp) are written as zeros.
 __global__ void __launch_bounds__(256) em_split_bt_kernel(const double2* __restrict__ src, int64_t K, int64_t ncol,
-                                                          int64_t ld, int64_t zs, float* __restrict__ dig,
+                                                          int64_t ld, int64_t zs, dig_t* __restrict__ dig,
                                                           int* __restrict__ ex, int64_t Kp) {
   __shared__ double2 tile[32][33];
   __shared__ double red[8][32];
@@ -201,7 +207,7 @@ __global__ void __launch_bounds__(256) em_split_bt_kernel(const double2* __restr
   const int64_t z = blockIdx.y;
   const double2* X = src + z * zs;
   const int64_t rowlen = (int64_t)EM_S * Kp;
-  float* D = dig + z * 2 * ncol * rowlen;
+  dig_t* D = dig + z * 2 * ncol * rowlen;
   int* E = ex + z * ncol;
   const int64_t n0 = (int64_t)blockIdx.x * 32;
   const int64_t n = n0 + tx;
@@ -235,13 +241,13 @@ __global__ void __launch_bounds__(256) em_split_bt_kernel(const double2* __restr
         float dr[EM_S], di[EM_S];
         em_digits(v.x, es[rr], dr);
         em_digits(v.y, es[rr], di);
-        float* r0 = D + (2 * col) * rowlen + 2 * j;
-        float* r1 = r0 + rowlen;
+        dig_t* r0 = D + (2 * col) * rowlen + 2 * j;
+        dig_t* r1 = r0 + rowlen;
 #pragma unroll
         for (int i = 0; i < EM_S; ++i) {
           const int64_t p = (int64_t)(EM_S - 1 - i) * Kp;
-          *(float2*)(r0 + p) = make_float2(dr[i], -di[i]);
-          *(float2*)(r1 + p) = make_float2(di[i], dr[i]);
+          *(__half2*)(r0 + p) = __floats2half2_rn(dr[i], -di[i]);
+          *(__half2*)(r1 + p) = __floats2half2_rn(di[i], dr[i]);
         }
       }
     }
@@ -283,15 +289,16 @@ int emul_launches(int64_t K, int nd) {
   return em_plan(2 * K, pl, nd);
 }
 
-int64_t emul_kpad(int64_t K) { return (2 * K + 31) / 32 * 32; }
-size_t emul_digit_bytes(int64_t rows, int64_t K) { return (size_t)rows * EM_S * emul_kpad(K) * 4; }
+// real K padded to whole 128-byte k-blocks of fp16
+int64_t emul_kpad(int64_t K) { return (2 * K + 63) / 64 * 64; }
+size_t emul_digit_bytes(int64_t rows, int64_t K) { return (size_t)rows * EM_S * emul_kpad(K) * sizeof(dig_t); }
 
-cudaError_t emul_split_b(const double2* B, int64_t rows, int64_t K, int64_t ldb, float* dig, int* ex,
+cudaError_t emul_split_b(const double2* B, int64_t rows, int64_t K, int64_t ldb, void* dig, int* ex,
                          cudaStream_t st) {
   const int64_t Kp = emul_kpad(K);
-  cudaError_t e = cudaMemsetAsync(dig, 0, (size_t)2 * rows * EM_S * Kp * 4, st);
+  cudaError_t e = cudaMemsetAsync(dig, 0, emul_digit_bytes(2 * rows, K), st);
   if (e != cudaSuccess) return e;
-  em_split_b_kernel<<<(unsigned)rows, 256, 0, st>>>(B, rows, K, ldb, dig, ex, Kp);
+  em_split_b_kernel<<<(unsigned)rows, 256, 0, st>>>(B, rows, K, ldb, (dig_t*)dig, ex, Kp);
   return cudaGetLastError();
 }
 
@@ -299,9 +306,11 @@ cudaError_t emul_split_b(const double2* B, int64_t rows, int64_t K, int64_t ldb,
 // stride ldx), FP64-exact up to ~2^-54 relative.  Bd/Be: digits and exponents of T
 // from emul_split_b (2*nrow rows).  Ad/Ae: workspace of emul_digit_bytes(ncol, K)
 // bytes (zeroed once by the caller: the padding columns must stay zero) and ncol ints.
-cudaError_t emul_transform(const float* Bd, const int* Be, int64_t nrow, const double2* X, int64_t K, int64_t ncol,
-                           int64_t ldx, double2* Y, int64_t ldy, float* Ad, int* Ae, int* err, cudaStream_t st) {
+cudaError_t emul_transform(const void* Bdv, const int* Be, int64_t nrow, const double2* X, int64_t K, int64_t ncol,
+                           int64_t ldx, double2* Y, int64_t ldy, void* Adv, int* Ae, int* err, cudaStream_t st) {
   if (ldy != ncol) return cudaErrorInvalidValue;   // transposed lane-per-row stores assume packed rows
+  const dig_t* Bd = (const dig_t*)Bdv;
+  dig_t* Ad = (dig_t*)Adv;
   const int64_t Kp = emul_kpad(K);
   em_split_t_kernel<<<dim3((unsigned)((ncol + 31) / 32), 1), 256, 0, st>>>(X, K, ncol, ldx, 0, Ad, Ae, Kp);
   cudaError_t e = cudaGetLastError();
@@ -312,8 +321,8 @@ cudaError_t emul_transform(const float* Bd, const int* Be, int64_t nrow, const d
   if (nl < 0) return cudaErrorInvalidValue;
   for (int l = 0; l < nl; ++l) {
     const int g = pl[l].g, i0 = pl[l].i0, np = pl[l].i1 - pl[l].i0 + 1;
-    UmmaOperand oa{Ad + (int64_t)(i0 - 1) * Kp, nullptr, ncol, 1, ld, 0};
-    UmmaOperand ob{const_cast<float*>(Bd) + (int64_t)(EM_S - g + i0) * Kp, nullptr, 2 * nrow, 1, ld, 0};
+    UmmaOperand oa{(const float*)(Ad + (int64_t)(i0 - 1) * Kp), nullptr, ncol, 1, ld, 0, 1};
+    UmmaOperand ob{(const float*)(Bd + (int64_t)(EM_S - g + i0) * Kp), nullptr, 2 * nrow, 1, ld, 0, 1};
     UmmaScale sc{Ae, Be, 0, 0, -EM_BETA * g};
     e = umma_gemm(oa, ob, (int)ncol, (int)(2 * nrow), (int64_t)np * Kp, 1, (void*)Y, true, 1.0, l > 0, 2, 0, 1,
                   err, st, 1, 0, 0, 2, 2 * ldy, nullptr, &sc, (int64_t)(np - 1) * Kp + 2 * K);
@@ -327,18 +336,19 @@ cudaError_t emul_transform(const float* Bd, const int* Be, int64_t nrow, const d
 // Ad/Ae: emul_digit_bytes(M, K) and M ints per batch; Bd/Be: emul_digit_bytes(2N, K)
 // and N ints per batch.
 cudaError_t emul_split_rows(const double2* A, int64_t count, int64_t M, int64_t K, int64_t lda, int64_t sa,
-                            float* Ad, int* Ae, cudaStream_t st) {
+                            void* Ad, int* Ae, cudaStream_t st) {
   const int64_t Kp = emul_kpad(K);
   const int64_t nb = (M * count + 7) / 8;
   if (nb > INT32_MAX) return cudaErrorInvalidValue;
-  em_split_r_kernel<<<(unsigned)nb, 256, 0, st>>>(A, M, K, lda, sa, count, Ad, Ae, Kp);
+  em_split_r_kernel<<<(unsigned)nb, 256, 0, st>>>(A, M, K, lda, sa, count, (dig_t*)Ad, Ae, Kp);
   return cudaGetLastError();
 }
 cudaError_t emul_split_cols(const double2* B, int64_t count, int64_t K, int64_t N, int64_t ldb, int64_t sb,
-                            float* Bd, int* Be, cudaStream_t st) {
+                            void* Bd, int* Be, cudaStream_t st) {
   const int64_t Kp = emul_kpad(K);
   if (count > 65535) return cudaErrorInvalidValue;
-  em_split_bt_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)count), 256, 0, st>>>(B, K, N, ldb, sb, Bd, Be, Kp);
+  em_split_bt_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)count), 256, 0, st>>>(B, K, N, ldb, sb, (dig_t*)Bd,
+                                                                                        Be, Kp);
   return cudaGetLastError();
 }
 
@@ -347,16 +357,18 @@ cudaError_t emul_split_cols(const double2* B, int64_t count, int64_t K, int64_t 
 // nd = 8 digits; nd < 8 keeps the pairs with i + j <= nd + 1 of the leading nd
 // digits: each real product then errs by up to ~(nd + 1) 2^(13 - 7 (nd + 2)) of
 // max|A_row| max|B_col| (9e-11 for nd = 5).
-cudaError_t emul_cgemm_batched(const float* Ad, const int* Ae, const float* Bd, const int* Be, int64_t count,
+cudaError_t emul_cgemm_batched(const void* Adv, const int* Ae, const void* Bdv, const int* Be, int64_t count,
                                int64_t M, int64_t N, int64_t K, double2* C, int* err, cudaStream_t st, int nd) {
+  const dig_t* Ad = (const dig_t*)Adv;
+  const dig_t* Bd = (const dig_t*)Bdv;
   const int64_t Kp = emul_kpad(K), ld = (int64_t)EM_S * Kp;
   EmLaunch pl[EM_MAXL];
   const int nl = em_plan(2 * K, pl, nd);
   if (nl < 0 || count > 65535) return cudaErrorInvalidValue;
   for (int l = 0; l < nl; ++l) {
     const int g = pl[l].g, i0 = pl[l].i0, np = pl[l].i1 - pl[l].i0 + 1;
-    UmmaOperand oa{Ad + (int64_t)(i0 - 1) * Kp, nullptr, M, count, ld, M * ld};
-    UmmaOperand ob{Bd + (int64_t)(EM_S - g + i0) * Kp, nullptr, 2 * N, count, ld, 2 * N * ld};
+    UmmaOperand oa{(const float*)(Ad + (int64_t)(i0 - 1) * Kp), nullptr, M, count, ld, M * ld, 1};
+    UmmaOperand ob{(const float*)(Bd + (int64_t)(EM_S - g + i0) * Kp), nullptr, 2 * N, count, ld, 2 * N * ld, 1};
     UmmaScale sc{Ae, Be, M, N, -EM_BETA * g};
     cudaError_t e = umma_gemm(oa, ob, (int)M, (int)(2 * N), (int64_t)np * Kp, (int)count, (void*)C, true, 1.0, l > 0,
                               2 * N, 2 * M * N, 1, err, st, 1, 0, 0, 0, 0, nullptr, &sc,
@@ -377,7 +389,7 @@ extern "C" int gwdbg_emul_transform(const double2* T, const double2* X, double2*
   const int64_t Kp = emul_kpad(K);
   float *Bd = nullptr, *Ad = nullptr;
   int *Be = nullptr, *Ae = nullptr, *err = nullptr;
-  if (cudaMalloc(&Bd, (size_t)2 * nrow * EM_S * Kp * 4) || cudaMalloc(&Be, (size_t)nrow * 4) ||
+  if (cudaMalloc(&Bd, emul_digit_bytes(2 * (int64_t)nrow, K)) || cudaMalloc(&Be, (size_t)nrow * 4) ||
       cudaMalloc(&Ad, emul_digit_bytes(ncol, K)) || cudaMalloc(&Ae, (size_t)ncol * 4) || cudaMalloc(&err, 4))
     return -1;
   cudaMemset(Ad, 0, emul_digit_bytes(ncol, K));
