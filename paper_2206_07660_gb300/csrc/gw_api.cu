@@ -137,6 +137,22 @@ static void* dalloc(gw_ctx* c, size_t bytes) {
   return p;
 }
 
+// gives back one allocation made with dalloc (optional workspaces that did not fit)
+static void dfree(gw_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->owned.size(); ++i)
+    if (c->owned[i] == p) { c->owned.erase(c->owned.begin() + (long)i); break; }
+  if (c->cfg.dev_free) c->cfg.dev_free(c->cfg.alloc_user, p); else cudaFree(p);
+}
+
+// budget of one optional workspace: its cap, and at most 1/32 of the device memory
+// free when the context is created (several contexts share the device)
+static size_t opt_budget(size_t cap) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cap;
+  return fr / 32 < cap ? fr / 32 : cap;
+}
+
 static void free_all(gw_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st); else cudaDeviceSynchronize();
   for (void* p : c->owned) {
@@ -348,16 +364,6 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
       c->Tdig[i] = (float*)need(A(emul_digit_bytes(2 * (int64_t)ntau, ntau)));
       c->Texp[i] = (int*)need(A((size_t)ntau * 4));
     }
-    if (screened_refine_ok(naux)) {
-      // as many (q, Omega) systems per batch as fit in kRefineBytes
-      const int64_t cnt = (int64_t)nk * ntau;
-      const size_t per = screened_refine_bytes(naux, 1);
-      int64_t chunk = (int64_t)(kRefineBytes / per);
-      if (chunk < 1) chunk = 1;
-      if (chunk > cnt) chunk = cnt;
-      c->irws_bytes = screened_refine_bytes(naux, chunk);
-      c->irws = need(A(c->irws_bytes));
-    }
   }
   c->r = (double2*)need(A(ntau * cb));
   c->d_fn = (int*)need(A(ntau * 4)); c->d_bm = (int*)need(A(ntau * 4));
@@ -382,15 +388,22 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     // the last P~0 step of pgroup k-points is one GEMM with their K ranges side by
     // side (one FP64 read-modify-write of P~0^q per group, long K loops); the group
     // is as large as kZGroupBytes of Z hi/lo planes allow
-    const size_t zk = (size_t)ntau * naux * c->kpadP * 4;
-    c->pgroup = (int)(kZGroupBytes / (2 * zk));
+    const size_t zk = (size_t)ntau * naux * c->kpadP * 4, vk = (size_t)2 * naux * c->kpadP * 4;
+    c->pgroup = (int)(opt_budget(kZGroupBytes) / (2 * zk));
     if (c->pgroup > nk) c->pgroup = nk;
     if (g_pgroup_cap > 0 && c->pgroup > g_pgroup_cap) c->pgroup = g_pgroup_cap;
     if (c->pgroup < 1) c->pgroup = 1;
-    const size_t zb = zk * c->pgroup, vb = (size_t)2 * naux * c->kpadP * 4 * c->pgroup;
+    size_t zb = 0;
+    for (;;) {   // a smaller group when the planes do not fit (one k-point at least)
+      zb = zk * c->pgroup;
+      const size_t vb = vk * c->pgroup;
+      c->Zhi = (float*)A(zb); c->Zlo = (float*)A(zb); c->Vhi = (float*)A(vb); c->Vlo = (float*)A(vb);
+      if ((c->Zhi && c->Zlo && c->Vhi && c->Vlo) || c->pgroup == 1) break;
+      dfree(c, c->Zhi); dfree(c, c->Zlo); dfree(c, c->Vhi); dfree(c, c->Vlo);
+      c->pgroup /= 2;
+    }
+    need(c->Zhi); need(c->Zlo); need(c->Vhi); need(c->Vlo);
     const size_t pb = (size_t)ntau * naux * c->kpadS * 4, tb = (size_t)2 * n2 * c->kpadS * 4;
-    c->Zhi = (float*)need(A(zb)); c->Zlo = (float*)need(A(zb));
-    c->Vhi = (float*)need(A(vb)); c->Vlo = (float*)need(A(vb));
     c->Pchi = (float*)need(A(pb)); c->Pclo = (float*)need(A(pb));
     c->zbytes = zb;
     if (nao <= 64) {
@@ -431,6 +444,21 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   c->mus = (MuState*)need(A(sizeof(MuState)));
   c->info = (int*)need(A(64));
   c->dscr = (double*)need(A(64 * 8));
+  if (ok && c->emul && screened_refine_ok(naux)) {
+    // refined screened solve: as many (q, Omega) systems per batch as the budget
+    // allows; without room for one system the FP64 Gauss-Jordan solve is used
+    const int64_t cnt = (int64_t)nk * ntau;
+    const size_t per = screened_refine_bytes(naux, 1);
+    int64_t chunk = (int64_t)(opt_budget(kRefineBytes) / per);
+    if (chunk < 1) chunk = 1;
+    if (chunk > cnt) chunk = cnt;
+    for (; chunk >= 1; chunk /= 2) {
+      c->irws_bytes = screened_refine_bytes(naux, chunk);
+      c->irws = A(c->irws_bytes);
+      if (c->irws) break;
+    }
+    if (!c->irws) c->irws_bytes = 0;
+  }
   if (!ok) { free_all(c); delete c; return fail(nullptr, GW_ERR_OOM, "device allocation failed"); }
   if (cudaMallocHost(&c->h_mus, sizeof(MuState)) != cudaSuccess ||
       cudaMallocHost(&c->h_scr, 64 * 8) != cudaSuccess) {
