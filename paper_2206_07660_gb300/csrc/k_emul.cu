@@ -434,3 +434,18 @@ extern "C" int gwdbg_emul_cgemm(const double2* A, const double2* B, double2* C, 
   cudaFree(Ad); cudaFree(Bd); cudaFree(Ae); cudaFree(Be); cudaFree(err);
   return e ? (int)e : herr;
 }
+
+// Host-only view of the launch plan of a digit-split product (no GPU needed): writes
+// up to cap launches as (g, i0, i1) triples into out and returns their number (-1
+// when kreal is too large for exact sums).
+extern "C" int gwdbg_emul_plan(int64_t kreal, int nd, int* out, int cap) {
+  using namespace gwk;
+  EmLaunch pl[EM_MAXL];
+  const int n = em_plan(kreal, pl, nd);
+  for (int l = 0; l < n && l < cap; ++l) {
+    out[3 * l] = pl[l].g;
+    out[3 * l + 1] = pl[l].i0;
+    out[3 * l + 2] = pl[l].i1;
+  }
+  return n;
+}
