@@ -70,6 +70,7 @@ struct gw_ctx {
   cudaStream_t gst = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  int64_t graph_kernels = 0;   // kernel nodes of the captured iteration (counted per replay)
   cudaEvent_t gev[3]{};
   // nao-sized steps on tensor cores: V slab split, doubled G(tau) per k, X hi/lo
   float *Vs_hi = nullptr, *Vs_lo = nullptr, *Ge_hi = nullptr, *Ge_lo = nullptr, *Xs_hi = nullptr, *Xs_lo = nullptr;
@@ -1546,6 +1547,17 @@ static gw_status capture_iteration(gw_ctx* c) {
       c->graph = g;
       e2 = cudaGraphInstantiate(&c->gexec, g, 0);
       if (e2 != cudaSuccess) s = fail(c, GW_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e2));
+      size_t nn = 0;
+      if (s == GW_OK && cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess) {
+          c->graph_kernels = 0;
+          for (size_t i = 0; i < nn; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++c->graph_kernels;
+          }
+        }
+      }
     } else if (g) {
       cudaGraphDestroy(g);
     }
@@ -1561,6 +1573,7 @@ static gw_status launch_graph(gw_ctx* c) {
   CK(cudaEventRecord(c->gev[0], c->st));
   CK(cudaStreamWaitEvent(c->gst, c->gev[0], 0));
   CK(cudaGraphLaunch(c->gexec, c->gst));
+  g_launches += c->graph_kernels;
   CK(cudaEventRecord(c->gev[1], c->gst));
   CK(cudaStreamWaitEvent(c->st, c->gev[1], 0));
   return GW_OK;
