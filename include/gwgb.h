@@ -76,9 +76,10 @@ enum {
                                 P~0 / Sigma~ chains also on tensor cores (split TF32)  */
   GW_SMALL_SIMT   = 1u << 4, /* GW_SPLIT_TF32, nao <= 64: those steps on the FP32
                                 SIMT small-product kernel.  Neither flag: library default */
-  GW_FP64_NATIVE  = 1u << 5  /* tau <-> i nu transforms on the FP64 SIMT contraction
-                                kernel instead of FP64-accurate digit-split products on
-                                the tensor cores (the default)                        */
+  GW_FP64_NATIVE  = 1u << 5  /* FP64 SIMT arithmetic for the tau <-> i nu transforms
+                                and the screened solve, instead of the defaults:
+                                FP64-accurate digit-split products on the tensor cores
+                                and a complex64 inversion refined to FP64 accuracy    */
 };
 
 typedef void* (*gw_alloc_fn)(void* user, size_t bytes);
@@ -169,7 +170,12 @@ gw_status gw_polarization(gw_ctx* ctx);
 
 /* Screened solve P~ = [I - P~0(i Omega)]^{-1} P~0(i Omega) for every (q, m)
  * (Eq. tilde_P_omega), then P~^q(tau) (Eq. Piw_to_Pt), Hermitian-symmetrised.
- * Returns GW_ERR_SINGULAR on a zero pivot.  Synchronises. */
+ * FP64-accurate either way: by default Y = (I - P~0)^{-1} is inverted in complex64
+ * on the tensor cores and refined by two Newton steps Y <- Y + Y (I - (I - P~0) Y)
+ * whose residual products are exact digit-split GEMMs; GW_FP64_NATIVE (or naux >
+ * 512, or no room for the refinement workspace) inverts in FP64 arithmetic.
+ * Returns GW_ERR_SINGULAR on a zero pivot, GW_ERR_TIMEOUT when a tensor-core wait
+ * gave up.  Synchronises. */
 gw_status gw_screened(gw_ctx* ctx);
 
 /* Sigma~^k(tau) = -(1/Nk) sum_q sum V^{k,k-q} G^{k-q}(tau) P~^q(tau) V^{k-q,k}
