@@ -128,6 +128,17 @@ class Clocks:
 HOST_V_LIMIT = 8e9   # bytes; larger V tensors are drawn slab by slab straight into HBM
 
 
+def max_over_ranks(value, device):
+    """The job's time is its slowest rank's: max of a per-rank float over all ranks
+    of the default process group (the value itself without one)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(workload, seed_offset=0, kmesh=None):
     from synth import CONFIGS, make_config_system
     cfg = dict(CONFIGS[workload])
@@ -384,11 +395,7 @@ def run_gw(args):
     launches = g.kernel_launches() - l0
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), "cuda")
     s_per_iter = ms / args.steps / 1e3
     K = args.steps
     p_tflops = fl["P0"] / (stage["ms_polarization"] / K / 1e3) / 1e12
