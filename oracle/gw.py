@@ -215,14 +215,16 @@ def green_tau(grid, G_iw):
 class State:
     """Oracle state of a self-consistent run."""
 
-    def __init__(self, sysd, s=2.0, damping=0.5, mu_tol=1e-9):
+    def __init__(self, sysd, s=2.0, damping=0.5, mu_tol=1e-9, grid=None):
         self.H0, self.S, self.V = sysd["H0"], sysd["S"], sysd["V"]
         self.km = KMesh(sysd["kmesh"])
-        self.grid = Grid(sysd["beta"], sysd["ntau"], sysd["fermi_n"], sysd["bose_m"])
+        # the Chebyshev grid of the system's (beta, ntau, index sets), or any grid with
+        # the same attributes (oracle.ir.IRGrid)
+        self.grid = grid if grid is not None else Grid(sysd["beta"], sysd["ntau"], sysd["fermi_n"], sysd["bose_m"])
         self.s, self.alpha, self.mu_tol = s, damping, mu_tol
         self.n_elec = float(sysd["n_elec"])
         nk, nao = self.H0.shape[0], self.H0.shape[1]
-        nw = self.grid.ntau
+        nw = len(self.grid.wf)
         self.Sigma_inf = np.zeros((nk, nao, nao), dtype=np.complex128)
         self.Sigma_iw = np.zeros((nw, nk, nao, nao), dtype=np.complex128)
         self.have_sigma = False

@@ -240,3 +240,38 @@ class IRBasis:
         tp, npts = self.tau_points(), self.matsubara_points()
         Ft, Fw = self.u(tp), self.uhat(npts)
         return tp, npts, Fw @ np.linalg.pinv(Ft), Ft @ np.linalg.pinv(Fw)
+
+
+class IRGrid:
+    """Sparse-sampling grid of one GW calculation on the IR basis, with the
+    attributes the oracle's GW steps read from the Chebyshev grid (tau, wf, wb,
+    TFf, TBf, TFb, TBb, l0, lb, r).
+
+    One tau grid serves both statistics: the sampling points of the fermionic basis
+    (G and Sigma~ live there; P~ is fitted in the bosonic basis at the same points).
+    Fermionic and bosonic Matsubara points are each basis' own, so the transforms are
+    rectangular: TFf = Uhat_F pinv(U_F(tau)) maps tau values to fermionic Matsubara
+    values, TBf = U_F(tau) pinv(Uhat_F) back (least squares), likewise for bosons.
+    lb and l0 are the rows U_F(beta^-) pinv(U_F(tau)) and U_F(0^+) pinv(U_F(tau)), so
+    gamma = -G(beta^-) = -lb G(tau) as on the Chebyshev grid, and r = lb TBf gives the
+    density from the Matsubara values.
+    """
+
+    def __init__(self, beta, lam, eps=1e-10):
+        self.beta = float(beta)
+        self.basis_f = IRBasis(lam, beta, "F", eps)
+        self.basis_b = IRBasis(lam, beta, "B", eps)
+        bf, bb = self.basis_f, self.basis_b
+        self.tau = bf.tau_points()
+        self.ntau = self.tau.size
+        self.fermi_n = bf.matsubara_points()
+        self.bose_m = bb.matsubara_points()
+        self.wf = bf.freq(self.fermi_n)
+        self.wb = bb.freq(self.bose_m)
+        Ft, Fw = bf.u(self.tau), bf.uhat(self.fermi_n)
+        Bt, Bw = bb.u(self.tau), bb.uhat(self.bose_m)
+        self.TFf, self.TBf = Fw @ np.linalg.pinv(Ft), Ft @ np.linalg.pinv(Fw)
+        self.TFb, self.TBb = Bw @ np.linalg.pinv(Bt), Bt @ np.linalg.pinv(Bw)
+        ends = bf.u(np.array([0.0, self.beta])) @ np.linalg.pinv(Ft)
+        self.l0, self.lb = ends[0], ends[1]
+        self.r = self.lb @ self.TBf
