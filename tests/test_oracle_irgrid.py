@@ -62,3 +62,25 @@ def test_gw_step_matches_chebyshev(c1):
     assert np.abs(Sinf - Sinf_c).max() < 1e-10
     L = lagrange_eval(2 * grid.tau / grid.beta - 1, nt)
     assert np.abs(np.einsum("mj,jkab->mkab", L, Stau_c) - Stau).max() < 1e-9
+
+
+def test_scgw_iterations_match_chebyshev():
+    # three damped scGW iterations (mu search, Dyson, Sigma, mixing): the IR grid with
+    # 58 points (lambda = 20 beta, covering the spectrum shifted by Sigma) and 192
+    # Chebyshev nodes give the same iterates
+    sysd = make_config_system("C1")
+    beta = sysd["beta"]
+    grid = IRGrid(beta, lam=20.0 * beta, eps=1e-10)
+    st = ogw.State(sysd, grid=grid, damping=0.5)
+    nt = 192
+    fn, bm = matsubara_indices(nt)
+    s2 = dict(sysd)
+    s2.update(ntau=nt, fermi_n=fn, bose_m=bm)
+    ch = ogw.State(s2, damping=0.5)
+    L = lagrange_eval(2 * grid.tau / beta - 1, nt)
+    for _ in range(3):
+        st.iterate()
+        ch.iterate()
+        assert abs(st.mu - ch.mu) < 1e-9
+        assert abs(st.N - st.n_elec) < 1e-8
+        assert np.abs(np.einsum("mj,jkab->mkab", L, ch.G_tau) - st.G_tau).max() < 1e-9
