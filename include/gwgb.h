@@ -112,7 +112,7 @@ typedef enum {
   GW_Q_G_TAU = 0,      /* [ntau][nk][nao][nao] c128  (get, set)                 */
   GW_Q_G_IW = 1,       /* [nw][nk][nao][nao]   c128  (get)                      */
   GW_Q_SIGMA_INF = 2,  /* [nk][nao][nao]       c128  (get, set) static part      */
-  GW_Q_SIGMA_TAU = 3,  /* [ntau][nk][nao][nao] c128  (get)                      */
+  GW_Q_SIGMA_TAU = 3,  /* [ntau][nk][nao][nao] c128  (get, set)                 */
   GW_Q_SIGMA_IW = 4,   /* [nw][nk][nao][nao]   c128  (get, set) dynamic part     */
   GW_Q_P0_TAU = 5,     /* [nq][ntau][naux][naux] c128 (get, set)                */
   GW_Q_P0_IW = 6,      /* [nq][nw][naux][naux]  c128 (get, set); overwritten by
@@ -154,7 +154,11 @@ gw_status gw_destroy(gw_ctx* ctx);
 
 /* Copy a quantity in (gw_set) or out (gw_get).  `bytes` must equal the size
  * listed for it in gw_quantity.  on_device != 0: src/dst is a device pointer.
- * gw_get synchronises the stream when dst is a host pointer. */
+ * gw_get synchronises the stream when dst is a host pointer.  gw_get returns
+ * GW_ERR_STATE for a quantity that neither gw_set nor the call computing it
+ * has written yet (Sigma_inf, Sigma(i w), the grid and the transforms are
+ * defined from gw_init on; P~0(i Omega) stops being readable once gw_screened
+ * has replaced it by P~(i Omega)). */
 gw_status gw_set(gw_ctx* ctx, gw_quantity which, const void* src, size_t bytes, int on_device);
 gw_status gw_get(gw_ctx* ctx, gw_quantity which, void* dst, size_t bytes, int on_device);
 
@@ -185,9 +189,31 @@ gw_status gw_screened(gw_ctx* ctx);
  * (else Sigma_new).  Requires G and P~(tau). */
 gw_status gw_selfenergy(gw_ctx* ctx);
 
-/* Dyson equation (Eq. Dyson) with chemical-potential search: bisection on
- * N(mu) = (s/Nk) sum_k tr[gamma^k S^k] until |N - n_elec| <= mu_tol and the
- * bracket is below 1e-13, then G(i w) = [(i w + mu) S - H0 - Sigma_inf -
+/* The two halves of gw_selfenergy, for a q range split over several contexts
+ * (one per GPU, Sec. "GPU acceleration": the q-points are distributed and the
+ * self-energy is reduced over them).  gw_selfenergy_partial computes
+ * Sigma~^k(tau) summed over the context's q range only (Eq. tilde_sigma2),
+ * symmetrised, into GW_Q_SIGMA_TAU; the caller adds the partial sums of all
+ * contexts (Sigma~ is a sum over q) and writes the total back with gw_set.
+ * gw_selfenergy_finish then computes the static part (as gw_hf), Sigma~(i w)
+ * from GW_Q_SIGMA_TAU (Eq. tau_to_iw) and the damped update.  Requires G and
+ * P~(tau) (partial) or Sigma~(tau) (finish); GW_ERR_STATE otherwise. */
+gw_status gw_selfenergy_partial(gw_ctx* ctx);
+gw_status gw_selfenergy_finish(gw_ctx* ctx);
+
+/* Restrict the q-points of gw_polarization, gw_screened and the Sigma~
+ * contraction (and of the tangents built on them) to [q0, q1), 0 <= q0 < q1 <=
+ * nk; the default is every q.  P~0 and P~ of the other q are neither computed
+ * nor read, and Sigma~(tau) becomes the partial sum over [q0, q1).  The
+ * adjoints always run over every q.  Forgets the P~0 / P~ / Sigma~(tau) of
+ * the previous range (GW_ERR_ARG for a bad range). */
+gw_status gw_set_q_range(gw_ctx* ctx, int32_t q0, int32_t q1);
+
+/* Dyson equation (Eq. Dyson) with chemical-potential search: a bracketing
+ * search on N(mu) = (s/Nk) sum_k tr[gamma^k S^k] (the bracket [mu_prev - 1,
+ * mu_prev + 1] widened until N - n_elec changes sign, then Illinois
+ * regula-falsi steps with a plain bisection every fourth step) until
+ * |N - n_elec| <= mu_tol and the bracket is below 1e-13, then G(i w) = [(i w + mu) S - H0 - Sigma_inf -
  * Sigma~(i w)]^{-1} and G(tau) (symmetrised).  With no self-energy set this is
  * the non-interacting G0.  Synchronises.  mu_out may be NULL. */
 gw_status gw_dyson(gw_ctx* ctx, double* mu_out);
@@ -299,7 +325,8 @@ gw_status gw_iterate_newton(gw_ctx* ctx, int32_t n_outer, int32_t m, double tol,
  * solve (memory owned by an arena or pool they do not control, hosts that
  * forbid cudaMalloc after start-up, code that must not hit an allocator's
  * implicit synchronisation).  P0 and P are device pointers owned by the caller
- * (P == P0 solves in place).  Scratch is one fixed array of 64 MiB inside the
+ * (P == P0 solves in place; otherwise the two ranges must not overlap, else
+ * GW_ERR_ARG).  Scratch is one fixed array of 64 MiB inside the
  * library (GW_NOALLOC_SCRATCH_BYTES), resident on every device that loads the
  * library until the process exits; n is limited to orders whose per-matrix
  * workspace fits it (GW_ERR_ARG otherwise; n = 20000 fits).  The first call on
@@ -312,7 +339,8 @@ gw_status gw_iterate_newton(gw_ctx* ctx, int32_t n_outer, int32_t m, double tol,
 #define GW_NOALLOC_SCRATCH_BYTES (64u << 20)
 gw_status gw_screened_solve_noalloc(const double* P0, double* P, int64_t n, int64_t count, void* stream);
 
-/* Message of the last failure of gw_screened_solve_noalloc. */
+/* Message of the last failure of gw_screened_solve_noalloc in the calling thread
+ * (empty after a successful call). */
 const char* gw_noalloc_last_error(void);
 
 #ifdef __cplusplus

@@ -74,14 +74,15 @@ def hartree(V, gamma, s=2.0):
     return (s / nk) * np.einsum("kQij,Q->kij", Vd, t)
 
 
-def exchange(V, gamma, kps=None):
+def exchange(V, gamma, kps=None, ks=None):
     """Eq. HF_K: K^k_ij = -(1/Nk) sum_{k',Q,ab} V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q).
 
-    `kps` restricts the k' sum (timing samples only)."""
+    `kps` restricts the k' sum (timing samples only); `ks` computes only the rows
+    of those k (the others stay zero; sampled checks)."""
     nk = gamma.shape[0]
     K = np.zeros_like(gamma)
     naux, nao = V.shape[2], V.shape[3]
-    for k in range(nk):
+    for k in (range(nk) if ks is None else ks):
         for kp in (range(nk) if kps is None else kps):
             A = np.matmul(V[k, kp], gamma[kp])                # [Q, i, b]
             At = A.transpose(1, 0, 2).reshape(nao, naux * nao)  # [i, (Q, b)]

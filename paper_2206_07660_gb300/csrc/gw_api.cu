@@ -19,6 +19,7 @@ namespace gwk { std::atomic<long long> g_launches{0}; }
 struct gw_ctx {
   gw_config cfg{};
   int nao = 0, naux = 0, nk = 0, ntau = 0, nw = 0;
+  int q0 = 0, q1 = 0;   // q-points [q0, q1) of the P~0, screened and Sigma~ contractions (all by default)
   int64_t n2 = 0, na2 = 0;
   double spin = 2.0;
   cudaStream_t st = nullptr;
@@ -88,6 +89,9 @@ struct gw_ctx {
   double mu = 0.0, n_at_mu = 0.0;
   int mu_steps = 0;
   bool have_G = false, have_mu = false, have_sigma = false, have_P0 = false, have_P = false;
+  // one bit per gw_quantity whose buffer holds a result (set by gw_set or by the call
+  // that computes it); gw_get refuses the others with GW_ERR_STATE
+  uint32_t valid = 0;
   cudaEvent_t ev[8]{};
   // optional per-launch timing of the contraction kernel (gw_profile)
   bool prof = false;
@@ -102,6 +106,10 @@ struct gw_ctx {
 };
 
 static thread_local std::string g_init_err;
+
+static inline uint32_t qbit(gw_quantity q) { return 1u << (unsigned)q; }
+static inline void mark(gw_ctx* c, gw_quantity q) { c->valid |= qbit(q); }
+static inline void unmark(gw_ctx* c, gw_quantity q) { c->valid &= ~qbit(q); }
 
 // The nao-sized chain steps (K = 2 nao) run on the tensor-core GEMM by default:
 // with the persistent kernel and lane-per-row stores of the transposed outputs they
@@ -322,6 +330,7 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   c->cfg = *cfg;
   c->nao = cfg->nao; c->naux = cfg->naux; c->ntau = cfg->ntau; c->nw = cfg->ntau;
   c->nk = cfg->kmesh[0] * cfg->kmesh[1] * cfg->kmesh[2];
+  c->q0 = 0; c->q1 = c->nk;
   c->n2 = (int64_t)c->nao * c->nao; c->na2 = (int64_t)c->naux * c->naux;
   c->spin = cfg->spin_factor > 0 ? cfg->spin_factor : 2;
   c->st = (cudaStream_t)cfg->stream;
@@ -529,6 +538,9 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     else if (h[4] > 1e-10 * (h[5] > 1e-300 ? h[5] : 1)) { s = GW_ERR_ARG; c->err = "V^{k'k}(Q) != V^{kk'}(Q)^H"; }
   }
   if (s != GW_OK) { g_init_err = c->err; free_all(c); delete c; return s; }
+  // zero self-energy and the grid are defined from the start
+  for (gw_quantity q : {GW_Q_SIGMA_INF, GW_Q_SIGMA_IW, GW_Q_TFF, GW_Q_TBF, GW_Q_TFB, GW_Q_TBB, GW_Q_LB, GW_Q_TAU})
+    mark(c, q);
   *out = c;
   return GW_OK;
 }
@@ -555,7 +567,7 @@ static bool qinfo(gw_ctx* c, gw_quantity q, void** p, size_t* bytes, bool* setta
     case GW_Q_G_IW: *p = c->G_iw; *bytes = gsz; return true;
     case GW_Q_SIGMA_INF: *p = c->Sinf; *bytes = ksz; *settable = true; return true;
     case GW_Q_SIGMA_INF_NEW: *p = c->Sinf_new; *bytes = ksz; return true;
-    case GW_Q_SIGMA_TAU: *p = c->Stau; *bytes = gsz; return true;
+    case GW_Q_SIGMA_TAU: *p = c->Stau; *bytes = gsz; *settable = true; return true;
     case GW_Q_SIGMA_IW: *p = c->Siw; *bytes = gsz; *settable = true; return true;
     case GW_Q_P0_TAU: *p = c->P0_tau; *bytes = psz; *settable = true; return true;
     case GW_Q_P0_IW: *p = c->P_iw; *bytes = psz; *settable = true; return true;
@@ -577,6 +589,7 @@ extern "C" gw_status gw_set(gw_ctx* c, gw_quantity q, const void* src, size_t by
   if (q == GW_Q_MU) {
     if (bytes != 8 || on_device) return fail(c, GW_ERR_ARG, "mu is one host double");
     c->mu = *(const double*)src; c->have_mu = true;
+    mark(c, GW_Q_MU);
     return GW_OK;
   }
   void* p; size_t nb; bool settable;
@@ -584,8 +597,9 @@ extern "C" gw_status gw_set(gw_ctx* c, gw_quantity q, const void* src, size_t by
   if (bytes != nb) return fail(c, GW_ERR_ARG, "byte count does not match the quantity");
   CK(cudaMemcpyAsync(p, src, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
   if (!on_device) CK(cudaStreamSynchronize(c->st));
+  mark(c, q);
   if (q == GW_Q_G_TAU) c->have_G = true;
-  if (q == GW_Q_P0_IW) c->have_P0 = true;
+  if (q == GW_Q_P0_IW) { c->have_P0 = true; unmark(c, GW_Q_P_IW); }
   if (q == GW_Q_P_TAU) c->have_P = true;
   if (q == GW_Q_SIGMA_INF || q == GW_Q_SIGMA_IW) c->have_sigma = true;
   return GW_OK;
@@ -595,12 +609,15 @@ extern "C" gw_status gw_get(gw_ctx* c, gw_quantity q, void* dst, size_t bytes, i
   if (!c || !dst) return fail(c, GW_ERR_ARG, "null argument");
   if (q == GW_Q_MU || q == GW_Q_N_ELEC) {
     if (bytes != 8 || on_device) return fail(c, GW_ERR_ARG, "scalar is one host double");
+    if (!(c->valid & qbit(q))) return fail(c, GW_ERR_STATE, "no chemical potential yet");
     *(double*)dst = q == GW_Q_MU ? c->mu : c->n_at_mu;
     return GW_OK;
   }
   void* p; size_t nb; bool settable;
   if (!qinfo(c, q, &p, &nb, &settable)) return fail(c, GW_ERR_ARG, "unknown quantity");
   if (bytes != nb) return fail(c, GW_ERR_ARG, "byte count does not match the quantity");
+  if (!(c->valid & qbit(q)))
+    return fail(c, GW_ERR_STATE, "quantity " + std::to_string((int)q) + " has not been computed or set yet");
   CK(cudaMemcpyAsync(dst, p, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
   if (!on_device) CK(cudaStreamSynchronize(c->st));
   return GW_OK;
@@ -672,7 +689,9 @@ static gw_status hf_core(gw_ctx* c, const double2* Gsrc, double2* gamma, double2
 extern "C" gw_status gw_hf(gw_ctx* c) {
   if (!c) return GW_ERR_ARG;
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
-  return hf_core(c, c->G_tau, c->gamma, c->Sinf_new);
+  gw_status s = hf_core(c, c->G_tau, c->gamma, c->Sinf_new);
+  if (s == GW_OK) { mark(c, GW_Q_GAMMA); mark(c, GW_Q_SIGMA_INF_NEW); }
+  return s;
 }
 
 // ------------------------------------------------------------------ A2/A3: polarization
@@ -709,7 +728,7 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
   // embedded V of k-point j of a group sit at column block j of rows of length G kp
   const int G = tc ? c->pgroup : 1;
   const int64_t zld = tc ? G * c->kpadP : 0;
-  for (int q = 0; q < nk; ++q) {
+  for (int q = c->q0; q < c->q1; ++q) {
     double2* Pq = out + (size_t)q * ntau * na2;
     for (int k = 0; k < nk; ++k) {
       const int kq = c->kplus[(size_t)q * nk + k];
@@ -822,12 +841,16 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
     memcpy(&h, c->h_scr, 4);
     if (h) return fail(c, GW_ERR_TIMEOUT, "tensor-core contraction gave up waiting (code " + std::to_string(h) + ")");
   }
-  CK(herm_batched(c->P0_tau, naux, (int64_t)nk * ntau, na2, c->st));
+  const int nq = c->q1 - c->q0;
+  double2* P0q = c->P0_tau + (size_t)c->q0 * ntau * na2;
+  CK(herm_batched(P0q, naux, (int64_t)nq * ntau, na2, c->st));
   count(1);
   // P~0(i Omega_m) = sum_j TFb[m][j] P~0(tau_j)   (Eq. P0t_to_P0w)
-  CK(transform(c, c->TFb, c->P0_tau, c->P_iw, c->nw, na2, nk, (int64_t)ntau * na2, (int64_t)c->nw * na2));
+  CK(transform(c, c->TFb, P0q, c->P_iw + (size_t)c->q0 * c->nw * na2, c->nw, na2, nq, (int64_t)ntau * na2,
+               (int64_t)c->nw * na2));
   c->have_P0 = true;
   c->have_P = false;
+  mark(c, GW_Q_P0_TAU); mark(c, GW_Q_P0_IW); unmark(c, GW_Q_P_IW);
   return GW_OK;
 }
 
@@ -836,25 +859,27 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
 extern "C" gw_status gw_screened(gw_ctx* c) {
   if (!c) return GW_ERR_ARG;
   if (!c->have_P0) return fail(c, GW_ERR_STATE, "no polarization yet");
-  const int nk = c->nk, naux = c->naux, ntau = c->ntau;
+  const int naux = c->naux, ntau = c->ntau, nq = c->q1 - c->q0;
   const int64_t na2 = c->na2;
+  double2* Pw = c->P_iw + (size_t)c->q0 * c->nw * na2;
+  double2* Pt = c->P_tau + (size_t)c->q0 * ntau * na2;
   if (!c->deferred) {
     CK(cudaMemsetAsync(c->info + 1, 0, 8, c->st));
   }
   if (c->irws) {
     // complex64 inversion refined to FP64 accuracy (P~0 Y on the tensor cores)
     int64_t nl = 0;
-    CK(screened_refine(c->P_iw, naux, (int64_t)nk * c->nw, c->irws, c->irws_bytes, kRefineSteps, c->info + 2,
+    CK(screened_refine(Pw, naux, (int64_t)nq * c->nw, c->irws, c->irws_bytes, kRefineSteps, c->info + 2,
                        c->info + 1, c->st, &nl));
     count((int)nl);
   } else {
-    CK(screened_inplace(c->P_iw, naux, (int64_t)nk * c->nw, (double2*)c->ws, c->ws_bytes, c->info + 2, c->st));
+    CK(screened_inplace(Pw, naux, (int64_t)nq * c->nw, (double2*)c->ws, c->ws_bytes, c->info + 2, c->st));
     int64_t nbk = (naux + 63) / 64;
     count((int)(2 + nbk * 7));
   }
   // P~(tau_j) = sum_m TBb[j][m] P~(i Omega_m)   (Eq. Piw_to_Pt), symmetrised
-  CK(transform(c, c->TBb, c->P_iw, c->P_tau, ntau, na2, nk, (int64_t)c->nw * na2, (int64_t)ntau * na2));
-  CK(herm_batched(c->P_tau, naux, (int64_t)nk * ntau, na2, c->st));
+  CK(transform(c, c->TBb, Pw, Pt, ntau, na2, nq, (int64_t)c->nw * na2, (int64_t)ntau * na2));
+  CK(herm_batched(Pt, naux, (int64_t)nq * ntau, na2, c->st));
   count(1);
   c->have_P0 = false;   // P~0(i Omega) was overwritten
   if (!c->deferred) {
@@ -866,6 +891,7 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
     if (h[1]) return fail(c, GW_ERR_SINGULAR, "zero pivot in the screened solve");
   }
   c->have_P = true;
+  mark(c, GW_Q_P_IW); mark(c, GW_Q_P_TAU); unmark(c, GW_Q_P0_IW);
   return GW_OK;
 }
 
@@ -896,7 +922,7 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
     count(2);
     Gp = c->G32; Pp = c->P32;
   }
-  for (int q = 0; q < nk; ++q) {
+  for (int q = c->q0; q < c->q1; ++q) {
     const char* Pq = (const char*)Pp + (size_t)q * ntau * na2 * es;
     if (tc) {
       // A operand of the tensor-core stage: conj P~^q(t) = P~^q(t)^T (Hermitian), split hi/lo
@@ -987,7 +1013,7 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
       d3.bk = I1(nao); d3.bn = I1(1); d3.bz = I1(0);
       d3.cm = I1(nao); d3.cn = I1(1); d3.cz = I1(gstep);
       d3.alpha = make_double2(-1.0 / nk, 0);
-      d3.beta = make_double2(accumulate || q > 0 ? 1.0 : 0.0, 0);
+      d3.beta = make_double2(accumulate || q > c->q0 ? 1.0 : 0.0, 0);
       d3.ksplit = 8;
       const char* Vk2 = (const char*)Vp + ((size_t)kmq * nk + k) * slab * es;
       CK(run_gett(d3, c->chB, tv, Vk2, tv, out + (size_t)k * n2, Ty::C128, acc, c));
@@ -996,9 +1022,10 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
   return GW_OK;
 }
 
-static gw_status sigma_dynamic(gw_ctx* c) {
+// Sigma~(tau) over the context's q range (Eq. tilde_sigma2), symmetrised, into Stau
+static gw_status sigma_tau_part(gw_ctx* c) {
   const int nk = c->nk, nao = c->nao, ntau = c->ntau;
-  const int64_t n2 = c->n2, gstep = (int64_t)nk * n2;
+  const int64_t n2 = c->n2;
   const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
   gw_status s = sigma_chain(c, c->G_tau, c->P_tau, c->Stau, false);
   if (s != GW_OK) return s;
@@ -1011,18 +1038,35 @@ static gw_status sigma_dynamic(gw_ctx* c) {
   }
   CK(herm_batched(c->Stau, nao, (int64_t)ntau * nk, n2, c->st));
   count(1);
-  // Sigma~(i w_n) = sum_j TFf[n][j] Sigma~(tau_j)
-  CK(transform(c, c->TFf, c->Stau, c->Siw_new, c->nw, gstep, 1, 0, 0));
+  mark(c, GW_Q_SIGMA_TAU);
   return GW_OK;
 }
 
-extern "C" gw_status gw_selfenergy(gw_ctx* c) {
+// Sigma~(i w_n) = sum_j TFf[n][j] Sigma~(tau_j)   (Eq. tau_to_iw) into Siw_new
+static gw_status sigma_iw_new(gw_ctx* c) {
+  CK(transform(c, c->TFf, c->Stau, c->Siw_new, c->nw, (int64_t)c->nk * c->n2, 1, 0, 0));
+  return GW_OK;
+}
+
+static gw_status sigma_dynamic(gw_ctx* c) {
+  gw_status s = sigma_tau_part(c);
+  return s != GW_OK ? s : sigma_iw_new(c);
+}
+
+extern "C" gw_status gw_selfenergy_partial(gw_ctx* c) {
   if (!c) return GW_ERR_ARG;
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
   if (!c->have_P) return fail(c, GW_ERR_STATE, "no screened interaction yet");
+  return sigma_tau_part(c);
+}
+
+extern "C" gw_status gw_selfenergy_finish(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
+  if (!(c->valid & qbit(GW_Q_SIGMA_TAU))) return fail(c, GW_ERR_STATE, "no Sigma~(tau) yet");
   gw_status s = gw_hf(c);
   if (s != GW_OK) return s;
-  s = sigma_dynamic(c);
+  s = sigma_iw_new(c);
   if (s != GW_OK) return s;
   const int64_t ksz = (int64_t)c->nk * c->n2, gsz = (int64_t)c->ntau * ksz;
   CK(cudaMemsetAsync(c->dscr + 8, 0, 8, c->st));
@@ -1033,6 +1077,21 @@ extern "C" gw_status gw_selfenergy(gw_ctx* c) {
   CK(axpby(c->Siw, c->Siw_new, a, 1.0 - a, gsz, c->st));
   count(2);
   c->have_sigma = true;
+  return GW_OK;
+}
+
+extern "C" gw_status gw_selfenergy(gw_ctx* c) {
+  gw_status s = gw_selfenergy_partial(c);
+  return s != GW_OK ? s : gw_selfenergy_finish(c);
+}
+
+extern "C" gw_status gw_set_q_range(gw_ctx* c, int32_t q0, int32_t q1) {
+  if (!c) return GW_ERR_ARG;
+  if (q0 < 0 || q1 > c->nk || q0 >= q1) return fail(c, GW_ERR_ARG, "q range must satisfy 0 <= q0 < q1 <= nk");
+  c->q0 = q0; c->q1 = q1;
+  // results of another range are not those of this one
+  c->have_P0 = c->have_P = false;
+  for (gw_quantity q : {GW_Q_P0_TAU, GW_Q_P0_IW, GW_Q_P_IW, GW_Q_P_TAU, GW_Q_SIGMA_TAU}) unmark(c, q);
   return GW_OK;
 }
 
@@ -1092,6 +1151,7 @@ extern "C" gw_status gw_dyson(gw_ctx* c, double* mu_out) {
   memcpy(&bad, c->h_scr, 4);
   if (bad) return fail(c, GW_ERR_SINGULAR, "zero pivot in the Dyson inversion");
   c->have_G = true;
+  mark(c, GW_Q_G_TAU); mark(c, GW_Q_G_IW); mark(c, GW_Q_MU); mark(c, GW_Q_N_ELEC);
   if (mu_out) *mu_out = c->mu;
   return GW_OK;
 }
@@ -1116,6 +1176,7 @@ static gw_status dyson_device(gw_ctx* c) {
   CK(transform(c, c->TBf, c->G_iw, c->G_tau, c->ntau, gstep, 1, 0, 0));
   CK(herm_batched(c->G_tau, c->nao, (int64_t)c->ntau * c->nk, c->n2, c->st));
   count(2);
+  mark(c, GW_Q_G_TAU); mark(c, GW_Q_G_IW);
   return GW_OK;
 }
 
@@ -1425,6 +1486,7 @@ static gw_status sc_forward(gw_ctx* c) {
   if ((s = gw_polarization(c)) != GW_OK) return s;
   if ((s = gw_screened(c)) != GW_OK) return s;
   if ((s = hf_core(c, c->G_tau, c->gamma, c->Sinf_new)) != GW_OK) return s;
+  mark(c, GW_Q_GAMMA); mark(c, GW_Q_SIGMA_INF_NEW);
   return sigma_dynamic(c);
 }
 
@@ -1592,6 +1654,7 @@ static gw_status finish_graph(gw_ctx* c, gw_iter_stats* stats) {
   if (flags[0]) return fail(c, GW_ERR_SINGULAR, "zero pivot in the Dyson inversion");
   if (!h->done || h->status != 0) return fail(c, GW_ERR_NOT_CONVERGED, "chemical-potential search hit its cap");
   c->mu = h->x; c->have_mu = true; c->n_at_mu = h->Nx;
+  mark(c, GW_Q_MU); mark(c, GW_Q_N_ELEC);
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->mu = c->mu; stats->n_elec = c->n_at_mu; stats->mu_steps = c->mu_steps;

@@ -66,8 +66,10 @@ def load():
     lib.gw_destroy.argtypes = [P]
     lib.gw_set.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int]
     lib.gw_get.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int]
-    for name in ("gw_hf", "gw_polarization", "gw_screened", "gw_selfenergy", "gw_reset_sigma"):
+    for name in ("gw_hf", "gw_polarization", "gw_screened", "gw_selfenergy", "gw_reset_sigma",
+                 "gw_selfenergy_partial", "gw_selfenergy_finish"):
         getattr(lib, name).argtypes = [P]
+    lib.gw_set_q_range.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
     lib.gw_dyson.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.gw_iterate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(GwIterStats)]
     lib.gw_last_error.argtypes = [P]
@@ -90,7 +92,7 @@ def load():
                  "gw_selfenergy", "gw_dyson", "gw_iterate", "gw_reset_sigma", "gw_profile", "gw_profile_read",
                  "gw_polarization_vjp", "gw_selfenergy_vjp", "gw_iterate_graph", "gw_batch_iterate",
                  "gw_polarization_jvp", "gw_screened_jvp", "gw_selfenergy_jvp", "gw_sc_jvp",
-                 "gw_iterate_newton"):
+                 "gw_iterate_newton", "gw_selfenergy_partial", "gw_selfenergy_finish", "gw_set_q_range"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -254,6 +256,15 @@ class GW:
 
     def selfenergy(self):
         self._check(self.lib.gw_selfenergy(self.ctx))
+
+    def selfenergy_partial(self):
+        self._check(self.lib.gw_selfenergy_partial(self.ctx))
+
+    def selfenergy_finish(self):
+        self._check(self.lib.gw_selfenergy_finish(self.ctx))
+
+    def set_q_range(self, q0, q1):
+        self._check(self.lib.gw_set_q_range(self.ctx, int(q0), int(q1)))
 
     def dyson(self):
         mu = ctypes.c_double()

@@ -5,8 +5,8 @@ V^{kk'}(Q), picks the sampled Matsubara integers and names the workloads.
 """
 from .generate import (CONFIGS, SEED_BASE, config_seed, matsubara_indices, v_slab,
                        make_config_system, batch_configs, make_batch_system,
-                       make_system, kmesh_size)
+                       make_system, kmesh_size, LazyV, device_V)
 
 __all__ = ["CONFIGS", "SEED_BASE", "config_seed", "matsubara_indices", "v_slab", "make_config_system",
            "batch_configs", "make_batch_system",
-           "make_system", "kmesh_size"]
+           "make_system", "kmesh_size", "LazyV", "device_V"]

@@ -221,3 +221,48 @@ def make_config_system(name, system=0, trs=False, materialize_V=True, **over):
     sysd.update(ntau=int(cfg["ntau"]), beta=float(cfg["beta"]), fermi_n=fn, bose_m=bm,
                 n_elec=float(cfg.get("n_elec", cfg["nao"])))
     return sysd
+
+
+class LazyV:
+    """V^{kk'}(Q) slabs drawn on demand, indexable as V[k, k'] (for oracle samples
+    of workloads whose full V tensor does not fit in host memory)."""
+
+    def __init__(self, sysd):
+        self.sysd = sysd
+        nk, naux, nao = sysd["nk"], sysd["naux"], sysd["nao"]
+        self.shape = (nk, nk, naux, nao, nao)
+        self.cache = {}
+
+    def __getitem__(self, idx):
+        k, k2 = idx
+        if isinstance(k, np.ndarray):
+            return np.stack([self[(int(a), int(b))] for a, b in zip(k, k2)])
+        key = (int(k), int(k2))
+        if key not in self.cache:
+            self.cache[key] = v_slab(self.sysd, *key)
+        return self.cache[key]
+
+
+def device_V(sysd, threads=16):
+    """The full V tensor [nk, nk, naux, nao, nao] complex128 in GPU memory, drawn
+    slab by slab on host threads (each unordered pair once, its partner by
+    conjugate transposition on the device)."""
+    import concurrent.futures as cf
+    import os
+    import torch
+    nk, naux, nao = sysd["nk"], sysd["naux"], sysd["nao"]
+    V = torch.empty((nk, nk, naux, nao, nao), dtype=torch.complex128, device="cuda")
+    pairs = [(k, k2) for k in range(nk) for k2 in range(k, nk)]
+
+    def draw(p):
+        return p, torch.from_numpy(v_slab(sysd, *p)).pin_memory()
+
+    with cf.ThreadPoolExecutor(max_workers=min(threads, os.cpu_count() or 4)) as ex:
+        for (k, k2), h in ex.map(draw, pairs):
+            d = h.to("cuda", non_blocking=False)
+            V[k, k2] = d
+            if k2 != k:
+                V[k2, k] = d.transpose(-1, -2).conj()
+    torch.cuda.synchronize()
+    return V
+

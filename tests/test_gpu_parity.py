@@ -148,18 +148,60 @@ def test_single_orbital_closed_form():
     assert abs(g.get("Sigma_inf_new")[0, 0, 0] - (cl["J"] + cl["K"])) < 1e-13
 
 
-@pytest.mark.parametrize("precision,small", [("fp32", "auto"), ("split_tf32", "simt"), ("split_tf32", "tensor")])
-def test_lowp_contractions_c1(precision, small):
-    # complex64 SIMT products, or split-TF32 tensor-core products, against the
-    # fp64 oracle: errors stay at the 1e-5 Ha level of fp32-class arithmetic
+def test_lowp_contractions_c1_fp32():
+    # complex64 SIMT products against the fp64 oracle: errors stay at the 1e-5 Ha
+    # level of plain fp32 arithmetic
     sysd = make_config_system("C1")
-    g = gpu(sysd, precision=precision, small_steps=small)
+    g = gpu(sysd, precision="fp32")
     st = oracle_state(sysd)
     g.iterate(1)
     st.iterate()
     err = np.abs(g.get("Sigma_tau") - st.Sigma_tau).max()
     assert err < 1e-5, err
     assert np.abs(g.get("Sigma_inf") - st.Sigma_inf).max() < 1e-5
+
+
+@pytest.mark.parametrize("small", ["simt", "tensor"])
+def test_mixed_path_c1_within_1e6_ha(small):
+    # the mixed path (split-TF32 tensor-core contractions, FP64 elsewhere) against the
+    # FP64 oracle over two damped iterations: max abs error of Sigma_inf, Sigma~(tau),
+    # Sigma~(i w) and G(tau) below the 1e-6 Ha target of the mixed path
+    sysd = make_config_system("C1")
+    g = gpu(sysd, precision="split_tf32", small_steps=small, damping=0.5)
+    st = oracle_state(sysd, damping=0.5)
+    for it in range(2):
+        g.iterate(1)
+        st.iterate()
+        errs = {q: float(np.abs(g.get(q) - getattr(st, q)).max())
+                for q in ("Sigma_inf", "Sigma_tau", "Sigma_iw", "G_tau")}
+        assert max(errs.values()) < 1e-6, (it, errs)
+        assert abs(g.get("mu") - st.mu) < 1e-6
+
+
+def test_get_refuses_unwritten_quantities():
+    # gw_get returns GW_ERR_STATE for buffers that nothing has written yet
+    from paper_2206_07660_gb300 import GWError
+    sysd = system(3, 5, (2, 1, 1), 8, 10.0, 2)
+    g = gpu(sysd)
+    for name in ("G_tau", "G_iw", "Sigma_tau", "P0_tau", "P0_iw", "P_iw", "P_tau", "gamma", "Sigma_inf_new", "mu"):
+        with pytest.raises(GWError) as e:
+            g.get(name)
+        assert e.value.status == 7, name
+    assert np.abs(g.get("Sigma_inf")).max() == 0.0      # zero self-energy from the start
+    assert np.abs(g.get("Sigma_iw")).max() == 0.0
+    g.get("TFf"); g.get("tau")
+    g.dyson()
+    g.get("G_tau"); g.get("G_iw"); g.get("mu")
+    g.polarization()
+    g.get("P0_tau"); g.get("P0_iw")
+    with pytest.raises(GWError):
+        g.get("P_iw")
+    g.screened()
+    g.get("P_iw"); g.get("P_tau")
+    with pytest.raises(GWError):
+        g.get("P0_iw")                                  # replaced by P~(i Omega)
+    g.selfenergy()
+    g.get("Sigma_tau"); g.get("gamma"); g.get("Sigma_inf_new")
 
 
 def test_rejects_bad_inputs():

@@ -84,7 +84,10 @@ def test_context_reports_timeout_and_recovers():
         ref = gpu(sysd, precision="split_tf32")
         ref.set("G_tau", G)
         ref.polarization()
-        P_ref = ref.get("P_tau")
+        # gw_polarization writes P~0(tau) and its transform P~0(i Omega) (Eqs.
+        # tilde_P0_tau, P0t_to_P0w); those are the quantities to compare
+        P_ref = ref.get("P0_tau")
+        Pw_ref = ref.get("P0_iw")
         g = gpu(sysd, precision="split_tf32")
         g.set("G_tau", G)
         old_spin = lib.gwdbg_umma_set_spin(1)
@@ -96,7 +99,10 @@ def test_context_reports_timeout_and_recovers():
         assert e.value.status == GW_ERR_TIMEOUT
         torch.cuda.synchronize()
         g.polarization()
-        P = g.get("P_tau")
+        P = g.get("P0_tau")
+        Pw = g.get("P0_iw")
     finally:
         lib.gwdbg_umma_force_bn(old_bn)
+    assert np.abs(P_ref).max() > 0
     assert np.abs(P - P_ref).max() <= 1e-12 * np.abs(P_ref).max()
+    assert np.abs(Pw - Pw_ref).max() <= 1e-12 * np.abs(Pw_ref).max()
