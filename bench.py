@@ -52,7 +52,8 @@ def parse():
     p.add_argument("--impl", default="gw", choices=["gw", "reference"])
     p.add_argument("--workload", default="C3", choices=["C1", "C2", "C3", "C4", "C5"])
     p.add_argument("--c5-vjp", action="store_true", help="C5: also time the FP64 adjoint chains")
-    p.add_argument("--precision", default="split_tf32", choices=["split_tf32", "fp32", "fp64"])
+    p.add_argument("--precision", default="split_tf32",
+                   choices=["split_f16", "split_bf16", "split_tf32", "fp32", "fp64"])
     p.add_argument("--fp64-gemm", default="tensor", choices=["tensor", "native"],
                    help="FP64 tau<->i nu transforms: digit-split tensor-core products or the FP64 SIMT kernel")
     p.add_argument("--small-steps", default="auto", choices=["auto", "tensor", "simt"],
@@ -163,7 +164,7 @@ def oracle_V(sysd):
 
 def source_sha(precision):
     """Hash of the contraction kernel's source (the counters are void once it changes)."""
-    kern = "k_umma.cu" if precision == "split_tf32" else "k_gett.cu"
+    kern = "k_umma.cu" if precision.startswith("split") else "k_gett.cu"
     src = os.path.join(ROOT, "paper_2206_07660_gb300", "csrc", kern)
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
@@ -506,7 +507,7 @@ def run_gw(args):
     torch.cuda.synchronize()
     prof = g.profile_read()
     g.profile(False)
-    dominant = "tensor" if args.precision == "split_tf32" else "simt"
+    dominant = "tensor" if args.precision.startswith("split") else "simt"
     gemm_ms, gemm_flops, gemm_launches = prof[dominant]
     p_tflops = s_tflops = None
     if last is not None and stage["ms_polarization"] > 0:
@@ -582,6 +583,14 @@ def run_gw(args):
                 "split_products": 3, "tensor_pipe_frac": 3.0 * achieved / peak,
                 "peak_basis": "of measured: bf16 dense %.1f TFLOP/s (MEASURED_PEAKS.json) x nominal tf32/bf16 "
                               "ratio 1.1/2.25" % bf16_peak()}
+    elif args.precision in ("split_f16", "split_bf16"):
+        peak = bf16_peak()
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "kernel": "umma_pkernel (tcgen05 kind::f16, %s hi/lo pieces, 3 products)" % args.precision[6:],
+                "split_products": 3, "tensor_pipe_frac": 3.0 * achieved / peak,
+                "peak_basis": "of measured: bf16 dense %.1f TFLOP/s burst (MEASURED_PEAKS.json; fp16 has the same "
+                              "nominal rate)" % bf16_peak()}
     else:
         peak = (SM_COUNT * (FP32_FLOPS_PER_CLK_SM if args.precision == "fp32" else FP64_FLOPS_PER_CLK_SM)
                 * SM_MAX_MHZ * 1e6 / 1e12)
@@ -602,7 +611,8 @@ def run_gw(args):
     line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iteration", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": False,
             "scaling": "strong" if world > 1 else "weak",
-            "vs_baseline": None, "dtype": {"fp32": "c64", "fp64": "c128", "split_tf32": "tf32x3/c64"}[args.precision],
+            "vs_baseline": None, "dtype": {"fp32": "c64", "fp64": "c128", "split_tf32": "tf32x3/c64", "split_f16": "f16x3/c64",
+                                  "split_bf16": "bf16x3/c64"}[args.precision],
             "data": "synthetic", "config": conf,
             "P_tflops": p_tflops, "Sigma_tflops": s_tflops,
             "stage_ms_per_iteration": {k: v / K for k, v in stage.items()},
@@ -671,7 +681,8 @@ def run_batch(args):
     line = {"metric": METRIC, "value": dt, "unit": "s/batch-iteration (16 systems)", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "c64", "fp64": "c128", "split_tf32": "tf32x3/c64"}[prec],
+            "dtype": {"fp32": "c64", "fp64": "c128", "split_tf32": "tf32x3/c64", "split_f16": "f16x3/c64",
+                                  "split_bf16": "bf16x3/c64"}[prec],
             "data": "synthetic",
             "config": {"workload": "C4: 16 systems, nao in {8,12,16,26,40}, naux = 8 nao, k-meshes 2^3..4^3, "
                                    "ntau = nw = 64, beta = 100, %s contractions, captured graphs on per-system "
@@ -759,7 +770,8 @@ def run_differentiation(args):
     line = {"metric": METRIC, "value": nk_s / n_outer, "unit": "s/Newton-Krylov step (GMRES(%d), %s)" % (m, prec),
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": nk_s / n_outer * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "c64", "fp64": "c128", "split_tf32": "tf32x3/c64"}[prec], "data": "synthetic",
+            "dtype": {"fp32": "c64", "fp64": "c128", "split_tf32": "tf32x3/c64", "split_f16": "f16x3/c64",
+                                  "split_bf16": "bf16x3/c64"}[prec], "data": "synthetic",
             "config": dict(workload_config(cfg, "C5", prec),
                            workload="C5: C2 sizes, tangent of the self-consistency map and Newton-Krylov "
                                     "self-consistency (GMRES(%d)) vs damped (0.5) iterations" % m),

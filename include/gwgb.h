@@ -62,10 +62,18 @@ typedef enum {
   GW_FP64 = 0,        /* complex128 throughout                                  */
   GW_FP32 = 1,        /* complex64 products, fp32 accumulation per k-slab,
                          fp64 accumulation across slabs                         */
-  GW_SPLIT_BF16 = 2,  /* reserved */
-  GW_SPLIT_TF32 = 3   /* the dominant GEMM of each contraction on tcgen05 tensor cores with
+  GW_SPLIT_BF16 = 2,  /* every GEMM of both chains on tcgen05 tensor cores (kind::f16) with
+                         x = hi + lo bf16 pieces (16 significant bits; hi*hi + hi*lo + lo*hi,
+                         fp32 accumulation, fp64 accumulation across (q, k) slabs); chain
+                         intermediates are written by the GEMMs as bf16 pieces             */
+  GW_SPLIT_TF32 = 3,  /* the dominant GEMM of each contraction on tcgen05 tensor cores with
                          x = hi + lo TF32 splits (hi*hi + hi*lo + lo*hi, fp32 accumulation,
                          fp64 accumulation across (q, k) slabs); other steps as GW_FP32 */
+  GW_SPLIT_F16 = 4    /* as GW_SPLIT_BF16 with fp16 pieces (22 significant bits, the accuracy
+                         of the TF32 split at twice its tensor rate and half its operand
+                         bytes); every operand row carries a power-of-two scale taken from
+                         an upper bound of its values (norms of V per auxiliary index and
+                         of G per tau), applied exactly in the GEMM epilogues            */
 } gw_precision;
 
 enum {
@@ -242,6 +250,17 @@ gw_status gw_batch_iterate(gw_ctx* const* ctxs, int32_t n, int32_t n_iter);
 
 /* Drop the stored self-energy so that the next gw_selfenergy is not mixed. */
 gw_status gw_reset_sigma(gw_ctx* ctx);
+
+/* Checkpoint / resume of a self-consistent run.  gw_save_state writes the state
+ * the next iteration starts from -- G(tau), Sigma_inf, Sigma~(i w), mu and whether
+ * a self-energy exists (so damping resumes as it would have) -- to `path` (host
+ * file, complex128 arrays after a fixed header, then a 64-bit FNV-1a hash of the
+ * file's contents).  gw_load_state reads it into a context of the same sizes and
+ * beta (GW_ERR_ARG on a mismatch, a missing, truncated or corrupt file); the next
+ * gw_iterate continues exactly as the saved run would have.  P~0 and P~ are not
+ * saved (they are recomputed from G).  Both synchronise the context's stream. */
+gw_status gw_save_state(gw_ctx* ctx, const char* path);
+gw_status gw_load_state(gw_ctx* ctx, const char* path);
 
 /* Message of the last failure of this context (or of gw_init when ctx is NULL). */
 const char* gw_last_error(const gw_ctx* ctx);

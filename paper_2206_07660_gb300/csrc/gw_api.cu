@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 #include <math.h>
+#include <cmath>
 #include <new>
 #include <string>
 #include <vector>
@@ -78,6 +79,13 @@ struct gw_ctx {
   float *Gp_hi = nullptr, *Gp_lo = nullptr;
   int64_t kpadA = 0;
   size_t zbytes = 0;
+  // 16-bit pieces (GW_SPLIT_F16 / GW_SPLIT_BF16): format (1 fp16, 2 bf16; 0 none), norms of V per Q
+  // (max, max row sum of moduli), their exponents, and the row exponents of every chain operand
+  int hfmt = 0;
+  float *vQmax = nullptr, *vQrs = nullptr, *gn = nullptr;   // gn: gmax, grs of G(t) and of G(-t) factor
+  int *eVQ = nullptr, *eVall = nullptr, *eV1 = nullptr, *eY = nullptr, *eZ = nullptr, *eGe = nullptr,
+      *eGp = nullptr, *ePc = nullptr, *ePs = nullptr, *eY3 = nullptr;
+  int h_Evmax = 0;   // exponent of max_Q vQmax (host copy)
   void* ws = nullptr;
   size_t ws_bytes = 0;
   double* partial = nullptr;
@@ -185,6 +193,13 @@ static void free_all(gw_ctx* c) {
 
 static inline void count(int n) { g_launches += n; }
 
+// contractions on the tensor cores (the wait-timeout flag is then meaningful)
+static inline bool uses_tc(const gw_ctx* c) {
+  return c->cfg.contract_prec == GW_SPLIT_TF32 || c->hfmt != 0;
+}
+// pointer to 16-bit element `e` of a buffer typed as float*
+static inline float* hofs(float* p, int64_t e) { return (float*)((uint16_t*)p + e); }
+
 static cudaError_t run_gett(const GettDesc& d, const void* A, Ty ta, const void* B, Ty tb, void* C, Ty tc, Ty acc,
                             gw_ctx* c) {
   count(d.ksplit > 1 ? 2 : 1);
@@ -209,7 +224,7 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
                             int64_t Kpad, int batch, void* C, bool c_fp64, double alpha, bool accumulate, int64_t c_ld,
                             int64_t c_zs, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
                             int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr,
-                            int64_t kvalid = 0) {
+                            int64_t kvalid = 0, const UmmaScale* scale = nullptr, const UmmaOut* out = nullptr) {
   count(1);
   if (c->prof) {
     while (c->uev.size() < c->uused + 2) {
@@ -224,7 +239,7 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
   // profiler can select exactly these launches
   nvtxRangePushA("contraction");
   cudaError_t r = umma_gemm(A, B, M, N, Kpad, batch, C, c_fp64, alpha, accumulate, c_ld, c_zs, 3, c->info + 1, c->st,
-                            ksplit, row_inner, row_s1, col_inner, col_s1, C_lo, nullptr, kvalid);
+                            ksplit, row_inner, row_s1, col_inner, col_s1, C_lo, scale, kvalid, out);
   nvtxRangePop();
   if (c->prof) {
     cudaEventRecord(c->uev[c->uused + 1], c->st);
@@ -317,7 +332,8 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     return fail(nullptr, GW_ERR_ARG, "sizes must be positive");
   if (cfg->nao > 96) return fail(nullptr, GW_ERR_ARG, "nao > 96 is not supported by the Dyson kernel");
   if (!(cfg->beta > 0) || !cfg->fermi_n || !cfg->bose_m) return fail(nullptr, GW_ERR_ARG, "bad beta or index sets");
-  if (cfg->contract_prec != GW_FP64 && cfg->contract_prec != GW_FP32 && cfg->contract_prec != GW_SPLIT_TF32)
+  if (cfg->contract_prec != GW_FP64 && cfg->contract_prec != GW_FP32 && cfg->contract_prec != GW_SPLIT_TF32 &&
+      cfg->contract_prec != GW_SPLIT_F16 && cfg->contract_prec != GW_SPLIT_BF16)
     return fail(nullptr, GW_ERR_ARG, "contract_prec not available");
   if ((cfg->flags & GW_BORROW_V) && !(cfg->flags & GW_INPUT_DEVICE))
     return fail(nullptr, GW_ERR_ARG, "GW_BORROW_V needs GW_INPUT_DEVICE");
@@ -435,6 +451,52 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     }
     c->VThi = (float*)need(A(tb)); c->VTlo = (float*)need(A(tb));
   }
+  if (cfg->contract_prec == GW_SPLIT_F16 || cfg->contract_prec == GW_SPLIT_BF16) {
+    // every contraction GEMM on the tensor cores with 16-bit pieces: operand rows padded to
+    // 64 elements (128 bytes), two bytes per element, one exponent per operand row
+    c->hfmt = cfg->contract_prec == GW_SPLIT_F16 ? 1 : 2;
+    auto r64 = [](int64_t x) { return (x + 63) / 64 * 64; };
+    c->kpadA = r64(2 * (int64_t)nao);
+    c->kpadP = r64(2 * n2);
+    c->kpadS = r64(2 * (int64_t)naux);
+    c->kpad3 = r64(2 * (int64_t)naux * nao);
+    const size_t zk = (size_t)ntau * naux * c->kpadP * 2, vk = (size_t)2 * naux * c->kpadP * 2;
+    c->pgroup = (int)(opt_budget(kZGroupBytes) / (2 * zk));
+    if (c->pgroup > nk) c->pgroup = nk;
+    if (g_pgroup_cap > 0 && c->pgroup > g_pgroup_cap) c->pgroup = g_pgroup_cap;
+    if (c->pgroup < 1) c->pgroup = 1;
+    size_t zb = 0;
+    for (;;) {
+      zb = zk * c->pgroup;
+      const size_t vb = vk * c->pgroup;
+      c->Zhi = (float*)A(zb); c->Zlo = (float*)A(zb); c->Vhi = (float*)A(vb); c->Vlo = (float*)A(vb);
+      if ((c->Zhi && c->Zlo && c->Vhi && c->Vlo) || c->pgroup == 1) break;
+      dfree(c, c->Zhi); dfree(c, c->Zlo); dfree(c, c->Vhi); dfree(c, c->Vlo);
+      c->pgroup /= 2;
+    }
+    need(c->Zhi); need(c->Zlo); need(c->Vhi); need(c->Vlo);
+    c->zbytes = zb;
+    const size_t pb = (size_t)ntau * naux * c->kpadS * 2, tb = (size_t)2 * n2 * c->kpadS * 2;
+    c->Pchi = (float*)need(A(pb)); c->Pclo = (float*)need(A(pb));
+    c->VThi = (float*)need(A(tb)); c->VTlo = (float*)need(A(tb));
+    const size_t vs = (size_t)naux * nao * c->kpadA * 2, ge = (size_t)nk * ntau * 2 * nao * c->kpadA * 2;
+    const size_t xs = (size_t)ntau * naux * nao * c->kpadA * 2;
+    c->Vs_hi = (float*)need(A(vs)); c->Vs_lo = (float*)need(A(vs));
+    c->Ge_hi = (float*)need(A(ge)); c->Ge_lo = (float*)need(A(ge));
+    c->Gp_hi = (float*)need(A(ge)); c->Gp_lo = (float*)need(A(ge));
+    c->Xs_hi = (float*)need(A(xs)); c->Xs_lo = (float*)need(A(xs));
+    c->y3bytes = (size_t)ntau * nao * c->kpad3 * 2;
+    c->Y3hi = (float*)need(A(c->y3bytes)); c->Y3lo = (float*)need(A(c->y3bytes));
+    c->W3hi = (float*)need(A((size_t)2 * nao * c->kpad3 * 2)); c->W3lo = (float*)need(A((size_t)2 * nao * c->kpad3 * 2));
+    c->vQmax = (float*)need(A((size_t)naux * 4)); c->vQrs = (float*)need(A((size_t)naux * 4));
+    c->gn = (float*)need(A((size_t)4 * ntau * 4));
+    c->eVQ = (int*)need(A((size_t)naux * 4)); c->eVall = (int*)need(A(16));
+    c->eV1 = (int*)need(A((size_t)naux * nao * 4));
+    c->eY = (int*)need(A((size_t)ntau * naux * 4)); c->eZ = (int*)need(A((size_t)ntau * naux * 4));
+    c->eGe = (int*)need(A((size_t)nk * ntau * 4)); c->eGp = (int*)need(A((size_t)nk * ntau * 4));
+    c->ePc = (int*)need(A((size_t)ntau * naux * 4)); c->ePs = (int*)need(A((size_t)ntau * naux * 4));
+    c->eY3 = (int*)need(A((size_t)ntau * 4));
+  }
   // workspace: split-K partials and the screened-solve panels
   size_t ws = screened_work_bytes(naux, (int64_t)nk * ntau);
   const size_t ws_cap = (size_t)4 << 30;
@@ -518,6 +580,21 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   chk(fermi_freqs(ntau, cfg->beta, c->d_fn, c->wn, st), "freqs");
   count(4);
   if (lowp) { chk(to_c64(c->V, c->V32, vbytes / cb, st), "V32"); count(1); }
+  if (c->hfmt) {
+    // V's norms per Q over every slab fix the exponents of the V operands (uniform over the
+    // (k, k') pairs, so that the operands of one grouped GEMM share them)
+    chk(v_norms(c->V, (int64_t)nk * nk, naux, nao, c->vQmax, c->vQrs, st), "V norms");
+    chk(row_exps(c->vQmax, naux, c->eVQ, st), "V exponents");
+    chk(max_exp(c->vQmax, naux, c->eVall + 1, st), "V exponent");
+    count(3);
+    chk(cudaMemsetAsync(c->Zhi, 0, c->zbytes, st), "memset");
+    chk(cudaMemsetAsync(c->Zlo, 0, c->zbytes, st), "memset");
+    chk(cudaMemsetAsync(c->Y3hi, 0, c->y3bytes, st), "memset");
+    chk(cudaMemsetAsync(c->Y3lo, 0, c->y3bytes, st), "memset");
+    const size_t xs = (size_t)ntau * naux * nao * c->kpadA * 2;
+    chk(cudaMemsetAsync(c->Xs_hi, 0, xs, st), "memset");
+    chk(cudaMemsetAsync(c->Xs_lo, 0, xs, st), "memset");
+  }
   // input checks
   chk(cudaMemsetAsync(c->dscr, 0, 64 * 8, st), "memset");
   if (!(cfg->flags & GW_SKIP_CHECKS)) {
@@ -529,11 +606,22 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   chk(cudaMemcpyAsync(c->h_scr, c->dscr, 64 * 8, cudaMemcpyDeviceToHost, st), "copy");
   int h_info = 0;
   chk(cudaMemcpyAsync(&h_info, c->info, 4, cudaMemcpyDeviceToHost, st), "copy");
+  int h_ev = 0;
+  if (c->hfmt) chk(cudaMemcpyAsync(&h_ev, c->eVall + 1, 4, cudaMemcpyDeviceToHost, st), "copy");
   chk(cudaStreamSynchronize(st), "sync");
+  if (c->hfmt) {
+    // uniform exponent of the transposed V operands: max |V| 2^-e < 2^15
+    c->h_Evmax = h_ev;
+    const int ev = h_ev - 15;
+    chk(cudaMemcpy(c->eVall, &ev, 4, cudaMemcpyHostToDevice), "copy");
+  }
   if (s == GW_OK && h_info) { s = GW_ERR_SINGULAR; c->err = "transform matrix is singular"; }
   if (s == GW_OK && !(cfg->flags & GW_SKIP_CHECKS)) {
     const double* h = c->h_scr;
-    if (h[0] > 1e-10 * (h[1] > 1 ? h[1] : 1)) { s = GW_ERR_ARG; c->err = "H0 is not Hermitian"; }
+    if (!std::isfinite(h[1]) || !std::isfinite(h[3]) || !std::isfinite(h[5])) {
+      s = GW_ERR_ARG;
+      c->err = std::string("non-finite value in ") + (!std::isfinite(h[1]) ? "H0" : !std::isfinite(h[3]) ? "S" : "V");
+    } else if (h[0] > 1e-10 * (h[1] > 1 ? h[1] : 1)) { s = GW_ERR_ARG; c->err = "H0 is not Hermitian"; }
     else if (h[2] > 1e-10 * (h[3] > 1 ? h[3] : 1)) { s = GW_ERR_ARG; c->err = "S is not Hermitian"; }
     else if (h[4] > 1e-10 * (h[5] > 1e-300 ? h[5] : 1)) { s = GW_ERR_ARG; c->err = "V^{k'k}(Q) != V^{kk'}(Q)^H"; }
   }
@@ -701,7 +789,12 @@ extern "C" gw_status gw_hf(gw_ctx* c) {
 // out (nq, ntau, naux, naux) receives the unsymmetrised sum, added to its contents
 // when accumulate.  The forward map uses G_tau for both; its tangent runs the chain
 // twice with the tangent in one slot.
+static gw_status polar_chain_half(gw_ctx* c, const double2* Gplus, const double2* Gminus, double2* out,
+                                  bool accumulate);
+static gw_status sigma_chain_half(gw_ctx* c, const double2* Gsrc, const double2* Psrc, double2* out, bool accumulate);
+
 static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gminus, double2* out, bool accumulate) {
+  if (c->hfmt) return polar_chain_half(c, Gplus, Gminus, out, accumulate);
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
   const bool f32 = c->cfg.contract_prec != GW_FP64;
@@ -826,12 +919,174 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
   return GW_OK;
 }
 
+// ------------------------------------------------------------------ chains with 16-bit pieces
+
+// The P~0 chain of Eq. tilde_P0_tau with every GEMM on the tensor cores in 16-bit pieces
+// (same steps and layouts as the split-TF32 chain above):
+//   Y[t][Q][d][b] = sum_a V^{k,k+q}_da(Q) G^{k+q}_ab(t)              (rows (Q, d), batch t)
+//   Z[t][Q][c][b] = -sum_d G^k_cd(t_{ntau-1-j}) Y[t][Q][d][b]         (rows (Q, b), batch t)
+//   P[t][Q][Q'] += (s/Nk) sum_(c,b) Z[t][Q][(c,b)] conj V^{k,k+q}_cb(Q')   (group of k-points)
+// Y and Z are written by the GEMM epilogues directly as the next GEMM's 16-bit operand,
+// scaled by 2^-e with e from the bounds |Y| <= vrs(Q) max|G(t)| and |Z| <= rowsum|G(-t)| |Y|.
+static gw_status polar_chain_half(gw_ctx* c, const double2* Gplus, const double2* Gminus, double2* out,
+                                  bool accumulate) {
+  const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau, fmt = c->hfmt;
+  const int64_t n2 = c->n2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
+  const int64_t ka = c->kpadA, per = 2 * (int64_t)nao * ka, kp = c->kpadP;
+  const int G = c->pgroup;
+  const int64_t zld = G * kp;
+  const int64_t kAll = (int64_t)1 << 40;   // exponent index divisor: one exponent per batch entry
+  cudaStream_t st = c->st;
+  if (!c->deferred) CK(cudaMemsetAsync(c->info + 1, 0, 4, st));
+  // norms of the two G factors, then the row exponents of Y and Z per (t, Q)
+  CK(g_norms(Gplus, ntau, nk, c->nao, c->gn, c->gn + ntau, st));
+  const float* grs_m = c->gn + ntau;
+  if (Gminus != Gplus) {
+    CK(g_norms(Gminus, ntau, nk, nao, c->gn + 2 * ntau, c->gn + 3 * ntau, st));
+    grs_m = c->gn + 3 * ntau;
+    count(1);
+  }
+  CK(polar_exps(c->vQrs, c->gn, grs_m, ntau, naux, c->eY, c->eZ, st));
+  count(2);
+  // G operands per k: Ge[k][t] from G^k(t) (C = A conj(Ge)^T = A G for Hermitian G),
+  // Gp[k][j] from G^k(t_{ntau-1-j}) (C = A Gp^T), one exponent per matrix
+  for (int k = 0; k < nk; ++k) {
+    CK(half_embed_mats(Gplus + (size_t)k * n2, ntau, gstep, nao, nao, hofs(c->Ge_hi, (int64_t)k * ntau * per),
+                       hofs(c->Ge_lo, (int64_t)k * ntau * per), ka, per, fmt, false, c->eGe + (size_t)k * ntau, st));
+    CK(half_embed_mats(Gminus + (size_t)(ntau - 1) * gstep + (size_t)k * n2, ntau, -gstep, nao, nao,
+                       hofs(c->Gp_hi, (int64_t)k * ntau * per), hofs(c->Gp_lo, (int64_t)k * ntau * per), ka, per, fmt,
+                       true, c->eGp + (size_t)k * ntau, st));
+  }
+  count(2 * nk);
+  const double fl12 = 8.0 * ntau * naux * (double)nao * n2;
+  for (int q = c->q0; q < c->q1; ++q) {
+    double2* Pq = out + (size_t)q * ntau * c->na2;
+    for (int k = 0; k < nk; ++k) {
+      const int kq = c->kplus[(size_t)q * nk + k];
+      const int j = k % G;
+      const double2* Vkq = c->V + ((size_t)k * nk + kq) * slab;
+      // Y: A = V^{k,k+q} rows (Q, d) with exact row exponents, B = Ge[k+q][t]
+      CK(half_rows(Vkq, (int64_t)naux * nao, nao, nao, false, c->Vs_hi, c->Vs_lo, ka, ka, fmt, c->eV1, nullptr, st));
+      count(1);
+      {
+        UmmaOperand oa{c->Vs_hi, c->Vs_lo, (int64_t)naux * nao, 1, ka, 0, fmt};
+        UmmaOperand ob{hofs(c->Ge_hi, (int64_t)kq * ntau * per), hofs(c->Ge_lo, (int64_t)kq * ntau * per),
+                       2 * (int64_t)nao, ntau, ka, per, fmt};
+        UmmaScale sc{c->eV1, c->eGe + (size_t)kq * ntau, 0, 1, 0, 1, kAll};
+        UmmaOut o{fmt, c->eY, naux, nao, 0};
+        CK(run_umma(c, fl12, oa, ob, naux * nao, 2 * nao, ka, ntau, c->Xs_hi, false, 1.0, false, 2,
+                    (int64_t)naux * nao * ka, 1, nao, (int64_t)nao * ka, 2, ka, c->Xs_lo, 2 * (int64_t)nao, &sc, &o));
+      }
+      // Z: A = Y^T rows (Q, b) per t (exponent per (t, Q)), B = Gp[k][t]; written into the
+      // (c, b) columns of block j of the grouped last step's A operand
+      {
+        UmmaOperand ya{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka, fmt};
+        UmmaOperand gb{hofs(c->Gp_hi, (int64_t)k * ntau * per), hofs(c->Gp_lo, (int64_t)k * ntau * per),
+                       2 * (int64_t)nao, ntau, ka, per, fmt};
+        UmmaScale sc{c->eY, c->eGp + (size_t)k * ntau, naux, 1, 0, nao, kAll};
+        UmmaOut o{fmt, c->eZ, naux, nao, 0};
+        CK(run_umma(c, fl12, ya, gb, naux * nao, 2 * nao, ka, ntau, hofs(c->Zhi, j * kp), false, -1.0, false, 2,
+                    (int64_t)naux * zld, 1, nao, zld, 2, 2 * (int64_t)nao, hofs(c->Zlo, j * kp), 2 * (int64_t)nao, &sc,
+                    &o));
+      }
+      // embedded conj V^{k,k+q}(Q') rows with the per-Q exponents shared by the group
+      CK(half_embed_conj(Vkq, naux, n2, hofs(c->Vhi, j * kp), hofs(c->Vlo, j * kp), kp, zld, fmt, c->eVQ, st));
+      count(1);
+      if (j == G - 1 || k == nk - 1) {
+        const int g = j + 1, k0 = k - j;
+        UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, zld, 0, fmt};
+        UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, zld, 0, fmt};
+        UmmaScale sc{c->eZ, c->eVQ, 0, 0, 0, 1, 1};
+        CK(run_umma(c, 8.0 * g * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, g * kp, 1, Pq, true,
+                    c->spin / nk, accumulate || k0 > 0, 2 * (int64_t)naux, 0, 1, 0, 0, 0, 0, nullptr,
+                    (g - 1) * kp + 2 * n2, &sc, nullptr));
+      }
+    }
+  }
+  return GW_OK;
+}
+
+// The Sigma~ chain of Eq. tilde_sigma2 with 16-bit pieces (steps and layouts of the
+// split-TF32 chain):
+//   X[t][Q'][(i,a)] = sum_Q conj P~^q_Q'Q(t) V^{k,k-q}_ia(Q)         (rows (t, Q'))
+//   Y[t][i][(Q',b)] = sum_a X[t][Q'][i][a] G^{k-q}_ab(t)             (rows (Q', i), batch t)
+//   Sigma~[t][k][i][j] += -(1/Nk) sum_(Q',b) Y[t][i][(Q',b)] V^{k-q,k}_bj(Q')
+// X's rows are scaled from P~'s row sums of moduli times max |V|; Y's from max_Q' of X's
+// bounds times the row sums of G(t).
+static gw_status sigma_chain_half(gw_ctx* c, const double2* Gsrc, const double2* Psrc, double2* out, bool accumulate) {
+  const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau, fmt = c->hfmt;
+  const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
+  const int64_t ka = c->kpadA, per = 2 * (int64_t)nao * ka, kps = c->kpadS, kp3 = c->kpad3;
+  const int64_t kAll = (int64_t)1 << 40;
+  const int shift = c->h_Evmax + 1;   // X rows: 2^(ePs + shift) bounds |X|
+  cudaStream_t st = c->st;
+  if (!c->deferred) CK(cudaMemsetAsync(c->info + 1, 0, 4, st));
+  if (!accumulate) CK(cudaMemsetAsync(out, 0, (size_t)ntau * gstep * 16, st));
+  CK(g_norms(Gsrc, ntau, nk, nao, c->gn, c->gn + ntau, st));
+  count(1);
+  for (int k = 0; k < nk; ++k)
+    CK(half_embed_mats(Gsrc + (size_t)k * n2, ntau, gstep, nao, nao, hofs(c->Ge_hi, (int64_t)k * ntau * per),
+                       hofs(c->Ge_lo, (int64_t)k * ntau * per), ka, per, fmt, false, c->eGe + (size_t)k * ntau, st));
+  count(nk);
+  const double fl1 = 8.0 * ntau * naux * (double)naux * n2, fl2 = 8.0 * ntau * naux * (double)nao * n2;
+  const int64_t mt = ((int64_t)ntau * nao + 127) / 128, nt = (2 * (int64_t)nao + 159) / 160;
+  int64_t ks = (304 + mt * nt - 1) / (mt * nt);
+  if (ks > kp3 / 64) ks = kp3 / 64;
+  if (ks < 1) ks = 1;
+  for (int q = c->q0; q < c->q1; ++q) {
+    // A operand of the first step: conj P~^q(t) rows (t, Q') with exact row exponents and
+    // the exponents of their sums of moduli; then Y's exponent per t
+    CK(half_rows(Psrc + (size_t)q * ntau * na2, (int64_t)ntau * naux, naux, naux, true, c->Pchi, c->Pclo, kps, kps, fmt,
+                 c->ePc, c->ePs, st));
+    CK(sigma_exps(c->ePs, shift, c->gn + ntau, ntau, naux, c->eY3, st));
+    count(2);
+    for (int k = 0; k < nk; ++k) {
+      const int kmq = c->kminus[(size_t)q * nk + k];
+      // X = conj(P~) V: B = V^{k,k-q} transposed, rows (i, a), K = Q, one exponent
+      CK(half_embed_t(c->V + ((size_t)k * nk + kmq) * slab, naux, n2, c->VThi, c->VTlo, kps, fmt, c->h_Evmax - 15, st));
+      count(1);
+      {
+        UmmaOperand oa{c->Pchi, c->Pclo, (int64_t)ntau * naux, 1, kps, 0, fmt};
+        UmmaOperand ob{c->VThi, c->VTlo, 2 * n2, 1, kps, 0, fmt};
+        UmmaScale sc{c->ePc, c->eVall, 0, 0, 0, 1, kAll};
+        UmmaOut o{fmt, c->ePs, 0, 1, shift};
+        CK(run_umma(c, fl1, oa, ob, ntau * naux, (int)(2 * n2), kps, 1, c->Xs_hi, false, 1.0, false,
+                    (int64_t)nao * ka, 0, 1, 0, 0, 2 * (int64_t)nao, ka, c->Xs_lo, 2 * (int64_t)naux, &sc, &o));
+      }
+      // Y = X G^{k-q}(t): A rows (Q', i) per t, B = Ge[k-q][t]; written as rows (t, i) of
+      // columns (Q', b) for the last step
+      {
+        UmmaOperand xa{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka, fmt};
+        UmmaOperand gb{hofs(c->Ge_hi, (int64_t)kmq * ntau * per), hofs(c->Ge_lo, (int64_t)kmq * ntau * per),
+                       2 * (int64_t)nao, ntau, ka, per, fmt};
+        UmmaScale sc{c->ePs, c->eGe + (size_t)kmq * ntau, naux, 1, shift, nao, kAll};
+        UmmaOut o{fmt, c->eY3, 1, kAll, 0};
+        CK(run_umma(c, fl2, xa, gb, naux * nao, 2 * nao, ka, ntau, c->Y3hi, false, 1.0, false, kp3,
+                    (int64_t)nao * kp3, 1, nao, 2 * (int64_t)nao, 0, 0, c->Y3lo, 2 * (int64_t)nao, &sc, &o));
+      }
+      // Sigma~ += -(1/Nk) Y V^{k-q,k}: B = V^{k-q,k} transposed, rows j, K = (Q', b)
+      CK(half_embed_t(c->V + ((size_t)kmq * nk + k) * slab, (int64_t)naux * nao, nao, c->W3hi, c->W3lo, kp3, fmt,
+                      c->h_Evmax - 15, st));
+      count(1);
+      {
+        UmmaOperand ya{c->Y3hi, c->Y3lo, (int64_t)ntau * nao, 1, kp3, 0, fmt};
+        UmmaOperand wb{c->W3hi, c->W3lo, 2 * (int64_t)nao, 1, kp3, 0, fmt};
+        UmmaScale sc{c->eY3, c->eVall, 0, 0, 0, nao, kAll};
+        CK(run_umma(c, fl2, ya, wb, ntau * nao, 2 * nao, kp3, 1, (double*)(out + (size_t)k * n2), true, -1.0 / nk, true,
+                    2 * (int64_t)nao, 0, (int)ks, nao, 2 * gstep, 0, 0, nullptr, 2 * (int64_t)naux * nao, &sc,
+                    nullptr));
+      }
+    }
+  }
+  return GW_OK;
+}
+
 extern "C" gw_status gw_polarization(gw_ctx* c) {
   if (!c) return GW_ERR_ARG;
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
   const int nk = c->nk, naux = c->naux, ntau = c->ntau;
   const int64_t na2 = c->na2;
-  const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
+  const bool tc = uses_tc(c);
   gw_status s = polar_chain(c, c->G_tau, c->G_tau, c->P0_tau, false);
   if (s != GW_OK) return s;
   if (tc && !c->deferred) {
@@ -902,6 +1157,7 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
 // contents when accumulate).  The forward map uses G_tau and P_tau; the tangent runs
 // it with the tangent in either slot.
 static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc, double2* out, bool accumulate) {
+  if (c->hfmt) return sigma_chain_half(c, Gsrc, Psrc, out, accumulate);
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const int64_t n2 = c->n2, na2 = c->na2, slab = (int64_t)naux * n2, gstep = (int64_t)nk * n2;
   const bool f32 = c->cfg.contract_prec != GW_FP64;
@@ -1026,7 +1282,7 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
 static gw_status sigma_tau_part(gw_ctx* c) {
   const int nk = c->nk, nao = c->nao, ntau = c->ntau;
   const int64_t n2 = c->n2;
-  const bool tc = c->cfg.contract_prec == GW_SPLIT_TF32;
+  const bool tc = uses_tc(c);
   gw_status s = sigma_chain(c, c->G_tau, c->P_tau, c->Stau, false);
   if (s != GW_OK) return s;
   if (tc && !c->deferred) {
@@ -1324,7 +1580,7 @@ extern "C" gw_status gw_selfenergy_vjp(gw_ctx* c, const double* Sbar, double* Gb
 // with the tangent in one G (or P~) slot at a time (P~0 is quadratic in G, Sigma~
 // bilinear in (G, P~)), then the symmetrisation.
 static gw_status tc_check(gw_ctx* c) {
-  if (c->cfg.contract_prec != GW_SPLIT_TF32 || c->deferred) return GW_OK;
+  if (!uses_tc(c) || c->deferred) return GW_OK;
   int h = 0;
   CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -1711,6 +1967,94 @@ extern "C" gw_status gw_batch_iterate(gw_ctx* const* ctxs, int32_t n, int32_t n_
     gw_status s = finish_graph(ctxs[i], nullptr);
     if (s != GW_OK) { g_init_err = "system " + std::to_string(i) + ": " + ctxs[i]->err; return s; }
   }
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint / resume
+
+// File layout: a fixed header (magic, version, sizes, beta, mu, state flags), then G(tau),
+// Sigma_inf and Sigma~(i w) as complex128 arrays, then an FNV-1a hash of everything before it.
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t version, nao, naux, ntau, kmesh[3], flags;
+  double beta, mu, n_at_mu;
+};
+constexpr char kStateMagic[8] = {'G', 'W', 'G', 'B', 'S', 'T', 'A', '1'};
+uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+  return h;
+}
+}  // namespace
+
+extern "C" gw_status gw_save_state(gw_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, GW_ERR_ARG, "null argument");
+  if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function to save");
+  const size_t gsz = (size_t)c->ntau * c->nk * c->n2, ksz = (size_t)c->nk * c->n2;
+  std::vector<double2> G(gsz), Si(ksz), Sw(gsz);
+  CK(cudaMemcpyAsync(G.data(), c->G_tau, gsz * 16, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(Si.data(), c->Sinf, ksz * 16, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(Sw.data(), c->Siw, gsz * 16, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  StateHeader h{};
+  memcpy(h.magic, kStateMagic, 8);
+  h.version = 1; h.nao = c->nao; h.naux = c->naux; h.ntau = c->ntau;
+  for (int i = 0; i < 3; ++i) h.kmesh[i] = c->cfg.kmesh[i];
+  h.flags = (c->have_sigma ? 1 : 0) | (c->have_mu ? 2 : 0);
+  h.beta = c->cfg.beta; h.mu = c->mu; h.n_at_mu = c->n_at_mu;
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(c, GW_ERR_ARG, std::string("cannot open ") + path + " for writing");
+  uint64_t hash = 1469598103934665603ull;
+  bool ok = fwrite(&h, sizeof h, 1, f) == 1;
+  hash = fnv1a(&h, sizeof h, hash);
+  for (const std::vector<double2>* v : {&G, &Si, &Sw}) {
+    ok = ok && fwrite(v->data(), 16, v->size(), f) == v->size();
+    hash = fnv1a(v->data(), v->size() * 16, hash);
+  }
+  ok = ok && fwrite(&hash, 8, 1, f) == 1;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return fail(c, GW_ERR_INTERNAL, std::string("write failed: ") + path);
+  return GW_OK;
+}
+
+extern "C" gw_status gw_load_state(gw_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, GW_ERR_ARG, "null argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(c, GW_ERR_ARG, std::string("cannot open ") + path);
+  StateHeader h{};
+  const size_t gsz = (size_t)c->ntau * c->nk * c->n2, ksz = (size_t)c->nk * c->n2;
+  std::vector<double2> G(gsz), Si(ksz), Sw(gsz);
+  uint64_t hash = 1469598103934665603ull, stored = 0;
+  bool ok = fread(&h, sizeof h, 1, f) == 1;
+  const bool same = ok && memcmp(h.magic, kStateMagic, 8) == 0 && h.version == 1 && h.nao == c->nao &&
+                    h.naux == c->naux && h.ntau == c->ntau && h.kmesh[0] == c->cfg.kmesh[0] &&
+                    h.kmesh[1] == c->cfg.kmesh[1] && h.kmesh[2] == c->cfg.kmesh[2] && h.beta == c->cfg.beta;
+  if (!same) { fclose(f); return fail(c, GW_ERR_ARG, "state file does not match this context's sizes"); }
+  hash = fnv1a(&h, sizeof h, hash);
+  for (std::vector<double2>* v : {&G, &Si, &Sw}) {
+    ok = ok && fread(v->data(), 16, v->size(), f) == v->size();
+    if (ok) hash = fnv1a(v->data(), v->size() * 16, hash);
+  }
+  ok = ok && fread(&stored, 8, 1, f) == 1;
+  char extra;
+  ok = ok && fread(&extra, 1, 1, f) == 0;
+  fclose(f);
+  if (!ok || stored != hash) return fail(c, GW_ERR_ARG, "state file is truncated or corrupt");
+  CK(cudaMemcpyAsync(c->G_tau, G.data(), gsz * 16, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->Sinf, Si.data(), ksz * 16, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->Siw, Sw.data(), gsz * 16, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->have_G = true;
+  c->have_sigma = (h.flags & 1) != 0;
+  c->have_mu = (h.flags & 2) != 0;
+  c->mu = h.mu; c->n_at_mu = h.n_at_mu;
+  c->have_P0 = c->have_P = false;
+  for (gw_quantity q : {GW_Q_P0_TAU, GW_Q_P0_IW, GW_Q_P_IW, GW_Q_P_TAU, GW_Q_SIGMA_TAU, GW_Q_G_IW, GW_Q_GAMMA,
+                        GW_Q_SIGMA_INF_NEW})
+    unmark(c, q);
+  mark(c, GW_Q_G_TAU);
+  if (c->have_mu) { mark(c, GW_Q_MU); mark(c, GW_Q_N_ELEC); }
   return GW_OK;
 }
 

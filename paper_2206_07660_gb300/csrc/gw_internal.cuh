@@ -128,7 +128,8 @@ struct UmmaOperand {
   const float* lo;
   int64_t rows, batch;   // rows per batch, batch count (1 = shared by all z)
   int64_t ld, bs;        // row stride and batch stride in elements
-  int f16 = 0;           // 1: hi/lo hold fp16 pieces (cast pointers), K and strides in fp16 elements
+  int f16 = 0;           // 1: hi/lo hold fp16 pieces, 2: bf16 pieces (cast pointers), K and strides in
+                         // 16-bit elements
 };
 // ksplit > 1: the K range is split over blocks and partial results are added to
 // an fp64 C with atomics (requires accumulate).  row_inner > 0: output row m =
@@ -145,12 +146,21 @@ struct UmmaScale {
   const int* eB;
   int64_t ea_zs, eb_zs;
   int eshift;
+  int64_t ea_div = 1, eb_div = 1;   // row m uses eA[z*ea_zs + m/ea_div], column n eB[z*eb_zs + (n/2)/eb_div]
+};
+// 16-bit pieces as the output of a GEMM (C: hi, C_lo: lo, fp32-class layout in 16-bit
+// elements): D * 2^-(eO[z*eo_zs + m/eo_div] + eo_shift) in fp16 (half = 1) or bf16 (2)
+struct UmmaOut {
+  int half;
+  const int* eO;
+  int64_t eo_zs, eo_div;
+  int eo_shift;
 };
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
                       int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr,
-                      const UmmaScale* scale = nullptr, int64_t kvalid = 0);
+                      const UmmaScale* scale = nullptr, int64_t kvalid = 0, const UmmaOut* out = nullptr);
 // FP64 complex products on tensor cores by exact digit splitting (k_emul.cu)
 int64_t emul_kpad(int64_t K);
 size_t emul_digit_bytes(int64_t rows, int64_t K);
@@ -185,5 +195,23 @@ cudaError_t embed_conj_batched(const double2* src, int64_t count, int64_t ss, in
                                float* lo, int64_t Kpad, int64_t ds, cudaStream_t st);
 cudaError_t embed_plain_batched(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, float* hi,
                                 float* lo, int64_t Kpad, int64_t ds, cudaStream_t st);
+
+// ------------------------------------------------------------------ 16-bit operand pieces (k_half.cu)
+// fmt: 1 fp16, 2 bf16.  Element offsets and Kpad / ldo / ds in 16-bit elements (Kpad a multiple of 64).
+cudaError_t half_rows(const double2* src, int64_t rows, int64_t K, int64_t ld, bool conj, void* hi, void* lo,
+                      int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs, cudaStream_t st);
+cudaError_t half_embed_conj(const double2* src, int64_t rows, int64_t K, void* hi, void* lo, int64_t Kpad,
+                            int64_t ldo, int fmt, const int* ex, cudaStream_t st);
+cudaError_t half_embed_t(const double2* src, int64_t K, int64_t N, void* hi, void* lo, int64_t Kpad, int fmt, int e,
+                         cudaStream_t st);
+cudaError_t half_embed_mats(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, void* hi,
+                            void* lo, int64_t Kpad, int64_t ds, int fmt, bool plain, int* ex, cudaStream_t st);
+cudaError_t v_norms(const double2* V, int64_t nslab, int naux, int nao, float* vmax, float* vrs, cudaStream_t st);
+cudaError_t g_norms(const double2* G, int ntau, int nk, int nao, float* gmax, float* grs, cudaStream_t st);
+cudaError_t polar_exps(const float* vrs, const float* gmax_p, const float* grs_m, int ntau, int naux, int* eY, int* eZ,
+                       cudaStream_t st);
+cudaError_t sigma_exps(const int* eX, int shift, const float* grs, int ntau, int naux, int* eY3, cudaStream_t st);
+cudaError_t max_exp(const float* v, int n, int* out, cudaStream_t st);
+cudaError_t row_exps(const float* v, int n, int* out, cudaStream_t st);
 
 }  // namespace gwk

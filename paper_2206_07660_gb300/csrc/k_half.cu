@@ -1,0 +1,398 @@
+// Operands of the tensor-core contraction chains as 16-bit pieces (fp16 or bf16)
+// with power-of-two scales, and the a-priori bounds that fix those scales.
+//
+// A value x of a row with scale exponent e is stored as hi = rn(x 2^-e),
+// lo = rn(x 2^-e - hi) in the 16-bit format; hi + lo carries 22 significant bits
+// (fp16) or 16 (bf16).  The GEMM's epilogue multiplies its fp32 sums by
+// 2^(eA + eB) and, when it writes the next GEMM's operand, by 2^-eO of that
+// operand's row.  With fp16 the scaled values must stay below 2^15 in magnitude;
+// every exponent here is taken from an upper bound of the row's values (a row
+// maximum, or a product of norms that bounds a matrix product), so nothing
+// overflows.  Values far below the bound keep an absolute error of 2^-24 of it.
+//
+// Exponent rule: for a bound b = f 2^E (f in [0.5, 1)), e = E - 15 when b is the
+// exact row maximum, E - 14 (one bit of margin) when it bounds a sum computed in
+// fp32 by the tensor cores.
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include "gw_internal.cuh"
+
+namespace gwk {
+
+__device__ __forceinline__ int bound_exp(double b, int margin) {
+  int E = 0;
+  if (b > 0.0) frexp(b, &E);
+  return E - 15 + margin;
+}
+
+__device__ __forceinline__ void pieces(int fmt, double x, int e, uint16_t& h, uint16_t& l) {
+  const double d = ldexp(x, -e);
+  if (fmt == 2) {
+    const __nv_bfloat16 hb = __double2bfloat16(d);
+    const __nv_bfloat16 lb = __double2bfloat16(d - (double)__bfloat162float(hb));
+    h = __bfloat16_as_ushort(hb);
+    l = __bfloat16_as_ushort(lb);
+  } else {
+    const __half hh = __double2half(d);
+    const __half lh = __double2half(d - (double)__half2float(hh));
+    h = __half_as_ushort(hh);
+    l = __half_as_ushort(lh);
+  }
+}
+
+__device__ __forceinline__ double wmax(double m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
+}
+__device__ __forceinline__ double wsum(double m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  return m;
+}
+__device__ __forceinline__ double cabs2(double2 v) { return sqrt(v.x * v.x + v.y * v.y); }
+
+// Rows r of a complex matrix (element (r, k) at src + r*ld + k) as real rows
+// (re, +-im) of Kpad 16-bit pieces at row stride ldo, one exponent per row from the
+// row's max |re|, |im| (ex[r]); exs (optional) receives the exponent of the row's
+// sum of moduli (a bound of any product of the row with a vector of modulus <= 1).
+// One warp per row.
+__global__ void __launch_bounds__(256) half_rows_kernel(const double2* __restrict__ src, int64_t rows, int64_t K,
+                                                        int64_t ld, int conj, uint16_t* hi, uint16_t* lo,
+                                                        int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  const double2* x = src + r * ld;
+  double m = 0.0, sm = 0.0;
+  for (int64_t k = lane; k < K; k += 32) {
+    const double2 v = x[k];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    sm += cabs2(v);
+  }
+  const int e = bound_exp(wmax(m), 0);
+  sm = wsum(sm);
+  if (lane == 0) {
+    ex[r] = e;
+    if (exs) exs[r] = bound_exp(sm, 0);
+  }
+  uint32_t* h2 = (uint32_t*)(hi + r * ldo);
+  uint32_t* l2 = (uint32_t*)(lo + r * ldo);
+  for (int64_t c = lane; 2 * c < Kpad; c += 32) {
+    double re = 0.0, im = 0.0;
+    if (c < K) {
+      const double2 v = x[c];
+      re = v.x;
+      im = conj ? -v.y : v.y;
+    }
+    uint16_t hr, lr, hm, lm;
+    pieces(fmt, re, e, hr, lr);
+    pieces(fmt, im, e, hm, lm);
+    h2[c] = (uint32_t)hr | ((uint32_t)hm << 16);
+    l2[c] = (uint32_t)lr | ((uint32_t)lm << 16);
+  }
+}
+
+// Doubled operand of C = A conj(B)^T from complex rows n of B (K entries): real rows
+// 2n = (re, im), 2n+1 = (-im, re) of 16-bit pieces at row stride ldo, with the given
+// exponent ex[n] of each complex row.  One warp per complex row.
+__global__ void __launch_bounds__(256) half_embed_conj_kernel(const double2* __restrict__ src, int64_t rows,
+                                                              int64_t K, uint16_t* hi, uint16_t* lo, int64_t Kpad,
+                                                              int64_t ldo, int fmt, const int* ex) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (n >= rows) return;
+  const double2* x = src + n * K;
+  const int e = ex[n];
+  uint32_t* h0 = (uint32_t*)(hi + 2 * n * ldo);
+  uint32_t* l0 = (uint32_t*)(lo + 2 * n * ldo);
+  uint32_t* h1 = (uint32_t*)(hi + (2 * n + 1) * ldo);
+  uint32_t* l1 = (uint32_t*)(lo + (2 * n + 1) * ldo);
+  for (int64_t c = lane; 2 * c < Kpad; c += 32) {
+    double re = 0.0, im = 0.0;
+    if (c < K) {
+      const double2 v = x[c];
+      re = v.x;
+      im = v.y;
+    }
+    uint16_t hr, lr, hi_, li, hn, ln;
+    pieces(fmt, re, e, hr, lr);
+    pieces(fmt, im, e, hi_, li);
+    pieces(fmt, -im, e, hn, ln);
+    h0[c] = (uint32_t)hr | ((uint32_t)hi_ << 16);
+    l0[c] = (uint32_t)lr | ((uint32_t)li << 16);
+    h1[c] = (uint32_t)hn | ((uint32_t)hr << 16);
+    l1[c] = (uint32_t)ln | ((uint32_t)lr << 16);
+  }
+}
+
+// Doubled operand of C = A B^T where B[n][k] = src[k][n] (K rows of N complex, row
+// stride N): rows 2n = (re, -im), 2n+1 = (im, re) of 16-bit pieces with one exponent
+// e for the whole operand, transposed through shared memory.  Grid (N/32, K/32).
+__global__ void half_embed_t_kernel(const double2* __restrict__ src, int64_t K, int64_t N, uint16_t* hi, uint16_t* lo,
+                                    int64_t Kpad, int fmt, int e) {
+  __shared__ double2 tile[32][33];
+  const int64_t k0 = blockIdx.y * 32, nb = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t k = k0 + r, n = nb + tx;
+    tile[r][tx] = (k < K && n < N) ? src[k * N + n] : make_double2(0, 0);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t n = nb + r, k = k0 + tx;
+    if (n >= N || k >= K) continue;
+    const double2 v = tile[tx][r];
+    uint16_t a, b, c, d, a2, b2, c2, d2;
+    pieces(fmt, v.x, e, a, a2);
+    pieces(fmt, -v.y, e, b, b2);
+    pieces(fmt, v.y, e, c, c2);
+    *(uint32_t*)(hi + (2 * n) * Kpad + 2 * k) = (uint32_t)a | ((uint32_t)b << 16);
+    *(uint32_t*)(lo + (2 * n) * Kpad + 2 * k) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+    *(uint32_t*)(hi + (2 * n + 1) * Kpad + 2 * k) = (uint32_t)c | ((uint32_t)a << 16);
+    *(uint32_t*)(lo + (2 * n + 1) * Kpad + 2 * k) = (uint32_t)c2 | ((uint32_t)a2 << 16);
+    (void)d; (void)d2;
+  }
+  // zero padding columns [2K, Kpad), by the first column of blocks
+  if (blockIdx.y == 0) {
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t n = nb + r;
+      if (n >= N) continue;
+      for (int64_t cc = 2 * K + tx; cc < Kpad; cc += 32) {
+        hi[(2 * n) * Kpad + cc] = 0; hi[(2 * n + 1) * Kpad + cc] = 0;
+        lo[(2 * n) * Kpad + cc] = 0; lo[(2 * n + 1) * Kpad + cc] = 0;
+      }
+    }
+  }
+}
+
+// Batched doubled operands of the nao x nao matrices src[z] (z < count, at src + z*ss
+// complex elements; ss may be negative): plain = 0 gives the operand of C = A conj(B)^T
+// (rows 2n = (re, im), 2n+1 = (-im, re)), plain = 1 that of C = A B^T (rows 2n =
+// (re, -im), 2n+1 = (im, re)).  One exponent per matrix from its max |re|, |im|
+// (ex[z]).  One block per matrix.
+__global__ void __launch_bounds__(256) half_embed_mats_kernel(const double2* __restrict__ src, int64_t ss, int64_t rows,
+                                                              int64_t K, uint16_t* hi, uint16_t* lo, int64_t Kpad,
+                                                              int64_t ds, int fmt, int plain, int* ex) {
+  __shared__ double red[8];
+  const int64_t z = blockIdx.x;
+  const double2* x = src + z * ss;
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < rows * K; i += blockDim.x) m = fmax(m, fmax(fabs(x[i].x), fabs(x[i].y)));
+  m = wmax(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
+    v = wmax(v);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const int e = bound_exp(red[0], 0);
+  if (threadIdx.x == 0) ex[z] = e;
+  uint16_t* H = hi + z * ds;
+  uint16_t* L = lo + z * ds;
+  const int64_t half = Kpad / 2;
+  for (int64_t i = threadIdx.x; i < rows * half; i += blockDim.x) {
+    const int64_t n = i / half, c = i - n * half;
+    double re = 0.0, im = 0.0;
+    if (c < K) {
+      const double2 v = x[n * K + c];
+      re = v.x;
+      im = v.y;
+    }
+    uint16_t hr, lr, hi_, li, hn, ln;
+    pieces(fmt, re, e, hr, lr);
+    pieces(fmt, im, e, hi_, li);
+    pieces(fmt, -im, e, hn, ln);
+    uint32_t* h0 = (uint32_t*)(H + 2 * n * Kpad);
+    uint32_t* l0 = (uint32_t*)(L + 2 * n * Kpad);
+    uint32_t* h1 = (uint32_t*)(H + (2 * n + 1) * Kpad);
+    uint32_t* l1 = (uint32_t*)(L + (2 * n + 1) * Kpad);
+    if (plain) {
+      h0[c] = (uint32_t)hr | ((uint32_t)hn << 16);
+      l0[c] = (uint32_t)lr | ((uint32_t)ln << 16);
+      h1[c] = (uint32_t)hi_ | ((uint32_t)hr << 16);
+      l1[c] = (uint32_t)li | ((uint32_t)lr << 16);
+    } else {
+      h0[c] = (uint32_t)hr | ((uint32_t)hi_ << 16);
+      l0[c] = (uint32_t)lr | ((uint32_t)li << 16);
+      h1[c] = (uint32_t)hn | ((uint32_t)hr << 16);
+      l1[c] = (uint32_t)ln | ((uint32_t)lr << 16);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ norms and bounds
+
+// atomic max of non-negative floats through their (order-preserving) bit patterns
+__device__ __forceinline__ void atomic_fmax_pos(float* p, float v) { atomicMax((int*)p, __float_as_int(v)); }
+
+// Per auxiliary index Q over every (k, k') slab of V [nk*nk][naux][nao][nao]:
+// vmax[Q] = max |V_da(Q)| and vrs[Q] = max_d sum_a |V_da(Q)| (moduli).  Rounded up
+// by a relative 1e-6 so that the float results bound the double values.
+__global__ void v_norms_kernel(const double2* __restrict__ V, int64_t nslab, int naux, int nao, float* vmax,
+                               float* vrs) {
+  const int64_t rowsall = nslab * naux * nao;
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t r = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); r < rowsall; r += (int64_t)gridDim.x * warps) {
+    const int Q = (int)((r / nao) % naux);
+    const double2* x = V + r * nao;
+    double m = 0.0, s = 0.0;
+    for (int a = lane; a < nao; a += 32) {
+      const double v = cabs2(x[a]);
+      m = fmax(m, v);
+      s += v;
+    }
+    m = wmax(m);
+    s = wsum(s);
+    if (lane == 0) {
+      atomic_fmax_pos(vmax + Q, (float)(m * (1 + 1e-6)));
+      atomic_fmax_pos(vrs + Q, (float)(s * (1 + 1e-6)));
+    }
+  }
+}
+
+// Per tau over every k of G [ntau][nk][nao][nao]: gmax[t] = max |G_ab(t)|,
+// grs[t] = max_c sum_d |G_cd(t)| (moduli), rounded up as above.  Grid (blocks, ntau).
+__global__ void g_norms_kernel(const double2* __restrict__ G, int nk, int nao, float* gmax, float* grs) {
+  const int t = blockIdx.y;
+  const int64_t rows = (int64_t)nk * nao;
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const double2* Gt = G + (int64_t)t * rows * nao;
+  for (int64_t r = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * warps) {
+    const double2* x = Gt + r * nao;
+    double m = 0.0, s = 0.0;
+    for (int a = lane; a < nao; a += 32) {
+      const double v = cabs2(x[a]);
+      m = fmax(m, v);
+      s += v;
+    }
+    m = wmax(m);
+    s = wsum(s);
+    if (lane == 0) {
+      atomic_fmax_pos(gmax + t, (float)(m * (1 + 1e-6)));
+      atomic_fmax_pos(grs + t, (float)(s * (1 + 1e-6)));
+    }
+  }
+}
+
+// Row exponents of the P~0 chain intermediates (one per (tau, Q)):
+//   Y[t][Q] = V(Q) G(t):          |Y_db| <= vrs[Q] gmax_p[t]                  -> eY
+//   Z[t][Q] = G(-t) V(Q) G(t):    |Z_cb| <= grs_m[ntau-1-t] vrs[Q] gmax_p[t]  -> eZ
+// (gmax_p from the G(t) factor, grs_m from the G(-t) factor; G(-t_j) = -G(t_{ntau-1-j})).
+__global__ void polar_exps_kernel(const float* vrs, const float* gmax_p, const float* grs_m, int ntau, int naux,
+                                  int* eY, int* eZ) {
+  const int64_t n = (int64_t)ntau * naux;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(i / naux), Q = (int)(i - (int64_t)t * naux);
+    const double y = (double)vrs[Q] * (double)gmax_p[t];
+    eY[i] = bound_exp(y, 1);
+    eZ[i] = bound_exp(y * (double)grs_m[ntau - 1 - t], 1);
+  }
+}
+
+// Row exponent of the Sigma~ chain's Y[t][i][(Q', b)] (uniform over Q'):
+// |Y| <= max_Q' 2^(eX[t][Q'] + 15) grs[t], with eX the exponents of X's rows.
+__global__ void sigma_exps_kernel(const int* eX, int shift, const float* grs, int ntau, int naux, int* eY3) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntau) return;
+  int m = -100000;
+  for (int q = 0; q < naux; ++q) m = max(m, eX[(int64_t)t * naux + q]);
+  int E = 0;
+  if (grs[t] > 0.f) frexpf(grs[t], &E);
+  eY3[t] = m + shift + E + 1;
+}
+
+__global__ void max_exp_kernel(const float* v, int n, int* out) {
+  float m = 0.f;
+  for (int i = 0; i < n; ++i) m = fmaxf(m, v[i]);
+  int E = 0;
+  if (m > 0.f) frexpf(m, &E);
+  out[0] = E;
+}
+
+__global__ void row_exps_kernel(const float* v, int n, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = bound_exp((double)v[i], 0);
+}
+
+static inline unsigned nblk(int64_t rows, int per) {
+  const int64_t b = (rows + per - 1) / per;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------------------------------ launch wrappers
+
+cudaError_t half_rows(const double2* src, int64_t rows, int64_t K, int64_t ld, bool conj, void* hi, void* lo,
+                      int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs, cudaStream_t st) {
+  if (Kpad % 64 || rows <= 0) return cudaErrorInvalidValue;
+  half_rows_kernel<<<nblk(rows, 8), 256, 0, st>>>(src, rows, K, ld, conj ? 1 : 0, (uint16_t*)hi, (uint16_t*)lo, Kpad,
+                                                   ldo > 0 ? ldo : Kpad, fmt, ex, exs);
+  return cudaGetLastError();
+}
+
+cudaError_t half_embed_conj(const double2* src, int64_t rows, int64_t K, void* hi, void* lo, int64_t Kpad,
+                            int64_t ldo, int fmt, const int* ex, cudaStream_t st) {
+  if (Kpad % 64 || rows <= 0) return cudaErrorInvalidValue;
+  half_embed_conj_kernel<<<nblk(rows, 8), 256, 0, st>>>(src, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad,
+                                                         ldo > 0 ? ldo : Kpad, fmt, ex);
+  return cudaGetLastError();
+}
+
+cudaError_t half_embed_t(const double2* src, int64_t K, int64_t N, void* hi, void* lo, int64_t Kpad, int fmt, int e,
+                         cudaStream_t st) {
+  if (Kpad % 64 || K <= 0 || N <= 0) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32), 1);
+  half_embed_t_kernel<<<grid, 256, 0, st>>>(src, K, N, (uint16_t*)hi, (uint16_t*)lo, Kpad, fmt, e);
+  return cudaGetLastError();
+}
+
+cudaError_t half_embed_mats(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, void* hi,
+                            void* lo, int64_t Kpad, int64_t ds, int fmt, bool plain, int* ex, cudaStream_t st) {
+  if (Kpad % 64 || count <= 0 || count > INT32_MAX) return cudaErrorInvalidValue;
+  half_embed_mats_kernel<<<(unsigned)count, 256, 0, st>>>(src, ss, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad, ds,
+                                                          fmt, plain ? 1 : 0, ex);
+  return cudaGetLastError();
+}
+
+cudaError_t v_norms(const double2* V, int64_t nslab, int naux, int nao, float* vmax, float* vrs, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(vmax, 0, (size_t)naux * 4, st);
+  if (!e) e = cudaMemsetAsync(vrs, 0, (size_t)naux * 4, st);
+  if (e) return e;
+  v_norms_kernel<<<152 * 8, 256, 0, st>>>(V, nslab, naux, nao, vmax, vrs);
+  return cudaGetLastError();
+}
+
+cudaError_t g_norms(const double2* G, int ntau, int nk, int nao, float* gmax, float* grs, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(gmax, 0, (size_t)ntau * 4, st);
+  if (!e) e = cudaMemsetAsync(grs, 0, (size_t)ntau * 4, st);
+  if (e) return e;
+  const int64_t rows = (int64_t)nk * nao;
+  dim3 grid(nblk(rows, 8 * 4) > 64 ? 64 : nblk(rows, 8 * 4), (unsigned)ntau);
+  g_norms_kernel<<<grid, 256, 0, st>>>(G, nk, nao, gmax, grs);
+  return cudaGetLastError();
+}
+
+cudaError_t polar_exps(const float* vrs, const float* gmax_p, const float* grs_m, int ntau, int naux, int* eY, int* eZ,
+                       cudaStream_t st) {
+  polar_exps_kernel<<<nblk((int64_t)ntau * naux, 256), 256, 0, st>>>(vrs, gmax_p, grs_m, ntau, naux, eY, eZ);
+  return cudaGetLastError();
+}
+
+cudaError_t sigma_exps(const int* eX, int shift, const float* grs, int ntau, int naux, int* eY3, cudaStream_t st) {
+  sigma_exps_kernel<<<nblk(ntau, 128), 128, 0, st>>>(eX, shift, grs, ntau, naux, eY3);
+  return cudaGetLastError();
+}
+
+cudaError_t max_exp(const float* v, int n, int* out, cudaStream_t st) {
+  max_exp_kernel<<<1, 1, 0, st>>>(v, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t row_exps(const float* v, int n, int* out, cudaStream_t st) {
+  row_exps_kernel<<<nblk(n, 256), 256, 0, st>>>(v, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace gwk

@@ -174,7 +174,8 @@ __global__ void vpair_kernel(const double2* __restrict__ V, int nk, int naux, in
     double2 a = V[e];
     double2 b = V[(((int64_t)k2 * nk + k) * naux + Q) * n2 + (int64_t)j * nao + i];
     dev = fmax(dev, hypot(a.x - b.x, a.y + b.y));
-    mx = fmax(mx, hypot(a.x, a.y));
+    // a non-finite entry makes the magnitude +inf (fmax alone would skip a NaN)
+    mx = (isfinite(a.x) && isfinite(a.y)) ? fmax(mx, hypot(a.x, a.y)) : INFINITY;
   }
   atomic_max_nonneg(out, dev);
   atomic_max_nonneg(out + 1, mx);
@@ -192,7 +193,7 @@ __global__ void herm_check_kernel(const double2* __restrict__ X, int64_t n, int6
     int64_t m = e / n2, r = e - m * n2, i = r / n, j = r - i * n;
     double2 a = X[e], b = X[m * n2 + j * n + i];
     dev = fmax(dev, hypot(a.x - b.x, a.y + b.y));
-    mx = fmax(mx, hypot(a.x, a.y));
+    mx = (isfinite(a.x) && isfinite(a.y)) ? fmax(mx, hypot(a.x, a.y)) : INFINITY;
   }
   atomic_max_nonneg(out, dev);
   atomic_max_nonneg(out + 1, mx);

@@ -27,6 +27,8 @@
 // code, skips the remaining work, releases its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 #include "gw_internal.cuh"
 
 #include <map>
@@ -66,16 +68,48 @@ struct UmmaArgs {
   int klast8;          // persistent kernel: K = 8 steps of the last k-block that hold data (1..4)
   uint32_t spin;       // persistent kernel: iteration limit of the pipeline waits (the teardown waits use
                        // UM_SPIN_LIMIT)
-  int f16;             // persistent kernel: operands are fp16 (kind::f16), else tf32 (kind::tf32)
-  int bke;             // elements per k-block (one 128-byte swizzle row): 32 (tf32) or 64 (fp16)
-  // eA != null: D[m][n] is scaled by 2^(eA[m] + eB[n/2] + eshift) (operands stored with
-  // power-of-two row scales: digit-split FP64 products, fp16 pieces)
+  int f16;             // persistent kernel: operands are 16-bit (kind::f16): 1 fp16, 2 bf16; 0: tf32 (kind::tf32)
+  int bke;             // elements per k-block (one 128-byte swizzle row): 32 (tf32) or 64 (fp16, bf16)
+  // eA != null: D[m][n] is scaled by 2^(eA[z*ea_zs + m/ea_div] + eB[z*eb_zs + (n/2)/eb_div] + eshift)
+  // (operands stored with power-of-two row scales: digit-split FP64 products, half pieces)
   const int* eA;
   const int* eB;
   int64_t ea_zs, eb_zs;
+  int64_t ea_div, eb_div;
   int eshift;
+  // o_half != 0: the fp32 output is written as 16-bit hi (C) / lo (C_lo) pieces (1 fp16, 2 bf16)
+  // of D * 2^-(eO[z*eo_zs + m/eo_div] + eo_shift): the next GEMM's operand with its row scale
+  int o_half;
+  const int* eO;
+  int64_t eo_zs, eo_div;
+  int eo_shift;
   int* err;
 };
+
+// exponent of the row scale of row m (output or operand side); 0 without scales
+__device__ __forceinline__ int row_exp(const UmmaArgs& a, int z, int64_t m) {
+  return a.eA ? a.eA[(int64_t)z * a.ea_zs + m / a.ea_div] + a.eshift : 0;
+}
+__device__ __forceinline__ int col_exp(const UmmaArgs& a, int z, int64_t n) {
+  return a.eB ? a.eB[(int64_t)z * a.eb_zs + (n >> 1) / a.eb_div] : 0;
+}
+__device__ __forceinline__ int out_exp(const UmmaArgs& a, int z, int64_t m) {
+  return a.eO ? a.eO[(int64_t)z * a.eo_zs + m / a.eo_div] + a.eo_shift : 0;
+}
+// v as 16-bit hi / lo pieces (hi = rn(v), lo = rn(v - hi)) in the output format
+__device__ __forceinline__ void half_pieces(int fmt, float v, uint16_t& h, uint16_t& l) {
+  if (fmt == 2) {
+    const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
+    h = __bfloat16_as_ushort(hb);
+    l = __bfloat16_as_ushort(lb);
+  } else {
+    const __half hh = __float2half_rn(v);
+    const __half lh = __float2half_rn(v - __half2float(hh));
+    h = __half_as_ushort(hh);
+    l = __half_as_ushort(lh);
+  }
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -400,8 +434,8 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
     double al = a.alpha;
     int myexp = 0;   // row exponent of row r0 + lane (scaled mode)
     if (a.eA) {
-      if (lane < nrow) myexp = a.eA[(int64_t)z * a.ea_zs + r0 + lane];
-      if (colok) al = ldexp(al, a.eB[(int64_t)z * a.eb_zs + (n >> 1)] + a.eshift);
+      if (lane < nrow) myexp = row_exp(a, z, r0 + lane);
+      if (colok) al = ldexp(al, col_exp(a, z, n));
     }
     if (a.ksplit > 1) {
       for (int r = 0; r < 32; ++r) {
@@ -443,10 +477,25 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
     // scaled operands: column exponent here, row exponent per row below
     int myexp = 0, colexp = 0;
     if (a.eA) {
-      if (lane < nrow) myexp = a.eA[(int64_t)z * a.ea_zs + r0 + lane];
-      if (colok) colexp = a.eB[(int64_t)z * a.eb_zs + (n >> 1)] + a.eshift;
+      if (lane < nrow) myexp = row_exp(a, z, r0 + lane);
+      if (colok) colexp = col_exp(a, z, n);
     }
-    if (a.eA) {
+    if (a.o_half) {
+      // 16-bit hi / lo pieces of D 2^(eA + eB - eO): the next GEMM's operand
+      if (lane < nrow) myexp -= out_exp(a, z, r0 + lane);
+      uint16_t* Ch = (uint16_t*)a.C;
+      uint16_t* Cl = (uint16_t*)a.C_lo;
+      for (int r = 0; r < 32; ++r) {
+        const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+        const int rs = __shfl_sync(0xffffffffu, myexp, r);
+        if (r < nrow && colok) {
+          uint16_t h, l;
+          half_pieces(a.o_half, ldexpf(al * stg[r * 33 + lane], colexp + rs), h, l);
+          Ch[base + coff] = h;
+          Cl[base + coff] = l;
+        }
+      }
+    } else if (a.eA) {
       // scaled operands: the row factor 2^eA (shuffled per row) times the column
       // factor 2^(eB + eshift), both exact powers of two
       const float rsc = ldexpf(1.0f, myexp), csc = ldexpf(al, colexp);
@@ -629,7 +678,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
       // instruction descriptor: D fp32, A/B tf32 (format 2) or fp16 (format 0), both
       // K-major, N = BN, M = 128
       const bool f16 = a.f16 != 0;
-      const uint32_t fmt = f16 ? 0u : 2u;
+      const uint32_t fmt = a.f16 == 2 ? 1u : f16 ? 0u : 2u;   // operand format: bf16 1, fp16 0, tf32 2
       const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
                              ((uint32_t)(UM_BM >> 4) << 24);
       uint32_t g = 0;
@@ -808,13 +857,13 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           if (rok && a.c_fp64) {
             double* Cd = (double*)a.C;
-            const int rexp = a.eA ? a.eA[(int64_t)z * a.ea_zs + row] + a.eshift : 0;
+            const int rexp = row_exp(a, z, row);
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const int ex = a.eB ? rexp + a.eB[(int64_t)z * a.eb_zs + (n >> 1)] : rexp;
+                const int ex = rexp + col_exp(a, z, n);
                 const double sre = ldexp(a.alpha * (double)__uint_as_float(v[j]), ex);
                 const double sim = ldexp(a.alpha * (double)__uint_as_float(v[j + 1]), ex);
                 double2* p2 = (double2*)(Cd + off);
@@ -826,15 +875,33 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
                 }
               }
             }
-          } else if (rok && a.eA) {
-            // scaled operands: 2^(eA[row] + eB[column pair] + eshift), exact powers of two
-            const float rsc = ldexpf(al, a.eA[(int64_t)z * a.ea_zs + row] + a.eshift);
+          } else if (rok && a.o_half) {
+            // 16-bit hi / lo pieces of D 2^(eA + eB - eO), (re, im) pairs as one 32-bit store
+            const int rexp = row_exp(a, z, row) - out_exp(a, z, row);
+            uint16_t* Ch = (uint16_t*)a.C;
+            uint16_t* Cl = (uint16_t*)a.C_lo;
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const float sc = rsc * ldexpf(1.0f, a.eB[(int64_t)z * a.eb_zs + (n >> 1)]);
+                const int ex = rexp + col_exp(a, z, n);
+                uint16_t hr, lr, hm, lm;
+                half_pieces(a.o_half, ldexpf(al * __uint_as_float(v[j]), ex), hr, lr);
+                half_pieces(a.o_half, ldexpf(al * __uint_as_float(v[j + 1]), ex), hm, lm);
+                *(uint32_t*)(Ch + off) = (uint32_t)hr | ((uint32_t)hm << 16);
+                *(uint32_t*)(Cl + off) = (uint32_t)lr | ((uint32_t)lm << 16);
+              }
+            }
+          } else if (rok && a.eA) {
+            // scaled operands: 2^(eA[row] + eB[column pair] + eshift), exact powers of two
+            const float rsc = ldexpf(al, row_exp(a, z, row));
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const int n = n0 + cbase + cb + j;
+              if (cb + j < BW && n < a.N) {
+                const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
+                const float sc = rsc * ldexpf(1.0f, col_exp(a, z, n));
                 const float re = sc * __uint_as_float(v[j]), im = sc * __uint_as_float(v[j + 1]);
                 if (a.C_lo) {
                   const float hr = tf32_rna_dev(re), hi_ = tf32_rna_dev(im);
@@ -925,7 +992,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 3-D tensor map {kdim, rows, batch} of fp32 (or fp16) elements with row stride ld and
 // batch stride bs (elements); the box is one 128-byte row of K by box_rows rows
 static bool make_map(CUtensorMap* m, const void* base, int64_t kdim, int64_t rows, int64_t batch, int64_t ld,
-                     int64_t bs, uint32_t box_rows, bool f16) {
+                     int64_t bs, uint32_t box_rows, int f16) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int64_t esz = f16 ? 2 : 4;
@@ -934,7 +1001,9 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t kdim, int64_t row
   cuuint64_t strides[2] = {(cuuint64_t)(ld * esz), (cuuint64_t)((batch > 1 ? bs : ld * rows) * esz)};
   cuuint32_t box[3] = {(cuuint32_t)(128 / esz), box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims,
+  const CUtensorMapDataType dt = f16 == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = fn(m, dt, 3, (void*)base, dims,
                   strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -991,7 +1060,7 @@ static cudaError_t umma_launch(int bn, const UmmaOperand& A, const UmmaOperand& 
                                const UmmaArgs& a, int batch, cudaStream_t st) {
   CUtensorMap maps[4];
   const uint32_t box = (uint32_t)bn;
-  const bool f16 = a.f16 != 0;
+  const int f16 = a.f16;
   if (!make_map(&maps[0], A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM, f16) ||
       !make_map(&maps[1], nseg > 1 ? A.lo : A.hi, Kpad, A.rows, A.batch, A.ld, A.bs, UM_BM, f16) ||
       !make_map(&maps[2], B.hi, Kpad, B.rows, B.batch, B.ld, B.bs, box, f16) ||
@@ -1084,7 +1153,7 @@ static int tune_bn(const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1, int64_t col_inner,
-                      int64_t col_s1, float* C_lo, const UmmaScale* scale, int64_t kvalid) {
+                      int64_t col_s1, float* C_lo, const UmmaScale* scale, int64_t kvalid, const UmmaOut* out) {
   const bool f16 = A.f16 != 0;
   const int bke = f16 ? 64 : UM_BK;   // elements per 128-byte k-block
   if (B.f16 != A.f16) return cudaErrorInvalidValue;   // one MMA kind: both operands fp16 or both tf32
@@ -1095,7 +1164,7 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   if ((int64_t)batch * ksplit > 65535) return cudaErrorInvalidValue;
   UmmaArgs a{};
   a.M = M; a.N = N; a.kblocks = (int)(Kpad / bke); a.nseg = nseg;
-  a.f16 = f16 ? 1 : 0;
+  a.f16 = A.f16;
   a.bke = bke;
   a.a_batched = A.batch > 1; a.b_batched = B.batch > 1;
   a.C = C; a.c_fp64 = c_fp64; a.accumulate = accumulate; a.alpha = alpha; a.c_ld = c_ld; a.c_zs = c_zs;
@@ -1106,11 +1175,19 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   a.col_s1 = col_s1;
   a.C_lo = C_lo;
   if (C_lo && (c_fp64 || accumulate)) return cudaErrorInvalidValue;
+  a.ea_div = a.eb_div = a.eo_div = 1;
+  if (out && out->half) {
+    // 16-bit pieces of the output (with a row scale for the next GEMM)
+    if (!C_lo || !g_persistent || (out->half != 1 && out->half != 2)) return cudaErrorInvalidValue;
+    a.o_half = out->half; a.eO = out->eO; a.eo_zs = out->eo_zs; a.eo_shift = out->eo_shift;
+    a.eo_div = out->eo_div > 0 ? out->eo_div : 1;
+  }
+  const int oes = a.o_half ? 2 : 4;   // bytes per element of an fp32-class output
   // (re, im) column pairs of a complex output that land next to each other while
   // consecutive rows are 2 floats apart: stored row by row from the tile lanes
   a.direct = (((!c_fp64 && !accumulate) || (c_fp64 && ksplit == 1)) && col_inner == 2 && c_ld == 2 &&
               (N % 2) == 0 && (c_zs % 2) == 0 && (a.row_s1 % 2) == 0 && (col_s1 % 2) == 0 &&
-              ((uintptr_t)C % (c_fp64 ? 16 : 8)) == 0 && ((uintptr_t)C_lo % 8) == 0) ? 1 : 0;
+              ((uintptr_t)C % (c_fp64 ? 16 : 2 * oes)) == 0 && ((uintptr_t)C_lo % (2 * oes)) == 0) ? 1 : 0;
   a.err = err;
   a.chunk_len = nseg == 3 ? g_chunk_len : UM_FLUSH;
   a.prefetch = g_prefetch;
@@ -1126,13 +1203,16 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   if (scale) {
     if (!g_persistent) return cudaErrorInvalidValue;
     a.eA = scale->eA; a.eB = scale->eB; a.ea_zs = scale->ea_zs; a.eb_zs = scale->eb_zs; a.eshift = scale->eshift;
+    a.ea_div = scale->ea_div > 0 ? scale->ea_div : 1;
+    a.eb_div = scale->eb_div > 0 ? scale->eb_div : 1;
   }
   int bn = cost_model_bn(N);
   if (g_force_bn) return umma_launch(g_force_bn, A, B, Kpad, nseg, a, batch, st);
   if (g_persistent && g_autotune) {
     const TuneKey key{M, N, batch, nseg, ksplit,
                       (c_fp64 ? 1 : 0) | (accumulate ? 2 : 0) | (a.direct ? 4 : 0) | (C_lo ? 8 : 0) |
-                          (a.a_batched ? 16 : 0) | (a.b_batched ? 32 : 0) | (scale ? 64 : 0) | (f16 ? 128 : 0),
+                          (a.a_batched ? 16 : 0) | (a.b_batched ? 32 : 0) | (scale ? 64 : 0) | (f16 ? 128 : 0) |
+                          (a.f16 == 2 ? 256 : 0) | (a.o_half << 9),
                       Kpad};
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);

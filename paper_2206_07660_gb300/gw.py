@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libgwgb.so")
 
 GW_OK, GW_ERR_ARG, GW_ERR_CUDA, GW_ERR_OOM, GW_ERR_NOT_CONVERGED, GW_ERR_SINGULAR, GW_ERR_TIMEOUT, \
     GW_ERR_STATE, GW_ERR_INTERNAL = range(9)
-PRECISIONS = {"fp64": 0, "fp32": 1, "split_bf16": 2, "split_tf32": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "split_bf16": 2, "split_tf32": 3, "split_f16": 4}
 GW_INPUT_DEVICE, GW_BORROW_V, GW_SKIP_CHECKS, GW_SMALL_TENSOR, GW_SMALL_SIMT, GW_FP64_NATIVE = 1, 2, 4, 8, 16, 32
 
 QUANTITIES = {
@@ -70,6 +70,8 @@ def load():
                  "gw_selfenergy_partial", "gw_selfenergy_finish"):
         getattr(lib, name).argtypes = [P]
     lib.gw_set_q_range.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+    lib.gw_save_state.argtypes = [P, ctypes.c_char_p]
+    lib.gw_load_state.argtypes = [P, ctypes.c_char_p]
     lib.gw_dyson.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.gw_iterate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(GwIterStats)]
     lib.gw_last_error.argtypes = [P]
@@ -92,7 +94,8 @@ def load():
                  "gw_selfenergy", "gw_dyson", "gw_iterate", "gw_reset_sigma", "gw_profile", "gw_profile_read",
                  "gw_polarization_vjp", "gw_selfenergy_vjp", "gw_iterate_graph", "gw_batch_iterate",
                  "gw_polarization_jvp", "gw_screened_jvp", "gw_selfenergy_jvp", "gw_sc_jvp",
-                 "gw_iterate_newton", "gw_selfenergy_partial", "gw_selfenergy_finish", "gw_set_q_range"):
+                 "gw_iterate_newton", "gw_selfenergy_partial", "gw_selfenergy_finish", "gw_set_q_range", "gw_save_state",
+                 "gw_load_state"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -265,6 +268,14 @@ class GW:
 
     def set_q_range(self, q0, q1):
         self._check(self.lib.gw_set_q_range(self.ctx, int(q0), int(q1)))
+
+    def save_state(self, path):
+        """Checkpoint G(tau), Sigma_inf, Sigma(i w) and mu to a host file."""
+        self._check(self.lib.gw_save_state(self.ctx, os.fsencode(path)))
+
+    def load_state(self, path):
+        """Resume from a checkpoint written by save_state (same sizes and beta)."""
+        self._check(self.lib.gw_load_state(self.ctx, os.fsencode(path)))
 
     def dyson(self):
         mu = ctypes.c_double()

@@ -22,7 +22,7 @@ from synth import LazyV, device_V, make_config_system
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-TOL_HA = {"split_tf32": 1e-6, "fp64": 1e-10}
+TOL_HA = {"split_tf32": 1e-6, "split_f16": 1e-6, "fp64": 1e-10}
 Q = 16          # q = (1, 0, 0) on the 4x4x4 mesh
 K0 = 5
 KS = 9          # Sigma~ row
@@ -56,7 +56,7 @@ def _ctx(sysd, Vd, precision):
                precision=precision, borrow_V=True, skip_checks=True)
 
 
-@pytest.mark.parametrize("precision", ["split_tf32", "fp64"])
+@pytest.mark.parametrize("precision", ["split_tf32", "split_f16", "fp64"])
 def test_c3_polarization_two_pairs(c3, precision):
     import torch
     sysd, st, Gs, P0, _, _, Vd = c3
@@ -74,7 +74,7 @@ def test_c3_polarization_two_pairs(c3, precision):
     assert err < TOL_HA[precision], (err, np.abs(P0).max())
 
 
-@pytest.mark.parametrize("precision", ["split_tf32", "fp64"])
+@pytest.mark.parametrize("precision", ["split_tf32", "split_f16", "fp64"])
 def test_c3_selfenergy_two_q(c3, precision):
     import torch
     sysd, st, _, _, Pslices, Sref, Vd = c3

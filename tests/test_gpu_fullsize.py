@@ -22,7 +22,7 @@ from synth import make_config_system
 
 pytestmark = pytest.mark.gpu
 
-TOL_HA = {"split_tf32": 1e-6, "fp64": 1e-10}
+TOL_HA = {"split_tf32": 1e-6, "split_f16": 1e-6, "fp64": 1e-10}
 Q_SLICE, K_SLICE = 5, 13
 
 
@@ -39,7 +39,7 @@ def c2():
     return sysd, st, P0q, P
 
 
-@pytest.mark.parametrize("precision", ["split_tf32", "fp64"])
+@pytest.mark.parametrize("precision", ["split_tf32", "split_f16", "fp64"])
 def test_c2_polarization_one_q(c2, precision):
     sysd, st, ref, _ = c2
     g = gpu(sysd, precision=precision)
@@ -65,7 +65,7 @@ def test_c2_screened_all(c2):
     g.close()
 
 
-@pytest.mark.parametrize("precision", ["split_tf32", "fp64"])
+@pytest.mark.parametrize("precision", ["split_tf32", "split_f16", "fp64"])
 def test_c2_selfenergy_one_k(c2, precision):
     sysd, st, _, P = c2
     k = K_SLICE

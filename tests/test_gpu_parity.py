@@ -161,13 +161,13 @@ def test_lowp_contractions_c1_fp32():
     assert np.abs(g.get("Sigma_inf") - st.Sigma_inf).max() < 1e-5
 
 
-@pytest.mark.parametrize("small", ["simt", "tensor"])
-def test_mixed_path_c1_within_1e6_ha(small):
-    # the mixed path (split-TF32 tensor-core contractions, FP64 elsewhere) against the
-    # FP64 oracle over two damped iterations: max abs error of Sigma_inf, Sigma~(tau),
-    # Sigma~(i w) and G(tau) below the 1e-6 Ha target of the mixed path
+@pytest.mark.parametrize("precision,small", [("split_tf32", "simt"), ("split_tf32", "tensor"), ("split_f16", "auto")])
+def test_mixed_path_c1_within_1e6_ha(precision, small):
+    # the mixed path (split-TF32 or row-scaled split-fp16 tensor-core contractions, FP64
+    # elsewhere) against the FP64 oracle over two damped iterations: max abs error of
+    # Sigma_inf, Sigma~(tau), Sigma~(i w) and G(tau) below the 1e-6 Ha target
     sysd = make_config_system("C1")
-    g = gpu(sysd, precision="split_tf32", small_steps=small, damping=0.5)
+    g = gpu(sysd, precision=precision, small_steps=small, damping=0.5)
     st = oracle_state(sysd, damping=0.5)
     for it in range(2):
         g.iterate(1)
@@ -176,6 +176,19 @@ def test_mixed_path_c1_within_1e6_ha(small):
                 for q in ("Sigma_inf", "Sigma_tau", "Sigma_iw", "G_tau")}
         assert max(errs.values()) < 1e-6, (it, errs)
         assert abs(g.get("mu") - st.mu) < 1e-6
+
+
+def test_split_bf16_c1_error():
+    # bf16 pieces carry 16 significant bits: the error against the FP64 oracle after one
+    # iteration is bounded at the 1e-4 Ha level (and reported by the benchmark)
+    sysd = make_config_system("C1")
+    g = gpu(sysd, precision="split_bf16")
+    st = oracle_state(sysd)
+    g.iterate(1)
+    st.iterate()
+    err = max(float(np.abs(g.get("Sigma_tau") - st.Sigma_tau).max()),
+              float(np.abs(g.get("Sigma_inf") - st.Sigma_inf).max()))
+    assert err < 1e-4, err
 
 
 def test_get_refuses_unwritten_quantities():
@@ -221,7 +234,8 @@ def test_rejects_bad_inputs():
         g.polarization()     # no G yet
 
 
-@pytest.mark.parametrize("precision,small", [("fp32", "auto"), ("split_tf32", "simt"), ("split_tf32", "tensor")])
+@pytest.mark.parametrize("precision,small", [("fp32", "auto"), ("split_tf32", "simt"), ("split_tf32", "tensor"),
+                                             ("split_f16", "auto"), ("split_bf16", "auto")])
 @pytest.mark.parametrize("nao,naux,kmesh,ntau", [(5, 70, (3, 1, 1), 12), (13, 20, (2, 1, 1), 10),
                                                  (64, 9, (1, 1, 1), 6), (65, 6, (1, 1, 1), 4)])
 def test_lowp_stages(nao, naux, kmesh, ntau, precision, small):
@@ -234,12 +248,13 @@ def test_lowp_stages(nao, naux, kmesh, ntau, precision, small):
     g = gpu(sysd, precision=precision, small_steps=small)
     g.set("G_tau", G)
     g.polarization()
+    tol = 3e-4 if precision == "split_bf16" else 2e-5
     P0 = ogw.polarization_tau(st.V, G, st.km)
-    assert rel(g.get("P0_tau"), P0) < 2e-5
+    assert rel(g.get("P0_tau"), P0) < tol
     g.set("P_tau", P)
     g.selfenergy()
     S = ogw.selfenergy_tau(st.V, G, P, st.km)
-    assert rel(g.get("Sigma_tau"), S) < 2e-5
+    assert rel(g.get("Sigma_tau"), S) < tol
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split_tf32"])
