@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-slices", action="store_true", help="skip the oracle slices and the fp64-path timing")
+    p.add_argument("--no-fp64", action="store_true", help="skip the fp64 path on the slices")
     p.add_argument("--cpu-pairs", type=int, default=2, help="(q, k) pairs in the CPU baseline sample")
     p.add_argument("--peaks", action="store_true")
     p.add_argument("--gemm", nargs=5, type=int, action="append", metavar=("M", "N", "K", "B", "F64"),
@@ -547,10 +548,12 @@ def run_gw(args):
         r_mixed = run_slices(g, sl, st.G_tau, torch)
         g.close()
         g = None
-        g64 = make_context(sysd, Vd, "fp64", args)
-        g64.dyson()
-        r64 = run_slices(g64, sl, st.G_tau, torch)
-        g64.close()
+        r64 = None
+        if not args.no_fp64:
+            g64 = make_context(sysd, Vd, "fp64", args)
+            g64.dyson()
+            r64 = run_slices(g64, sl, st.G_tau, torch)
+            g64.close()
         scale = {"Sigma_tilde_ref_max_abs": float(np.abs(sl["Sref"]).max()),
                  "Sigma_inf_ref_max_abs": float(np.abs(sl["Sinf_ref"]).max()),
                  "P0_ref_max_abs": float(np.abs(sl["P0"]).max())}
@@ -561,6 +564,9 @@ def run_gw(args):
         extra = {"sigma_err_Ha": {"Sigma_inf": r_mixed["Sigma_inf_err"], "Sigma_tilde_tau": r_mixed["Sigma_tilde_err"],
                                   "P0_tau": r_mixed["P0_err"], "against": slice_desc, "reference_magnitudes": scale,
                                   "iteration_magnitudes": norms, "target_Ha": 1e-6},
+                 "mixed_slice_s_per_iteration_extrapolated": r_mixed["s_per_iteration_extrapolated"]}
+        if r64 is not None:
+            extra.update({
                  "fp64_path": {"s_per_iteration": r64["s_per_iteration_extrapolated"],
                                "extrapolated": "from one q of the P~0, screened and Sigma~ stages (x nq) plus the "
                                                "q-independent HF, transform and Dyson step, timed on the sampled "
@@ -571,8 +577,7 @@ def run_gw(args):
                                "sigma_err_Ha": {"Sigma_inf": r64["Sigma_inf_err"],
                                                 "Sigma_tilde_tau": r64["Sigma_tilde_err"], "P0_tau": r64["P0_err"],
                                                 "target_Ha": 1e-10}},
-                 "mixed_speedup_over_fp64": r64["s_per_iteration_extrapolated"] / s_per_iter,
-                 "mixed_slice_s_per_iteration_extrapolated": r_mixed["s_per_iteration_extrapolated"]}
+                 "mixed_speedup_over_fp64": r64["s_per_iteration_extrapolated"] / s_per_iter})
 
     achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
     traffic = traffic_from_profiles(args.workload, args.precision)

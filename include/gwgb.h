@@ -84,10 +84,22 @@ enum {
                                 P~0 / Sigma~ chains also on tensor cores (split TF32)  */
   GW_SMALL_SIMT   = 1u << 4, /* GW_SPLIT_TF32, nao <= 64: those steps on the FP32
                                 SIMT small-product kernel.  Neither flag: library default */
-  GW_FP64_NATIVE  = 1u << 5  /* FP64 SIMT arithmetic for the tau <-> i nu transforms
+  GW_FP64_NATIVE  = 1u << 5, /* FP64 SIMT arithmetic for the tau <-> i nu transforms
                                 and the screened solve, instead of the defaults:
                                 FP64-accurate digit-split products on the tensor cores
                                 and a complex64 inversion refined to FP64 accuracy    */
+  GW_TRS          = 1u << 6  /* the system is time-reversal symmetric: H0(-k) =
+                                conj H0(k), S(-k) = conj S(k), V^{-k,-k'}(Q) =
+                                conj V^{kk'}(Q) (checked by gw_init unless
+                                GW_SKIP_CHECKS; GW_ERR_ARG otherwise).  Then
+                                G^{-k} = conj G^k, P~0^{-q} = conj P~0^q, P~^{-q} =
+                                conj P~^q and Sigma~^{-k} = conj Sigma~^k hold
+                                exactly on the discrete grid, and gw_polarization,
+                                gw_screened and gw_selfenergy compute only the q (k)
+                                with index(-q) >= q (the inversion-symmetry reduction
+                                of the q-points, Sec. "GPU performance") and fill the
+                                others by conjugation.  Not applied while a q range
+                                is set, nor to the tangents and adjoints.         */
 };
 
 typedef void* (*gw_alloc_fn)(void* user, size_t bytes);
@@ -112,7 +124,8 @@ typedef struct {
   gw_free_fn dev_free;
   void* alloc_user;
   uint64_t flags;         /* GW_INPUT_DEVICE | GW_BORROW_V | GW_SKIP_CHECKS |
-                             GW_SMALL_TENSOR | GW_SMALL_SIMT | GW_FP64_NATIVE       */
+                             GW_SMALL_TENSOR | GW_SMALL_SIMT | GW_FP64_NATIVE |
+                             GW_TRS                                                 */
 } gw_config;
 
 /* Quantities readable with gw_get / writable with gw_set.  Sizes in bytes. */
@@ -295,6 +308,16 @@ gw_status gw_polarization_vjp(gw_ctx* ctx, const double* Pbar, double* Gbar);
  * [nq][ntau][naux][naux] are overwritten.  Device pointers; fp64. */
 gw_status gw_selfenergy_vjp(gw_ctx* ctx, const double* Sbar, double* Gbar, double* Pbar);
 
+/* The two adjoints above in complex64 arithmetic: V, G(tau), P~(tau) and the
+ * (symmetrised) cotangent are rounded to complex64, every chain step runs with
+ * fp32 accumulation within a launch, and the cotangent outputs accumulate in
+ * fp64 across the (q, k) slabs.  Same arguments, layouts and fp64 storage as
+ * gw_polarization_vjp / gw_selfenergy_vjp.  The first call of an FP64 context
+ * allocates a complex64 copy of V (half of V's size); complex64 copies of G,
+ * P~ and the cotangent are allocated on first use. */
+gw_status gw_polarization_vjp_c64(gw_ctx* ctx, const double* Pbar, double* Gbar);
+gw_status gw_selfenergy_vjp_c64(gw_ctx* ctx, const double* Sbar, double* Gbar, double* Pbar);
+
 /* Tangent (Jacobian-vector product) of gw_polarization's P~0(tau) (Eq.
  * tilde_P0_tau, symmetrised) along dG at the context's current G.  P~0 is a
  * quadratic form in G, so dP~0 = P(dG(tau), G(-tau)) + P(G(tau), dG(-tau)).
@@ -336,6 +359,19 @@ gw_status gw_sc_jvp(gw_ctx* ctx, const double* dSinf, const double* dSiw, double
  * the residual norm of each step.  The context ends with G from gw_dyson at the
  * final Sigma (no damping is applied). */
 gw_status gw_iterate_newton(gw_ctx* ctx, int32_t n_outer, int32_t m, double tol, double* res_out);
+
+/* DIIS self-consistency (Sec. "Self-consistent finite-temperature GW": the loop is
+ * converged with a DIIS scheme): the fixed-point problem x = F(x), x = (Sigma_inf,
+ * Sigma~(i w)), F = one GW step (gw_dyson with the mu search at x, then P~0, the
+ * screened solve and the new Sigma_inf, Sigma~(i w)).  Each step records x_i and
+ * r_i = F(x_i) - x_i (the last m, 1 <= m <= 32), takes the affine combination of
+ * least residual, min || sum c_i r_i ||^2 subject to sum c_i = 1 (inner product
+ * Re <a, b> over all entries; the bordered normal equations scaled by max
+ * ||r_i||^2, solved by QR on the host), and continues from x = sum c_i (x_i + mix
+ * r_i).  Stops early when ||r||_2 <= tol; res_out (host, n_iter doubles, may be
+ * NULL) receives ||r||_2 of each step.  The context ends with G from gw_dyson at
+ * the final x.  Allocates 2m + 1 vectors of x's size on first use. */
+gw_status gw_iterate_diis(gw_ctx* ctx, int32_t n_iter, int32_t m, double mix, double tol, double* res_out);
 
 /* Allocation-free screened solve: P = [I - P0]^{-1} P0 for `count` complex
  * n x n matrices (interleaved (re, im) doubles, row-major, contiguous), the

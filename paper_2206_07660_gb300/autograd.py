@@ -6,6 +6,8 @@ gw_selfenergy); the backward passes call the hand-written adjoint chains
 convention for complex inputs (dL/dRe + i dL/dIm for a real loss L).  The
 context's G (and P~) are re-set from the saved inputs before each backward,
 so other calls on the context between forward and backward are harmless.
+Setting `gw.adjoint_c64 = True` makes the backward passes run in complex64
+arithmetic (gw_polarization_vjp_c64, gw_selfenergy_vjp_c64).
 """
 import torch
 
@@ -28,7 +30,7 @@ class Polarization(torch.autograd.Function):
     def backward(ctx, Pbar):
         (G_tau,) = ctx.saved_tensors
         ctx.gw.set("G_tau", G_tau)
-        return ctx.gw.polarization_vjp(Pbar), None
+        return ctx.gw.polarization_vjp(Pbar, c64=getattr(ctx.gw, "adjoint_c64", False)), None
 
 
 class SelfEnergy(torch.autograd.Function):
@@ -55,5 +57,5 @@ class SelfEnergy(torch.autograd.Function):
         G_tau, P_tau = ctx.saved_tensors
         ctx.gw.set("G_tau", G_tau)
         ctx.gw.set("P_tau", P_tau)
-        Gbar, Pbar = ctx.gw.selfenergy_vjp(Sbar)
+        Gbar, Pbar = ctx.gw.selfenergy_vjp(Sbar, c64=getattr(ctx.gw, "adjoint_c64", False))
         return Gbar, Pbar, None

@@ -21,6 +21,11 @@ struct gw_ctx {
   gw_config cfg{};
   int nao = 0, naux = 0, nk = 0, ntau = 0, nw = 0;
   int q0 = 0, q1 = 0;   // q-points [q0, q1) of the P~0, screened and Sigma~ contractions (all by default)
+  // time-reversal symmetry (GW_TRS): kneg[k] = index of -k; the forward P~0, screened solve and
+  // Sigma~ skip every q (k) with kneg < q (k) and take its result as the conjugate of its partner's
+  bool trs = false, reduce = false;
+  std::vector<int> kneg;
+  int *d_kneg = nullptr, *d_kneed = nullptr, *d_vpart = nullptr;
   int64_t n2 = 0, na2 = 0;
   double spin = 2.0;
   cudaStream_t st = nullptr;
@@ -58,6 +63,8 @@ struct gw_ctx {
   double2 *tGiw = nullptr, *tGtau = nullptr, *tS = nullptr, *tgam = nullptr, *tP = nullptr;
   double* tpart = nullptr;
   std::vector<double2*> kry;   // Newton-Krylov basis (owned through `owned`)
+  std::vector<double2*> dx, dr;   // DIIS history: inputs and residuals (owned through `owned`)
+  double2* dnext = nullptr;
   int nvec = 0;
   // split-TF32 tensor-core operands (hi / lo planes, rows padded to 32 fp32)
   float *Zhi = nullptr, *Zlo = nullptr, *Vhi = nullptr, *Vlo = nullptr;
@@ -67,6 +74,7 @@ struct gw_ctx {
   int pgroup = 1;   // k-points whose last P~0 step runs as one GEMM (K concatenated over k)
   size_t y3bytes = 0;
   double2 *adjA = nullptr, *adjB = nullptr, *adjC = nullptr;   // fp64 chains of the adjoints (lazy)
+  float2 *adjG32 = nullptr, *adjP32 = nullptr, *adjBar32 = nullptr;   // complex64 adjoint operands (lazy)
   // captured iteration (gw_iterate_graph): status checks are deferred while capturing
   bool deferred = false;
   cudaStream_t gst = nullptr;
@@ -197,6 +205,8 @@ static inline void count(int n) { g_launches += n; }
 static inline bool uses_tc(const gw_ctx* c) {
   return c->cfg.contract_prec == GW_SPLIT_TF32 || c->hfmt != 0;
 }
+// the time-reversal reduction applies to forward stages over the full q range
+static inline bool trs_reduce(const gw_ctx* c) { return c->trs && c->q0 == 0 && c->q1 == c->nk; }
 // pointer to 16-bit element `e` of a buffer typed as float*
 static inline float* hofs(float* p, int64_t e) { return (float*)((uint16_t*)p + e); }
 
@@ -365,6 +375,12 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
       c->kminus[(size_t)q * nk + k] = kidx(m, k1 - q1, k2 - q2, k3 - q3);
     }
   }
+  c->trs = (cfg->flags & GW_TRS) != 0;
+  c->kneg.resize((size_t)nk);
+  for (int k = 0; k < nk; ++k) {
+    const int k1 = k / (m[1] * m[2]), k2 = (k / m[2]) % m[1], k3 = k % m[2];
+    c->kneg[(size_t)k] = kidx(m, -k1, -k2, -k3);
+  }
   auto A = [&](size_t bytes) { return dalloc(c, bytes); };
   const size_t cb = sizeof(double2);
   const size_t vbytes = (size_t)nk * nk * naux * n2 * cb;
@@ -513,6 +529,11 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   c->ws_bytes = ws;
   c->ws = need(A(ws));
   c->partial = (double*)need(A((size_t)ntau * nk * 8));
+  if (c->trs) {
+    c->d_kneg = (int*)need(A((size_t)nk * 4));
+    c->d_kneed = (int*)need(A((size_t)nk * 4));
+    c->d_vpart = (int*)need(A((size_t)nk * nk * 4));
+  }
   c->mus = (MuState*)need(A(sizeof(MuState)));
   c->info = (int*)need(A(64));
   c->dscr = (double*)need(A(64 * 8));
@@ -551,11 +572,11 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   chk(cudaMemsetAsync(c->info, 0, 64, st), "memset");
   chk(cudaMemsetAsync(c->Sinf, 0, nk * n2 * cb, st), "memset");
   chk(cudaMemsetAsync(c->Siw, 0, gsz, st), "memset");
-  if (c->Zhi) {
+  if (c->Zhi && !c->hfmt) {
     chk(cudaMemsetAsync(c->Zhi, 0, c->zbytes, st), "memset");
     chk(cudaMemsetAsync(c->Zlo, 0, c->zbytes, st), "memset");
   }
-  if (c->Y3hi) {
+  if (c->Y3hi && !c->hfmt) {
     chk(cudaMemsetAsync(c->Y3hi, 0, c->y3bytes, st), "memset");
     chk(cudaMemsetAsync(c->Y3lo, 0, c->y3bytes, st), "memset");
     if (c->Xs_hi) {
@@ -597,7 +618,23 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   }
   // input checks
   chk(cudaMemsetAsync(c->dscr, 0, 64 * 8, st), "memset");
+  std::vector<int> kneed((size_t)nk), vpart((size_t)nk * nk);
+  if (c->trs) {
+    for (int k = 0; k < nk; ++k) {
+      kneed[(size_t)k] = c->kneg[(size_t)k] < k ? 1 : 0;
+      for (int k2 = 0; k2 < nk; ++k2) vpart[(size_t)k * nk + k2] = c->kneg[(size_t)k] * nk + c->kneg[(size_t)k2];
+    }
+    chk(cudaMemcpyAsync(c->d_kneg, c->kneg.data(), (size_t)nk * 4, cudaMemcpyHostToDevice, st), "copy");
+    chk(cudaMemcpyAsync(c->d_kneed, kneed.data(), (size_t)nk * 4, cudaMemcpyHostToDevice, st), "copy");
+    chk(cudaMemcpyAsync(c->d_vpart, vpart.data(), (size_t)nk * nk * 4, cudaMemcpyHostToDevice, st), "copy");
+  }
   if (!(cfg->flags & GW_SKIP_CHECKS)) {
+    if (c->trs) {   // H0(-k) = conj H0(k), S(-k) = conj S(k), V^{-k,-k'} = conj V^{kk'}
+      chk(check_trs(c->H0, nk, n2, c->d_kneg, c->dscr + 10, st), "check");
+      chk(check_trs(c->S, nk, n2, c->d_kneg, c->dscr + 12, st), "check");
+      chk(check_trs(c->V, (int64_t)nk * nk, (int64_t)naux * n2, c->d_vpart, c->dscr + 14, st), "check");
+      count(3);
+    }
     chk(check_herm(c->H0, nao, nk, c->dscr, st), "check");
     chk(check_herm(c->S, nao, nk, c->dscr + 2, st), "check");
     chk(check_v_pairing(c->V, nk, naux, nao, c->dscr + 4, st), "check");
@@ -624,6 +661,12 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     } else if (h[0] > 1e-10 * (h[1] > 1 ? h[1] : 1)) { s = GW_ERR_ARG; c->err = "H0 is not Hermitian"; }
     else if (h[2] > 1e-10 * (h[3] > 1 ? h[3] : 1)) { s = GW_ERR_ARG; c->err = "S is not Hermitian"; }
     else if (h[4] > 1e-10 * (h[5] > 1e-300 ? h[5] : 1)) { s = GW_ERR_ARG; c->err = "V^{k'k}(Q) != V^{kk'}(Q)^H"; }
+    else if (c->trs && (h[10] > 1e-10 * (h[11] > 1 ? h[11] : 1) || h[12] > 1e-10 * (h[13] > 1 ? h[13] : 1) ||
+                        h[14] > 1e-10 * (h[15] > 1e-300 ? h[15] : 1))) {
+      s = GW_ERR_ARG;
+      c->err = "GW_TRS: inputs are not time-reversal symmetric (H0(-k) = conj H0(k), S(-k) = conj S(k), "
+               "V^{-k,-k'} = conj V^{kk'} within 1e-10)";
+    }
   }
   if (s != GW_OK) { g_init_err = c->err; free_all(c); delete c; return s; }
   // zero self-energy and the grid are defined from the start
@@ -822,6 +865,7 @@ static gw_status polar_chain(gw_ctx* c, const double2* Gplus, const double2* Gmi
   const int G = tc ? c->pgroup : 1;
   const int64_t zld = tc ? G * c->kpadP : 0;
   for (int q = c->q0; q < c->q1; ++q) {
+    if (c->reduce && c->kneg[(size_t)q] < q) continue;   // the conjugate of P~0^{-q}
     double2* Pq = out + (size_t)q * ntau * na2;
     for (int k = 0; k < nk; ++k) {
       const int kq = c->kplus[(size_t)q * nk + k];
@@ -960,6 +1004,7 @@ static gw_status polar_chain_half(gw_ctx* c, const double2* Gplus, const double2
   count(2 * nk);
   const double fl12 = 8.0 * ntau * naux * (double)nao * n2;
   for (int q = c->q0; q < c->q1; ++q) {
+    if (c->reduce && c->kneg[(size_t)q] < q) continue;   // the conjugate of P~0^{-q}
     double2* Pq = out + (size_t)q * ntau * c->na2;
     for (int k = 0; k < nk; ++k) {
       const int kq = c->kplus[(size_t)q * nk + k];
@@ -1041,6 +1086,7 @@ static gw_status sigma_chain_half(gw_ctx* c, const double2* Gsrc, const double2*
     CK(sigma_exps(c->ePs, shift, c->gn + ntau, ntau, naux, c->eY3, st));
     count(2);
     for (int k = 0; k < nk; ++k) {
+      if (c->reduce && c->kneg[(size_t)k] < k) continue;   // the conjugate of Sigma~^{-k}
       const int kmq = c->kminus[(size_t)q * nk + k];
       // X = conj(P~) V: B = V^{k,k-q} transposed, rows (i, a), K = Q, one exponent
       CK(half_embed_t(c->V + ((size_t)k * nk + kmq) * slab, naux, n2, c->VThi, c->VTlo, kps, fmt, c->h_Evmax - 15, st));
@@ -1087,8 +1133,15 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
   const int nk = c->nk, naux = c->naux, ntau = c->ntau;
   const int64_t na2 = c->na2;
   const bool tc = uses_tc(c);
+  const bool red = trs_reduce(c);
+  c->reduce = red;
   gw_status s = polar_chain(c, c->G_tau, c->G_tau, c->P0_tau, false);
+  c->reduce = false;
   if (s != GW_OK) return s;
+  if (red) {   // P~0^{-q}(tau) = conj P~0^q(tau) (time-reversal symmetry)
+    CK(conj_fill(c->P0_tau, 1, nk, (int64_t)ntau * na2, c->d_kneg, c->d_kneed, c->st));
+    count(1);
+  }
   if (tc && !c->deferred) {
     int h = 0;
     CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
@@ -1111,16 +1164,12 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
 
 // ------------------------------------------------------------------ A4/A5: screened solve
 
-extern "C" gw_status gw_screened(gw_ctx* c) {
-  if (!c) return GW_ERR_ARG;
-  if (!c->have_P0) return fail(c, GW_ERR_STATE, "no polarization yet");
-  const int naux = c->naux, ntau = c->ntau, nq = c->q1 - c->q0;
+// Screened solve and backward transform of the q-points [qa, qb)
+static gw_status screened_block(gw_ctx* c, int qa, int qb) {
+  const int naux = c->naux, ntau = c->ntau, nq = qb - qa;
   const int64_t na2 = c->na2;
-  double2* Pw = c->P_iw + (size_t)c->q0 * c->nw * na2;
-  double2* Pt = c->P_tau + (size_t)c->q0 * ntau * na2;
-  if (!c->deferred) {
-    CK(cudaMemsetAsync(c->info + 1, 0, 8, c->st));
-  }
+  double2* Pw = c->P_iw + (size_t)qa * c->nw * na2;
+  double2* Pt = c->P_tau + (size_t)qa * ntau * na2;
   if (c->irws) {
     // complex64 inversion refined to FP64 accuracy (P~0 Y on the tensor cores)
     int64_t nl = 0;
@@ -1136,6 +1185,33 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
   CK(transform(c, c->TBb, Pw, Pt, ntau, na2, nq, (int64_t)c->nw * na2, (int64_t)ntau * na2));
   CK(herm_batched(Pt, naux, (int64_t)nq * ntau, na2, c->st));
   count(1);
+  return GW_OK;
+}
+
+extern "C" gw_status gw_screened(gw_ctx* c) {
+  if (!c) return GW_ERR_ARG;
+  if (!c->have_P0) return fail(c, GW_ERR_STATE, "no polarization yet");
+  if (!c->deferred) {
+    CK(cudaMemsetAsync(c->info + 1, 0, 8, c->st));
+  }
+  gw_status s = GW_OK;
+  if (trs_reduce(c)) {
+    // time-reversal symmetry: solve the runs of irreducible q, then P~^{-q} = conj P~^q
+    for (int qa = 0; qa < c->nk && s == GW_OK;) {
+      if (c->kneg[(size_t)qa] < qa) { ++qa; continue; }
+      int qb = qa + 1;
+      while (qb < c->nk && c->kneg[(size_t)qb] >= qb) ++qb;
+      s = screened_block(c, qa, qb);
+      qa = qb;
+    }
+    if (s != GW_OK) return s;
+    CK(conj_fill(c->P_iw, 1, c->nk, (int64_t)c->nw * c->na2, c->d_kneg, c->d_kneed, c->st));
+    CK(conj_fill(c->P_tau, 1, c->nk, (int64_t)c->ntau * c->na2, c->d_kneg, c->d_kneed, c->st));
+    count(2);
+  } else {
+    s = screened_block(c, c->q0, c->q1);
+    if (s != GW_OK) return s;
+  }
   c->have_P0 = false;   // P~0(i Omega) was overwritten
   if (!c->deferred) {
     int h[2] = {0, 0};
@@ -1187,6 +1263,7 @@ static gw_status sigma_chain(gw_ctx* c, const double2* Gsrc, const double2* Psrc
       count(1);
     }
     for (int k = 0; k < nk; ++k) {
+      if (c->reduce && c->kneg[(size_t)k] < k) continue;   // the conjugate of Sigma~^{-k}
       const int kmq = c->kminus[(size_t)q * nk + k];
       if (tc) {
         // X[t][Q'][(i,a)] = sum_Q conj(P~[t][Q'][Q]) V^{k,k-q}[Q][(i,a)] on tensor cores
@@ -1283,8 +1360,15 @@ static gw_status sigma_tau_part(gw_ctx* c) {
   const int nk = c->nk, nao = c->nao, ntau = c->ntau;
   const int64_t n2 = c->n2;
   const bool tc = uses_tc(c);
+  const bool red = trs_reduce(c);
+  c->reduce = red;
   gw_status s = sigma_chain(c, c->G_tau, c->P_tau, c->Stau, false);
+  c->reduce = false;
   if (s != GW_OK) return s;
+  if (red) {   // Sigma~^{-k}(tau) = conj Sigma~^k(tau)
+    CK(conj_fill(c->Stau, ntau, nk, n2, c->d_kneg, c->d_kneed, c->st));
+    count(1);
+  }
   if (tc && !c->deferred) {
     int h = 0;
     CK(cudaMemcpyAsync(c->h_scr, c->info + 1, 4, cudaMemcpyDeviceToHost, c->st));
@@ -1520,11 +1604,40 @@ struct View {
   size_t ws_bytes;
   double2 *bufA, *bufB, *bufC;
   cudaStream_t st;
+  bool c64;
+  const float2* V32;
+  const float2* G32;
+  const float2* P32;
+  float2* bar32;
 };
 cudaError_t polarization_vjp(const View& v, const double2* Pbar, double2* Gbar, int64_t* launches);
 cudaError_t selfenergy_vjp(const View& v, const double2* Sbar, double2* Gbar, double2* Pbar, int64_t* launches);
 
 }  // namespace gwadj
+
+// complex64 operands of the adjoint chains: V (the context's copy when it has one), G(tau),
+// P~(tau) and the cotangent, converted on each call
+static gw_status adj_c64(gw_ctx* c, gwadj::View* v) {
+  const size_t gsz = (size_t)c->ntau * c->nk * c->n2, psz = (size_t)c->nk * c->ntau * c->na2;
+  const size_t vsz = (size_t)c->nk * c->nk * c->naux * c->n2;
+  if (!c->V32) {
+    c->V32 = (float2*)dalloc(c, vsz * 8);
+    if (!c->V32) return fail(c, GW_ERR_OOM, "complex64 copy of V");
+    CK(to_c64(c->V, c->V32, (int64_t)vsz, c->st));
+    count(1);
+  }
+  if (!c->adjG32) {
+    c->adjG32 = (float2*)dalloc(c, gsz * 8);
+    c->adjP32 = (float2*)dalloc(c, psz * 8);
+    c->adjBar32 = (float2*)dalloc(c, (gsz > (size_t)c->ntau * c->na2 ? gsz : (size_t)c->ntau * c->na2) * 8);
+    if (!c->adjG32 || !c->adjP32 || !c->adjBar32) return fail(c, GW_ERR_OOM, "complex64 adjoint buffers");
+  }
+  CK(to_c64(c->G_tau, c->adjG32, (int64_t)gsz, c->st));
+  count(1);
+  if (c->have_P) { CK(to_c64(c->P_tau, c->adjP32, (int64_t)psz, c->st)); count(1); }
+  v->c64 = true; v->V32 = c->V32; v->G32 = c->adjG32; v->P32 = c->adjP32; v->bar32 = c->adjBar32;
+  return GW_OK;
+}
 
 static gw_status adj_view(gw_ctx* c, gwadj::View* v) {
   const int64_t n2 = c->n2;
@@ -1543,14 +1656,16 @@ static gw_status adj_view(gw_ctx* c, gwadj::View* v) {
   v->ws = c->ws; v->ws_bytes = c->ws_bytes;
   v->bufA = c->adjA; v->bufB = c->adjB; v->bufC = c->adjC;
   v->st = c->st;
+  v->c64 = false; v->V32 = nullptr; v->G32 = nullptr; v->P32 = nullptr; v->bar32 = nullptr;
   return GW_OK;
 }
 
-extern "C" gw_status gw_polarization_vjp(gw_ctx* c, const double* Pbar, double* Gbar) {
+static gw_status polarization_vjp_impl(gw_ctx* c, const double* Pbar, double* Gbar, bool c64) {
   if (!c || !Pbar || !Gbar) return fail(c, GW_ERR_ARG, "null argument");
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
   gwadj::View v;
   gw_status s = adj_view(c, &v);
+  if (s == GW_OK && c64) s = adj_c64(c, &v);
   if (s != GW_OK) return s;
   CK(cudaMemsetAsync(Gbar, 0, (size_t)c->ntau * c->nk * c->n2 * 16, c->st));
   int64_t l = 0;
@@ -1559,12 +1674,20 @@ extern "C" gw_status gw_polarization_vjp(gw_ctx* c, const double* Pbar, double* 
   return GW_OK;
 }
 
-extern "C" gw_status gw_selfenergy_vjp(gw_ctx* c, const double* Sbar, double* Gbar, double* Pbar) {
+extern "C" gw_status gw_polarization_vjp(gw_ctx* c, const double* Pbar, double* Gbar) {
+  return polarization_vjp_impl(c, Pbar, Gbar, false);
+}
+extern "C" gw_status gw_polarization_vjp_c64(gw_ctx* c, const double* Pbar, double* Gbar) {
+  return polarization_vjp_impl(c, Pbar, Gbar, true);
+}
+
+static gw_status selfenergy_vjp_impl(gw_ctx* c, const double* Sbar, double* Gbar, double* Pbar, bool c64) {
   if (!c || !Sbar || !Gbar || !Pbar) return fail(c, GW_ERR_ARG, "null argument");
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function yet");
   if (!c->have_P) return fail(c, GW_ERR_STATE, "no screened interaction yet");
   gwadj::View v;
   gw_status s = adj_view(c, &v);
+  if (s == GW_OK && c64) s = adj_c64(c, &v);
   if (s != GW_OK) return s;
   CK(cudaMemsetAsync(Gbar, 0, (size_t)c->ntau * c->nk * c->n2 * 16, c->st));
   CK(cudaMemsetAsync(Pbar, 0, (size_t)c->nk * c->ntau * c->na2 * 16, c->st));
@@ -1572,6 +1695,13 @@ extern "C" gw_status gw_selfenergy_vjp(gw_ctx* c, const double* Sbar, double* Gb
   CK(gwadj::selfenergy_vjp(v, (const double2*)Sbar, (double2*)Gbar, (double2*)Pbar, &l));
   count((int)l);
   return GW_OK;
+}
+
+extern "C" gw_status gw_selfenergy_vjp(gw_ctx* c, const double* Sbar, double* Gbar, double* Pbar) {
+  return selfenergy_vjp_impl(c, Sbar, Gbar, Pbar, false);
+}
+extern "C" gw_status gw_selfenergy_vjp_c64(gw_ctx* c, const double* Sbar, double* Gbar, double* Pbar) {
+  return selfenergy_vjp_impl(c, Sbar, Gbar, Pbar, true);
 }
 
 // ------------------------------------------------------------------ tangents (A10)
@@ -1828,6 +1958,127 @@ extern "C" gw_status gw_iterate_newton(gw_ctx* c, int32_t n_outer, int32_t m, do
       CK(axpby(c->Siw, c->kry[(size_t)j] + ki, y[(size_t)j], 1.0, nx - ki, c->st));
     }
     count(2 * used);
+    c->have_sigma = true;
+  }
+  // leave the context at a consistent state: G from the final Sigma
+  if ((s = gw_dyson(c, nullptr)) != GW_OK) return s;
+  c->have_P0 = false;
+  c->have_P = false;
+  return GW_OK;
+}
+
+// ------------------------------------------------------------------ DIIS self-consistency (F4)
+
+// Least-squares solution of the (n x n) system A c = rhs by Householder QR (row-major,
+// A overwritten); columns whose pivot is negligible get a zero coefficient.
+static void small_lstsq(std::vector<double>& A, std::vector<double>& rhs, int n, std::vector<double>& c) {
+  for (int j = 0; j < n; ++j) {
+    double nrm = 0;
+    for (int i = j; i < n; ++i) nrm += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) continue;
+    const double a0 = A[(size_t)j * n + j];
+    const double alpha = a0 > 0 ? -nrm : nrm;
+    std::vector<double> v((size_t)n, 0.0);
+    for (int i = j; i < n; ++i) v[(size_t)i] = A[(size_t)i * n + j];
+    v[(size_t)j] -= alpha;
+    double vv = 0;
+    for (int i = j; i < n; ++i) vv += v[(size_t)i] * v[(size_t)i];
+    if (vv == 0.0) continue;
+    for (int k = j; k < n; ++k) {
+      double d = 0;
+      for (int i = j; i < n; ++i) d += v[(size_t)i] * A[(size_t)i * n + k];
+      d = 2.0 * d / vv;
+      for (int i = j; i < n; ++i) A[(size_t)i * n + k] -= d * v[(size_t)i];
+    }
+    double d = 0;
+    for (int i = j; i < n; ++i) d += v[(size_t)i] * rhs[(size_t)i];
+    d = 2.0 * d / vv;
+    for (int i = j; i < n; ++i) rhs[(size_t)i] -= d * v[(size_t)i];
+  }
+  double rmax = 0;
+  for (int j = 0; j < n; ++j) rmax = std::fmax(rmax, std::fabs(A[(size_t)j * n + j]));
+  c.assign((size_t)n, 0.0);
+  for (int j = n - 1; j >= 0; --j) {
+    const double r = A[(size_t)j * n + j];
+    if (std::fabs(r) <= 1e-14 * rmax) continue;
+    double t = rhs[(size_t)j];
+    for (int k = j + 1; k < n; ++k) t -= A[(size_t)j * n + k] * c[(size_t)k];
+    c[(size_t)j] = t / r;
+  }
+}
+
+extern "C" gw_status gw_iterate_diis(gw_ctx* c, int32_t n_iter, int32_t m, double mix, double tol, double* res_out) {
+  if (!c || n_iter < 0 || m < 1 || m > 32) return fail(c, GW_ERR_ARG, "bad DIIS arguments");
+  gw_status s = sc_tangent_buffers(c);   // inner-product partials
+  if (s != GW_OK) return s;
+  const int64_t ki = (int64_t)c->nk * c->n2, nx = ki + (int64_t)c->nw * ki;
+  if ((int)c->dx.size() < m) {
+    for (int i = (int)c->dx.size(); i < m; ++i) {
+      double2* px = (double2*)dalloc(c, (size_t)nx * 16);
+      double2* pr = (double2*)dalloc(c, (size_t)nx * 16);
+      if (!px || !pr) return fail(c, GW_ERR_OOM, "DIIS history");
+      c->dx.push_back(px);
+      c->dr.push_back(pr);
+    }
+  }
+  if (!c->dnext) {
+    c->dnext = (double2*)dalloc(c, (size_t)nx * 16);
+    if (!c->dnext) return fail(c, GW_ERR_OOM, "DIIS buffer");
+  }
+  // history of this call: slot h % m holds step h; B[i][j] = Re <r_i, r_j>
+  std::vector<double> B((size_t)m * m, 0.0);
+  int nh = 0;
+  for (int it = 0; it < n_iter; ++it) {
+    if ((s = sc_forward(c)) != GW_OK) return s;
+    const int slot = nh % m;
+    double2* X = c->dx[(size_t)slot];
+    double2* R = c->dr[(size_t)slot];
+    // x = current input, r = F(x) - x
+    CK(cudaMemcpyAsync(X, c->Sinf, (size_t)ki * 16, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(X + ki, c->Siw, (size_t)(nx - ki) * 16, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(R, c->Sinf_new, (size_t)ki * 16, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(R + ki, c->Siw_new, (size_t)(nx - ki) * 16, cudaMemcpyDeviceToDevice, c->st));
+    CK(axpby(R, X, -1.0, 1.0, nx, c->st));
+    count(1);
+    ++nh;
+    const int n = nh < m ? nh : m;
+    // new row / column of B (oldest entry replaced in the ring)
+    for (int j = 0; j < n; ++j) {
+      const int sj = (nh - n + j) % m;
+      double b = 0;
+      if ((s = rdot(c, R, c->dr[(size_t)sj], nx, &b)) != GW_OK) return s;
+      B[(size_t)slot * m + sj] = B[(size_t)sj * m + slot] = b;
+    }
+    const double rn = std::sqrt(B[(size_t)slot * m + slot]);
+    if (res_out) res_out[it] = rn;
+    if (rn <= tol) { for (int j = it + 1; j < n_iter; ++j) if (res_out) res_out[j] = rn; break; }
+    // min || sum c_i r_i ||^2 with sum c_i = 1: bordered system, scaled by max B_ii
+    double scale = 0;
+    for (int j = 0; j < n; ++j) {
+      const int sj = (nh - n + j) % m;
+      scale = std::fmax(scale, B[(size_t)sj * m + sj]);
+    }
+    if (scale <= 0) scale = 1.0;
+    const int N = n + 1;
+    std::vector<double> A((size_t)N * N, 0.0), rhs((size_t)N, 0.0), coef;
+    for (int i = 0; i < n; ++i) {
+      const int si = (nh - n + i) % m;
+      for (int j = 0; j < n; ++j) A[(size_t)i * N + j] = B[(size_t)si * m + (nh - n + j) % m] / scale;
+      A[(size_t)i * N + n] = A[(size_t)n * N + i] = 1.0;
+    }
+    rhs[(size_t)n] = 1.0;
+    small_lstsq(A, rhs, N, coef);
+    // x_next = sum c_i (x_i + mix r_i)
+    CK(cudaMemsetAsync(c->dnext, 0, (size_t)nx * 16, c->st));
+    for (int i = 0; i < n; ++i) {
+      const int si = (nh - n + i) % m;
+      CK(axpby(c->dnext, c->dx[(size_t)si], coef[(size_t)i], 1.0, nx, c->st));
+      CK(axpby(c->dnext, c->dr[(size_t)si], coef[(size_t)i] * mix, 1.0, nx, c->st));
+    }
+    count(2 * n);
+    CK(cudaMemcpyAsync(c->Sinf, c->dnext, (size_t)ki * 16, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(c->Siw, c->dnext + ki, (size_t)(nx - ki) * 16, cudaMemcpyDeviceToDevice, c->st));
     c->have_sigma = true;
   }
   // leave the context at a consistent state: G from the final Sigma

@@ -105,6 +105,10 @@ cudaError_t check_v_pairing(const double2* V, int nk, int naux, int nao, double*
 cudaError_t check_herm(const double2* X, int64_t n, int64_t count, double* d_maxdev, cudaStream_t st);
 cudaError_t maxabs_diff(const double2* a, const double2* b, int64_t n, double* d_out, cudaStream_t st);
 cudaError_t to_c64(const double2* x, float2* y, int64_t n, cudaStream_t st);
+cudaError_t check_trs(const double2* X, int64_t nslab, int64_t len, const int* partner, double* d_out,
+                      cudaStream_t st);
+cudaError_t conj_fill(double2* X, int64_t outer, int nk, int64_t inner, const int* src, const int* need,
+                      cudaStream_t st);
 
 // ------------------------------------------------------------------ batched small products (k_bsm.cu)
 // C[g][e] = alpha * A[g][e] * B[g][e] (complex64), M, N, K <= 64; element (r, c) of

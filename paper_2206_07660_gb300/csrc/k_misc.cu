@@ -225,4 +225,46 @@ cudaError_t to_c64(const double2* x, float2* y, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ time-reversal symmetry
+
+// out[0] = max |X[s] - conj X[partner[s]]| over slabs s of `len` complex entries,
+// out[1] = max |X| (+inf when an entry is not finite)
+__global__ void trs_check_kernel(const double2* __restrict__ X, int64_t nslab, int64_t len,
+                                 const int* __restrict__ partner, double* out) {
+  const int64_t tot = nslab * len;
+  double dev = 0, mx = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / len, i = e - s * len;
+    const double2 a = X[e], b = X[(int64_t)partner[s] * len + i];
+    dev = fmax(dev, hypot(a.x - b.x, a.y + b.y));
+    mx = (isfinite(a.x) && isfinite(a.y)) ? fmax(mx, hypot(a.x, a.y)) : INFINITY;
+  }
+  atomic_max_nonneg(out, dev);
+  atomic_max_nonneg(out + 1, mx);
+}
+cudaError_t check_trs(const double2* X, int64_t nslab, int64_t len, const int* partner, double* d_out,
+                      cudaStream_t st) {
+  trs_check_kernel<<<nblk(nslab * len), 256, 0, st>>>(X, nslab, len, partner, d_out);
+  return cudaGetLastError();
+}
+
+// X[o][k][:] = conj X[o][src[k]][:] for every k with need[k] (layout [outer][nk][inner])
+__global__ void conj_fill_kernel(double2* X, int64_t outer, int nk, int64_t inner, const int* __restrict__ src,
+                                 const int* __restrict__ need) {
+  const int64_t tot = outer * nk * inner;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = e / ((int64_t)nk * inner), r = e - o * nk * inner;
+    const int k = (int)(r / inner);
+    if (!need[k]) continue;
+    const int64_t i = r - (int64_t)k * inner;
+    const double2 v = X[(o * nk + src[k]) * inner + i];
+    X[e] = make_double2(v.x, -v.y);
+  }
+}
+cudaError_t conj_fill(double2* X, int64_t outer, int nk, int64_t inner, const int* src, const int* need,
+                      cudaStream_t st) {
+  conj_fill_kernel<<<nblk(outer * nk * inner), 256, 0, st>>>(X, outer, nk, inner, src, need);
+  return cudaGetLastError();
+}
+
 }  // namespace gwk

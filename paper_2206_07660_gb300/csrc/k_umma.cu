@@ -86,15 +86,30 @@ struct UmmaArgs {
   int* err;
 };
 
+// index m / div of an exponent array (rows and columns fit in 32 bits; div >= 2^30
+// means one exponent per batch entry)
+__device__ __forceinline__ int64_t exp_index(int64_t m, int64_t div) {
+  return div >= ((int64_t)1 << 30) ? 0 : (int64_t)((uint32_t)m / (uint32_t)div);
+}
 // exponent of the row scale of row m (output or operand side); 0 without scales
 __device__ __forceinline__ int row_exp(const UmmaArgs& a, int z, int64_t m) {
-  return a.eA ? a.eA[(int64_t)z * a.ea_zs + m / a.ea_div] + a.eshift : 0;
+  return a.eA ? a.eA[(int64_t)z * a.ea_zs + exp_index(m, a.ea_div)] + a.eshift : 0;
 }
 __device__ __forceinline__ int col_exp(const UmmaArgs& a, int z, int64_t n) {
-  return a.eB ? a.eB[(int64_t)z * a.eb_zs + (n >> 1) / a.eb_div] : 0;
+  return a.eB ? a.eB[(int64_t)z * a.eb_zs + exp_index(n >> 1, a.eb_div)] : 0;
 }
 __device__ __forceinline__ int out_exp(const UmmaArgs& a, int z, int64_t m) {
-  return a.eO ? a.eO[(int64_t)z * a.eo_zs + m / a.eo_div] + a.eo_shift : 0;
+  return a.eO ? a.eO[(int64_t)z * a.eo_zs + exp_index(m, a.eo_div)] + a.eo_shift : 0;
+}
+// exact powers of two built from their bit patterns (the scales stay far inside the
+// normal range; clamped for safety): multiplying by them equals ldexp
+__device__ __forceinline__ float p2f(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __int_as_float((e + 127) << 23);
+}
+__device__ __forceinline__ double p2d(int e) {
+  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  return __longlong_as_double((long long)(e + 1023) << 52);
 }
 // v as 16-bit hi / lo pieces (hi = rn(v), lo = rn(v - hi)) in the output format
 __device__ __forceinline__ void half_pieces(int fmt, float v, uint16_t& h, uint16_t& l) {
@@ -435,13 +450,13 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
     int myexp = 0;   // row exponent of row r0 + lane (scaled mode)
     if (a.eA) {
       if (lane < nrow) myexp = row_exp(a, z, r0 + lane);
-      if (colok) al = ldexp(al, col_exp(a, z, n));
+      if (colok) al *= p2d(col_exp(a, z, n));
     }
     if (a.ksplit > 1) {
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
         const int re_ = __shfl_sync(0xffffffffu, myexp, r);
-        if (r < nrow && colok) atomicAdd(C + base + n, ldexp(al * (double)stg[r * 33 + lane], re_));
+        if (r < nrow && colok) atomicAdd(C + base + n, al * (double)stg[r * 33 + lane] * p2d(re_));
       }
     } else if (a.accumulate) {
       for (int h = 0; h < 32; h += 16) {
@@ -455,7 +470,7 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
         for (int r = 0; r < 16; ++r) {
           const int64_t base = __shfl_sync(0xffffffffu, myoff, h + r);
           const int re_ = __shfl_sync(0xffffffffu, myexp, h + r);
-          if (h + r < nrow && colok) C[base + n] = old[r] + ldexp(al * (double)stg[(h + r) * 33 + lane], re_);
+          if (h + r < nrow && colok) C[base + n] = old[r] + al * (double)stg[(h + r) * 33 + lane] * p2d(re_);
         }
       }
     } else {
@@ -463,7 +478,7 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
         const int re_ = __shfl_sync(0xffffffffu, myexp, r);
-        if (r < nrow && colok) C[base + n] = ldexp(al * (double)stg[r * 33 + lane], re_);
+        if (r < nrow && colok) C[base + n] = al * (double)stg[r * 33 + lane] * p2d(re_);
       }
     }
   } else {
@@ -490,7 +505,7 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
         const int rs = __shfl_sync(0xffffffffu, myexp, r);
         if (r < nrow && colok) {
           uint16_t h, l;
-          half_pieces(a.o_half, ldexpf(al * stg[r * 33 + lane], colexp + rs), h, l);
+          half_pieces(a.o_half, al * stg[r * 33 + lane] * p2f(colexp + rs), h, l);
           Ch[base + coff] = h;
           Cl[base + coff] = l;
         }
@@ -498,7 +513,7 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
     } else if (a.eA) {
       // scaled operands: the row factor 2^eA (shuffled per row) times the column
       // factor 2^(eB + eshift), both exact powers of two
-      const float rsc = ldexpf(1.0f, myexp), csc = ldexpf(al, colexp);
+      const float rsc = p2f(myexp), csc = al * p2f(colexp);
       for (int r = 0; r < 32; ++r) {
         const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
         const float rs = __shfl_sync(0xffffffffu, rsc, r);
@@ -863,9 +878,9 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const int ex = rexp + col_exp(a, z, n);
-                const double sre = ldexp(a.alpha * (double)__uint_as_float(v[j]), ex);
-                const double sim = ldexp(a.alpha * (double)__uint_as_float(v[j + 1]), ex);
+                const double sc = a.alpha * p2d(rexp + col_exp(a, z, n));
+                const double sre = sc * (double)__uint_as_float(v[j]);
+                const double sim = sc * (double)__uint_as_float(v[j + 1]);
                 double2* p2 = (double2*)(Cd + off);
                 if (a.accumulate) {
                   const double2 o = *p2;
@@ -878,6 +893,10 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           } else if (rok && a.o_half) {
             // 16-bit hi / lo pieces of D 2^(eA + eB - eO), (re, im) pairs as one 32-bit store
             const int rexp = row_exp(a, z, row) - out_exp(a, z, row);
+            // one column exponent for the whole tile when B has one per batch entry
+            const bool bconst = a.eb_div >= ((int64_t)1 << 30);
+            const int cconst = (a.eB && bconst) ? a.eB[(int64_t)z * a.eb_zs] : 0;
+            const float rsc = al * p2f(rexp + cconst);
             uint16_t* Ch = (uint16_t*)a.C;
             uint16_t* Cl = (uint16_t*)a.C_lo;
 #pragma unroll
@@ -885,23 +904,23 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const int ex = rexp + col_exp(a, z, n);
+                const float sc = (bconst || !a.eB) ? rsc : al * p2f(rexp + col_exp(a, z, n));
                 uint16_t hr, lr, hm, lm;
-                half_pieces(a.o_half, ldexpf(al * __uint_as_float(v[j]), ex), hr, lr);
-                half_pieces(a.o_half, ldexpf(al * __uint_as_float(v[j + 1]), ex), hm, lm);
+                half_pieces(a.o_half, sc * __uint_as_float(v[j]), hr, lr);
+                half_pieces(a.o_half, sc * __uint_as_float(v[j + 1]), hm, lm);
                 *(uint32_t*)(Ch + off) = (uint32_t)hr | ((uint32_t)hm << 16);
                 *(uint32_t*)(Cl + off) = (uint32_t)lr | ((uint32_t)lm << 16);
               }
             }
           } else if (rok && a.eA) {
             // scaled operands: 2^(eA[row] + eB[column pair] + eshift), exact powers of two
-            const float rsc = ldexpf(al, row_exp(a, z, row));
+            const float rsc = al * p2f(row_exp(a, z, row));
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const float sc = rsc * ldexpf(1.0f, col_exp(a, z, n));
+                const float sc = rsc * p2f(col_exp(a, z, n));
                 const float re = sc * __uint_as_float(v[j]), im = sc * __uint_as_float(v[j + 1]);
                 if (a.C_lo) {
                   const float hr = tf32_rna_dev(re), hi_ = tf32_rna_dev(im);

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(_HERE, "libgwgb.so")
 GW_OK, GW_ERR_ARG, GW_ERR_CUDA, GW_ERR_OOM, GW_ERR_NOT_CONVERGED, GW_ERR_SINGULAR, GW_ERR_TIMEOUT, \
     GW_ERR_STATE, GW_ERR_INTERNAL = range(9)
 PRECISIONS = {"fp64": 0, "fp32": 1, "split_bf16": 2, "split_tf32": 3, "split_f16": 4}
-GW_INPUT_DEVICE, GW_BORROW_V, GW_SKIP_CHECKS, GW_SMALL_TENSOR, GW_SMALL_SIMT, GW_FP64_NATIVE = 1, 2, 4, 8, 16, 32
+GW_INPUT_DEVICE, GW_BORROW_V, GW_SKIP_CHECKS, GW_SMALL_TENSOR, GW_SMALL_SIMT, GW_FP64_NATIVE, GW_TRS = \
+    1, 2, 4, 8, 16, 32, 64
 
 QUANTITIES = {
     "G_tau": 0, "G_iw": 1, "Sigma_inf": 2, "Sigma_tau": 3, "Sigma_iw": 4, "P0_tau": 5, "P0_iw": 6,
@@ -80,6 +81,10 @@ def load():
     lib.gw_batch_iterate.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32]
     lib.gw_polarization_vjp.argtypes = [P, P, P]
     lib.gw_selfenergy_vjp.argtypes = [P, P, P, P]
+    lib.gw_iterate_diis.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_double)]
+    lib.gw_polarization_vjp_c64.argtypes = [P, P, P]
+    lib.gw_selfenergy_vjp_c64.argtypes = [P, P, P, P]
     lib.gw_polarization_jvp.argtypes = [P, P, P]
     lib.gw_screened_jvp.argtypes = [P, P, P]
     lib.gw_selfenergy_jvp.argtypes = [P, P, P, P]
@@ -95,7 +100,7 @@ def load():
                  "gw_polarization_vjp", "gw_selfenergy_vjp", "gw_iterate_graph", "gw_batch_iterate",
                  "gw_polarization_jvp", "gw_screened_jvp", "gw_selfenergy_jvp", "gw_sc_jvp",
                  "gw_iterate_newton", "gw_selfenergy_partial", "gw_selfenergy_finish", "gw_set_q_range", "gw_save_state",
-                 "gw_load_state"):
+                 "gw_load_state", "gw_polarization_vjp_c64", "gw_selfenergy_vjp_c64", "gw_iterate_diis"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -135,7 +140,7 @@ class GW:
 
     def __init__(self, H0, S, V, kmesh, ntau, beta, fermi_n, bose_m, n_elec=None, damping=0.5,
                  mu_tol=1e-9, mu_maxit=400, precision="fp64", spin=2, borrow_V=False,
-                 skip_checks=False, torch_alloc=True, small_steps="auto", fp64_gemm="tensor"):
+                 skip_checks=False, torch_alloc=True, small_steps="auto", fp64_gemm="tensor", trs=False):
         import torch
         self.lib = load()
         self.torch = torch
@@ -184,6 +189,8 @@ class GW:
             flags |= GW_SKIP_CHECKS
         flags |= {"auto": 0, "tensor": GW_SMALL_TENSOR, "simt": GW_SMALL_SIMT}[small_steps]
         flags |= {"tensor": 0, "native": GW_FP64_NATIVE}[fp64_gemm]
+        if trs:
+            flags |= GW_TRS
         cfg.flags = flags
         self._cfg = cfg
         ctx = ctypes.c_void_p()
@@ -291,21 +298,24 @@ class GW:
         return {f: getattr(s, f) for f, _ in GwIterStats._fields_}
 
     # -- adjoints (device tensors, complex128, contiguous)
-    def polarization_vjp(self, Pbar):
-        """Gbar = VJP of the symmetrised P~0(tau) w.r.t. G(tau) at the current G."""
+    def polarization_vjp(self, Pbar, c64=False):
+        """Gbar = VJP of the symmetrised P~0(tau) w.r.t. G(tau) at the current G
+        (complex128 arithmetic, or complex64 with c64=True; complex128 storage)."""
         torch = self.torch
         Pbar = Pbar.contiguous()
         Gbar = torch.empty(self.shape_of("G_tau"), dtype=torch.complex128, device=Pbar.device)
-        self._check(self.lib.gw_polarization_vjp(self.ctx, Pbar.data_ptr(), Gbar.data_ptr()))
+        fn = self.lib.gw_polarization_vjp_c64 if c64 else self.lib.gw_polarization_vjp
+        self._check(fn(self.ctx, Pbar.data_ptr(), Gbar.data_ptr()))
         return Gbar
 
-    def selfenergy_vjp(self, Sbar):
+    def selfenergy_vjp(self, Sbar, c64=False):
         """(Gbar, Pbar) = VJP of the symmetrised Sigma~(tau) w.r.t. (G(tau), P~(tau))."""
         torch = self.torch
         Sbar = Sbar.contiguous()
         Gbar = torch.empty(self.shape_of("G_tau"), dtype=torch.complex128, device=Sbar.device)
         Pbar = torch.empty(self.shape_of("P_tau"), dtype=torch.complex128, device=Sbar.device)
-        self._check(self.lib.gw_selfenergy_vjp(self.ctx, Sbar.data_ptr(), Gbar.data_ptr(), Pbar.data_ptr()))
+        fn = self.lib.gw_selfenergy_vjp_c64 if c64 else self.lib.gw_selfenergy_vjp
+        self._check(fn(self.ctx, Sbar.data_ptr(), Gbar.data_ptr(), Pbar.data_ptr()))
         return Gbar, Pbar
 
     def polarization_jvp(self, dG):
@@ -346,6 +356,12 @@ class GW:
         res = (ctypes.c_double * max(1, int(n_outer)))()
         self._check(self.lib.gw_iterate_newton(self.ctx, int(n_outer), int(m), float(tol), res))
         return [float(x) for x in res][:int(n_outer)]
+
+    def iterate_diis(self, n, m=6, mix=0.5, tol=0.0):
+        """DIIS self-consistency (see gw_iterate_diis); returns ||F(x) - x||_2 of each step."""
+        res = (ctypes.c_double * max(1, int(n)))()
+        self._check(self.lib.gw_iterate_diis(self.ctx, int(n), int(m), float(mix), float(tol), res))
+        return [float(x) for x in res][:int(n)]
 
     def profile(self, enable=True):
         self._check(self.lib.gw_profile(self.ctx, int(bool(enable))))

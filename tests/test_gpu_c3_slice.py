@@ -11,7 +11,8 @@ can evaluate in seconds:
 
 The GPU computes with the same per-(q, k) GEMM shapes and launches as a full
 iteration (the context is restricted to the q block of the slice).  Targets:
-mixed path 1e-6 Ha, FP64 path 1e-10 Ha.
+Sigma~ within 1e-6 Ha (mixed) and 1e-10 Ha (FP64); P~0 (dimensionless) within
+3e-6 and 1e-12 of its largest entry.
 """
 import numpy as np
 import pytest
@@ -23,6 +24,8 @@ from synth import LazyV, device_V, make_config_system
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TOL_HA = {"split_tf32": 1e-6, "split_f16": 1e-6, "fp64": 1e-10}
+# P~0 is dimensionless (P~ = V P V, W~ = (1 - P~)^-1 P~): relative to its largest entry
+TOL_P_REL = {"split_tf32": 3e-6, "split_f16": 3e-6, "fp64": 1e-12}
 Q = 16          # q = (1, 0, 0) on the 4x4x4 mesh
 K0 = 5
 KS = 9          # Sigma~ row
@@ -71,7 +74,7 @@ def test_c3_polarization_two_pairs(c3, precision):
     g.close()
     err = np.abs(got - P0).max()
     assert np.abs(P0).max() > 1e-6
-    assert err < TOL_HA[precision], (err, np.abs(P0).max())
+    assert err < TOL_P_REL[precision] * np.abs(P0).max(), (err, np.abs(P0).max())
 
 
 @pytest.mark.parametrize("precision", ["split_tf32", "split_f16", "fp64"])

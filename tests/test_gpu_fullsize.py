@@ -9,8 +9,9 @@ in absolute units, on outputs the oracle computes on its own in seconds:
   workload's own magnitude: the oracle's screened P~^q(tau) of one q, used for
   every q.
 
-Targets: the mixed path (split-TF32 tensor-core contractions) within 1e-6 Ha of
-the FP64 oracle, the FP64 path within 1e-10 Ha.  Every input is seeded or
+Targets: Sigma~ of the mixed path (split tensor-core contractions) within 1e-6 Ha
+of the FP64 oracle, of the FP64 path within 1e-10 Ha; P~0 (dimensionless) within
+3e-6 (mixed) and 1e-12 (FP64) of its largest entry.  Every input is seeded or
 computed by the oracle; nothing comes from the CUDA path.
 """
 import numpy as np
@@ -23,6 +24,8 @@ from synth import make_config_system
 pytestmark = pytest.mark.gpu
 
 TOL_HA = {"split_tf32": 1e-6, "split_f16": 1e-6, "fp64": 1e-10}
+# P~0 is dimensionless (P~ = V P V, W~ = (1 - P~)^-1 P~): relative to its largest entry
+TOL_P_REL = {"split_tf32": 3e-6, "split_f16": 3e-6, "fp64": 1e-12}
 Q_SLICE, K_SLICE = 5, 13
 
 
@@ -48,7 +51,7 @@ def test_c2_polarization_one_q(c2, precision):
     got = g.get("P0_tau")[Q_SLICE]
     g.close()
     err = np.abs(got - ref).max()
-    assert err < TOL_HA[precision], (err, np.abs(ref).max())
+    assert err < TOL_P_REL[precision] * np.abs(ref).max(), (err, np.abs(ref).max())
 
 
 def test_c2_screened_all(c2):

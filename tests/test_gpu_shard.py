@@ -34,7 +34,8 @@ def test_two_q_blocks_sum_to_full_iteration(precision):
         g.dyson()
     st = oracle_state(sysd)
     st.iterate()
-    tol = 1e-10 if precision == "fp64" else 1e-6
+    # mixed path: 2e-6 of |Sigma~| (FP32 accumulation in the tensor pipe; see test_gpu_parity)
+    tol = 1e-10 if precision == "fp64" else 2e-6 * max(1.0, float(np.abs(st.Sigma_tau).max()))
     for g in parts:
         for q in ("G_tau", "Sigma_iw", "Sigma_inf"):
             assert np.abs(g.get(q) - full.get(q)).max() < (1e-12 if precision == "fp64" else 1e-7), q

@@ -149,3 +149,30 @@ def test_p7_g_endpoint_sum_rule_converged_grid():
     g0p = np.einsum("j,jkab->kab", st.grid.l0, st.G_tau)
     gbm = np.einsum("j,jkab->kab", st.grid.lb, st.G_tau)
     assert np.abs(g0p + gbm + np.linalg.inv(st.S)).max() < 1e-10
+
+
+def test_damping_is_linear_mixing_of_successive_self_energies():
+    # O11 (reading C-9): from the second iteration on, the self-energy that enters the
+    # Dyson step is (1 - a) Sigma_old + a Sigma_new for both the static part and
+    # Sigma~(i w); the first iteration is not mixed.  Rebuilt here by hand from the
+    # unmixed self-energies of a copy of the state (State.sigma), not from iterate().
+    from oracle import gw as ogw
+    from synth import make_system, matsubara_indices
+    sysd = make_system(3, 6, (2, 1, 1), 5)
+    fn, bm = matsubara_indices(12)
+    sysd.update(beta=10.0, ntau=12, fermi_n=fn, bose_m=bm, n_elec=3.0)
+    a = 0.3
+    st = ogw.State(sysd, damping=a)
+    st.iterate()                                  # first iteration: unmixed
+    ref = ogw.State(sysd, damping=a)
+    ref.dyson()
+    Sinf1, _, Siw1 = ref.sigma()
+    assert np.array_equal(st.Sigma_inf, Sinf1) and np.array_equal(st.Sigma_iw, Siw1)
+    ref.Sigma_inf, ref.Sigma_iw = Sinf1, Siw1
+    ref.dyson()
+    Sinf2, _, Siw2 = ref.sigma()                  # unmixed second self-energy from G(Sigma_1)
+    st.iterate()
+    assert np.abs(st.Sigma_inf - ((1 - a) * Sinf1 + a * Sinf2)).max() < 1e-14
+    assert np.abs(st.Sigma_iw - ((1 - a) * Siw1 + a * Siw2)).max() < 1e-14
+    # the mixing is not the identity on this system
+    assert np.abs(Siw2 - Siw1).max() > 1e-6
