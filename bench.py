@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--impl", default="gw", choices=["gw", "reference"])
     p.add_argument("--workload", default="C3", choices=["C1", "C2", "C3", "C4", "C5"])
     p.add_argument("--c5-vjp", action="store_true", help="C5: also time the FP64 adjoint chains")
-    p.add_argument("--precision", default="split_tf32",
+    p.add_argument("--precision", default="split_f16",
                    choices=["split_f16", "split_bf16", "split_tf32", "fp32", "fp64"])
     p.add_argument("--fp64-gemm", default="tensor", choices=["tensor", "native"],
                    help="FP64 tau<->i nu transforms: digit-split tensor-core products or the FP64 SIMT kernel")

@@ -498,16 +498,30 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
     if (a.o_half) {
       // 16-bit hi / lo pieces of D 2^(eA + eB - eO): the next GEMM's operand
       if (lane < nrow) myexp -= out_exp(a, z, r0 + lane);
-      uint16_t* Ch = (uint16_t*)a.C;
-      uint16_t* Cl = (uint16_t*)a.C_lo;
-      for (int r = 0; r < 32; ++r) {
-        const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
-        const int rs = __shfl_sync(0xffffffffu, myexp, r);
-        if (r < nrow && colok) {
-          uint16_t h, l;
-          half_pieces(a.o_half, al * stg[r * 33 + lane] * p2f(colexp + rs), h, l);
-          Ch[base + coff] = h;
-          Cl[base + coff] = l;
+      uint16_t* Ch = (uint16_t*)a.C + coff;
+      uint16_t* Cl = (uint16_t*)a.C_lo + coff;
+      const float csc = al * p2f(colexp);
+      if (a.o_half == 2) {
+        for (int r = 0; r < 32; ++r) {
+          const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+          const int rs = __shfl_sync(0xffffffffu, myexp, r);
+          if (r < nrow && colok) {
+            const float x = stg[r * 33 + lane] * csc * p2f(rs);
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            Ch[base] = __bfloat16_as_ushort(h);
+            Cl[base] = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+          }
+        }
+      } else {
+        for (int r = 0; r < 32; ++r) {
+          const int64_t base = __shfl_sync(0xffffffffu, myoff, r);
+          const int rs = __shfl_sync(0xffffffffu, myexp, r);
+          if (r < nrow && colok) {
+            const float x = stg[r * 33 + lane] * csc * p2f(rs);
+            const __half h = __float2half_rn(x);
+            Ch[base] = __half_as_ushort(h);
+            Cl[base] = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+          }
         }
       }
     } else if (a.eA) {
@@ -777,6 +791,9 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
       for (int j = 0; j < BW; ++j) acc[j] = 0.f;
       bool ok = true;
       int blast = 0;
+      // a tile whose K range fits in one chunk needs no register sums: its chunk buffer
+      // already holds the tile's sums and the write-out reads it directly
+      const bool single = nch == 1;
       for (int c = 0; c < nch; ++c) {
         const uint32_t chunk = cg + (uint32_t)c;
         const int b = (int)(chunk & 1u);
@@ -788,6 +805,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (single) { blast = b; break; }
         // GRP columns in flight per wait (fewer load round trips, within the register budget)
         constexpr int GRP = BW >= 112 ? 16 : BW > 80 ? 32 : 64;
 #pragma unroll
@@ -829,6 +847,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
       const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((grp * 2 + blast) * BN + cbase);
 #pragma unroll
       for (int c0 = 0; c0 < BW; c0 += 16) {
+        if (single) break;
         asm volatile(
             "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
             ::"r"(tbase + (uint32_t)c0), "r"(__float_as_uint(acc[c0 + 0])), "r"(__float_as_uint(acc[c0 + 1])),
@@ -839,7 +858,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
               "r"(__float_as_uint(acc[c0 + 14])), "r"(__float_as_uint(acc[c0 + 15]))
             : "memory");
       }
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      if (!single) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       // write-out
       const int row = m0 + quarter * 32 + lane;
       if (a.direct && m0 + quarter * 32 < a.M) {
@@ -891,25 +910,42 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
               }
             }
           } else if (rok && a.o_half) {
-            // 16-bit hi / lo pieces of D 2^(eA + eB - eO), (re, im) pairs as one 32-bit store
+            // 16-bit hi / lo pieces of D 2^(eA + eB - eO): each (re, im) pair converted as one
+            // fp16x2 / bf16x2 value and stored with one 32-bit store per plane
             const int rexp = row_exp(a, z, row) - out_exp(a, z, row);
             // one column exponent for the whole tile when B has one per batch entry
-            const bool bconst = a.eb_div >= ((int64_t)1 << 30);
+            const bool bconst = a.eb_div >= ((int64_t)1 << 30) || !a.eB;
             const int cconst = (a.eB && bconst) ? a.eB[(int64_t)z * a.eb_zs] : 0;
             const float rsc = al * p2f(rexp + cconst);
-            uint16_t* Ch = (uint16_t*)a.C;
-            uint16_t* Cl = (uint16_t*)a.C_lo;
+            const int nb = n0 + cbase + cb;   // first column of this 32-column block
+            int nv = a.N - nb;
+            nv = nv < 0 ? 0 : (nv > BW - cb ? BW - cb : nv);
+            const int64_t cs = a.col_s1;
+            uint16_t* ph = (uint16_t*)a.C + myoff + (int64_t)(nb >> 1) * cs;
+            uint16_t* pl = (uint16_t*)a.C_lo + myoff + (int64_t)(nb >> 1) * cs;
+            if (a.o_half == 2) {
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              const int n = n0 + cbase + cb + j;
-              if (cb + j < BW && n < a.N) {
-                const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const float sc = (bconst || !a.eB) ? rsc : al * p2f(rexp + col_exp(a, z, n));
-                uint16_t hr, lr, hm, lm;
-                half_pieces(a.o_half, sc * __uint_as_float(v[j]), hr, lr);
-                half_pieces(a.o_half, sc * __uint_as_float(v[j + 1]), hm, lm);
-                *(uint32_t*)(Ch + off) = (uint32_t)hr | ((uint32_t)hm << 16);
-                *(uint32_t*)(Cl + off) = (uint32_t)lr | ((uint32_t)lm << 16);
+              for (int j = 0; j < 32; j += 2) {
+                if (j < nv) {
+                  const float sc = bconst ? rsc : al * p2f(rexp + col_exp(a, z, nb + j));
+                  const float2 x = make_float2(sc * __uint_as_float(v[j]), sc * __uint_as_float(v[j + 1]));
+                  const __nv_bfloat162 h2 = __float22bfloat162_rn(x);
+                  const float2 hx = __bfloat1622float2(h2);
+                  *(__nv_bfloat162*)(ph + (j >> 1) * cs) = h2;
+                  *(__nv_bfloat162*)(pl + (j >> 1) * cs) = __float22bfloat162_rn(make_float2(x.x - hx.x, x.y - hx.y));
+                }
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; j += 2) {
+                if (j < nv) {
+                  const float sc = bconst ? rsc : al * p2f(rexp + col_exp(a, z, nb + j));
+                  const float2 x = make_float2(sc * __uint_as_float(v[j]), sc * __uint_as_float(v[j + 1]));
+                  const __half2 h2 = __float22half2_rn(x);
+                  const float2 hx = __half22float2(h2);
+                  *(__half2*)(ph + (j >> 1) * cs) = h2;
+                  *(__half2*)(pl + (j >> 1) * cs) = __float22half2_rn(make_float2(x.x - hx.x, x.y - hx.y));
+                }
               }
             }
           } else if (rok && a.eA) {

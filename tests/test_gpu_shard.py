@@ -41,7 +41,7 @@ def test_two_q_blocks_sum_to_full_iteration(precision):
             assert np.abs(g.get(q) - full.get(q)).max() < (1e-12 if precision == "fp64" else 1e-7), q
         assert np.abs(g.get("G_tau") - st.G_tau).max() < tol
         assert np.abs(g.get("Sigma_iw") - st.Sigma_iw).max() < tol
-        assert abs(g.get("mu") - st.mu) < 1e-8
+        assert abs(g.get("mu") - st.mu) < (1e-8 if precision == "fp64" else 1e-5)
     # a partial Sigma~(tau) alone is not the full one (both blocks contribute)
     assert np.abs(S - partial[0]).max() > 1e-3 * np.abs(S).max()
 

@@ -26,7 +26,7 @@ def test_trs_reduction_matches_full(precision, tol_full, tol_oracle):
         assert np.abs(a - b).max() <= tol_full * max(1.0, np.abs(b).max()), q
     for q in ("G_tau", "Sigma_iw", "Sigma_inf"):
         assert np.abs(red.get(q) - getattr(st, q)).max() < tol_oracle, q
-    assert abs(red.get("mu") - st.mu) < 1e-8
+    assert abs(red.get("mu") - st.mu) < (1e-8 if precision == "fp64" else 1e-6)
 
 
 def test_trs_flag_rejects_asymmetric_system():
