@@ -9,17 +9,21 @@
  *   - Complex arrays are interleaved (re, im) IEEE doubles, row-major.
  *   - nk = kmesh[0]*kmesh[1]*kmesh[2]; k = (i1*kmesh[1] + i2)*kmesh[2] + i3
  *     (Gamma-centred mesh); k+q and k-q are taken componentwise modulo the mesh.
- *   - nw = ntau: the same number of sampled Matsubara points as tau nodes,
- *     for both fermionic and bosonic functions.
+ *   - nwf, nwb: sampled fermionic / bosonic Matsubara points.  With gw_init both
+ *     equal ntau; with gw_init_grid they are the caller's grid's.
  *   - Layouts:  H0, S, Sigma_inf, gamma          [nk][nao][nao]
  *               V^{k k'}_{ij}(Q)                 [nk][nk][naux][nao][nao]
- *               G, Sigma~ (tau or i w)           [ntau][nk][nao][nao]
- *               P~0, P~ (tau or i Omega)         [nq = nk][ntau][naux][naux]
- *   - The tau grid is the first-kind Chebyshev roots on [0, beta]; a function
- *     of tau is represented by the interpolating polynomial through its node
- *     values.  The forward transform is the exact Fourier integral of that
+ *               G, Sigma~ (tau)                  [ntau][nk][nao][nao]
+ *               G, Sigma~ (i w)                  [nwf][nk][nao][nao]
+ *               P~0, P~ (tau)                    [nq = nk][ntau][naux][naux]
+ *               P~0, P~ (i Omega)                [nq][nwb][naux][naux]
+ *   - gw_init's tau grid is the first-kind Chebyshev roots on [0, beta]; a
+ *     function of tau is represented by the interpolating polynomial through its
+ *     node values.  The forward transform is the exact Fourier integral of that
  *     interpolant at the sampled frequencies (Eq. tau_to_iw); the backward
- *     transform is its exact inverse (stand-in for Eq. iw_to_tau).
+ *     transform is its exact inverse (stand-in for Eq. iw_to_tau).  gw_init_grid
+ *     takes any sparse-sampling grid instead (the paper's IR basis, Sec.
+ *     "Representation on the imaginary axes").
  *
  * Ownership and errors
  *   - Inputs are copied during gw_init (device pointers with GW_INPUT_DEVICE;
@@ -131,21 +135,21 @@ typedef struct {
 /* Quantities readable with gw_get / writable with gw_set.  Sizes in bytes. */
 typedef enum {
   GW_Q_G_TAU = 0,      /* [ntau][nk][nao][nao] c128  (get, set)                 */
-  GW_Q_G_IW = 1,       /* [nw][nk][nao][nao]   c128  (get)                      */
+  GW_Q_G_IW = 1,       /* [nwf][nk][nao][nao]  c128  (get)                      */
   GW_Q_SIGMA_INF = 2,  /* [nk][nao][nao]       c128  (get, set) static part      */
   GW_Q_SIGMA_TAU = 3,  /* [ntau][nk][nao][nao] c128  (get, set)                 */
-  GW_Q_SIGMA_IW = 4,   /* [nw][nk][nao][nao]   c128  (get, set) dynamic part     */
+  GW_Q_SIGMA_IW = 4,   /* [nwf][nk][nao][nao]  c128  (get, set) dynamic part     */
   GW_Q_P0_TAU = 5,     /* [nq][ntau][naux][naux] c128 (get, set)                */
-  GW_Q_P0_IW = 6,      /* [nq][nw][naux][naux]  c128 (get, set); overwritten by
+  GW_Q_P0_IW = 6,      /* [nq][nwb][naux][naux] c128 (get, set); overwritten by
                           gw_screened, which leaves P~(i Omega) in its place    */
   GW_Q_P_IW = 7,       /* same buffer as GW_Q_P0_IW after gw_screened (get)     */
   GW_Q_P_TAU = 8,      /* [nq][ntau][naux][naux] c128 (get, set)                */
   GW_Q_GAMMA = 9,      /* [nk][nao][nao] c128 density matrix (get)              */
   GW_Q_MU = 10,        /* double (get, set)                                     */
-  GW_Q_TFF = 11,       /* [nw][ntau] c128 fermionic tau -> i w   (get)          */
-  GW_Q_TBF = 12,       /* [ntau][nw] c128 fermionic i w -> tau   (get)          */
-  GW_Q_TFB = 13,       /* [nw][ntau] c128 bosonic tau -> i Omega (get)          */
-  GW_Q_TBB = 14,       /* [ntau][nw] c128 bosonic i Omega -> tau (get)          */
+  GW_Q_TFF = 11,       /* [nwf][ntau] c128 fermionic tau -> i w   (get)         */
+  GW_Q_TBF = 12,       /* [ntau][nwf] c128 fermionic i w -> tau   (get)         */
+  GW_Q_TFB = 13,       /* [nwb][ntau] c128 bosonic tau -> i Omega (get)         */
+  GW_Q_TBB = 14,       /* [ntau][nwb] c128 bosonic i Omega -> tau (get)         */
   GW_Q_LB = 15,        /* [ntau] double  L_j(beta^-)             (get)          */
   GW_Q_TAU = 16,       /* [ntau] double  tau nodes               (get)          */
   GW_Q_N_ELEC = 17,    /* double electron count at the last mu   (get)          */
@@ -162,6 +166,27 @@ typedef struct {
   float ms_polarization, ms_screened, ms_selfenergy, ms_dyson, ms_hf;
 } gw_iter_stats;
 
+/* A sparse-sampling grid supplied by the caller (host arrays, read during
+ * gw_init_grid only): the paper represents functions of tau and i w on the IR
+ * basis and samples them at points of that basis (Sec. "Representation on the
+ * imaginary axes"); any grid with the same structure works.  A function X of tau
+ * is given by its values at the ntau points; X(i w_n) = sum_j TFf[n][j] X(tau_j)
+ * at the nwf fermionic points, X(tau_j) = sum_n TBf[j][n] X(i w_n) back (and TFb,
+ * TBb at the nwb bosonic points); X(beta^-) = sum_j lb[j] X(tau_j) gives the
+ * density matrix.  Complex matrices are interleaved (re, im) doubles, row-major. */
+typedef struct {
+  int32_t ntau;            /* tau points (must equal the config's ntau)            */
+  int32_t nwf, nwb;        /* fermionic / bosonic Matsubara points                  */
+  const double* tau;       /* [ntau] in [0, beta]                                   */
+  const int32_t* fermi_n;  /* [nwf] w_n = (2n+1) pi / beta (distinct)               */
+  const int32_t* bose_m;   /* [nwb] Omega_m = 2 m pi / beta (distinct)              */
+  const double* TFf;       /* [nwf][ntau] complex                                   */
+  const double* TBf;       /* [ntau][nwf] complex                                   */
+  const double* TFb;       /* [nwb][ntau] complex                                   */
+  const double* TBb;       /* [ntau][nwb] complex                                   */
+  const double* lb;        /* [ntau] real                                           */
+} gw_grid;
+
 /* Create a context: validates sizes, copies H0, S (Eq. scalar_S) and V (Eq.
  * U_decompose), builds the tau grid, the transform matrices and the density
  * weights on the device.  Unless GW_SKIP_CHECKS, rejects with GW_ERR_ARG
@@ -169,6 +194,12 @@ typedef struct {
  * 1e-10 relative.  Synchronises cfg->stream.  *out is NULL on failure. */
 gw_status gw_init(const gw_config* cfg, const double* H0, const double* S, const double* V,
                   gw_ctx** out);
+
+/* gw_init on the caller's sampling grid instead of the Chebyshev grid (the
+ * config's fermi_n / bose_m are then ignored).  GW_ERR_ARG for a null array, a
+ * grid whose ntau differs from the config's, or repeated Matsubara indices. */
+gw_status gw_init_grid(const gw_config* cfg, const gw_grid* grid, const double* H0, const double* S,
+                       const double* V, gw_ctx** out);
 
 /* Free every device buffer of the context (borrowed V excepted). */
 gw_status gw_destroy(gw_ctx* ctx);
@@ -344,7 +375,7 @@ gw_status gw_selfenergy_jvp(gw_ctx* ctx, const double* dG, const double* dP_tau,
 /* Tangent of the self-consistency map F: (Sigma_inf, Sigma(i w)) -> (Sigma_inf',
  * Sigma'(i w)) (one pass of Eqs. Dyson, iw_to_tau, HF_J/HF_K, tilde_P0_tau,
  * tilde_P_omega, tilde_sigma2, tau_to_iw, with mu held at N(mu) = n_elec) along
- * (dSinf [nk][nao][nao], dSiw [nw][nk][nao][nao]), at the context's state: G
+ * (dSinf [nk][nao][nao], dSiw [nwf][nk][nao][nao]), at the context's state: G
  * from gw_dyson at the current Sigma and P~ from gw_polarization + gw_screened
  * at that G (GW_ERR_STATE otherwise).  Outputs oSinf, oSiw (same shapes) are
  * overwritten; all device pointers.  The Dyson and mu tangents

@@ -19,7 +19,8 @@ namespace gwk { std::atomic<long long> g_launches{0}; }
 
 struct gw_ctx {
   gw_config cfg{};
-  int nao = 0, naux = 0, nk = 0, ntau = 0, nw = 0;
+  int nao = 0, naux = 0, nk = 0, ntau = 0, nw = 0;   // nw: fermionic Matsubara points (= nwf)
+  int nwf = 0, nwb = 0;                              // fermionic / bosonic Matsubara points
   int q0 = 0, q1 = 0;   // q-points [q0, q1) of the P~0, screened and Sigma~ contractions (all by default)
   // time-reversal symmetry (GW_TRS): kneg[k] = index of -k; the forward P~0, screened solve and
   // Sigma~ skip every q (k) with kneg < q (k) and take its result as the conjugate of its partner's
@@ -305,22 +306,24 @@ static GettDesc base_desc(int64_t M, int64_t N, int64_t K, int64_t Z) {
 // way: digit-split products on the tensor cores (k_emul.cu) or the FP64 contraction kernel.
 static cudaError_t transform(gw_ctx* c, const double2* T, const double2* X, double2* Y, int64_t nrow, int64_t ncol,
                              int64_t batch, int64_t xstride, int64_t ystride) {
-  if (c->emul) {
-    const double2* Ts[4] = {c->TFf, c->TBf, c->TFb, c->TBb};
-    int idx = -1;
-    for (int i = 0; i < 4; ++i) if (Ts[i] == T) idx = i;
-    if (idx >= 0 && emul_digit_bytes(ncol, c->ntau) <= c->emA_bytes) {
-      for (int64_t z = 0; z < batch; ++z) {
-        cudaError_t e = emul_transform(c->Tdig[idx], c->Texp[idx], nrow, X + z * xstride, c->ntau, ncol, ncol,
-                                       Y + z * ystride, ncol, c->emA, c->emAe, c->info + 1, c->st);
-        if (e != cudaSuccess) return e;
-      }
-      count((int)(batch * (1 + emul_launches(c->ntau))));
-      return cudaSuccess;
+  // K of each transform: TFf, TFb take tau values; TBf takes nwf, TBb nwb Matsubara values
+  const double2* Ts[4] = {c->TFf, c->TBf, c->TFb, c->TBb};
+  const int64_t Ks[4] = {c->ntau, c->nwf, c->ntau, c->nwb};
+  int idx = -1;
+  for (int i = 0; i < 4; ++i) if (Ts[i] == T) idx = i;
+  if (idx < 0) return cudaErrorInvalidValue;
+  const int64_t K = Ks[idx];
+  if (c->emul && emul_digit_bytes(ncol, K) <= c->emA_bytes) {
+    for (int64_t z = 0; z < batch; ++z) {
+      cudaError_t e = emul_transform(c->Tdig[idx], c->Texp[idx], nrow, X + z * xstride, K, ncol, ncol,
+                                     Y + z * ystride, ncol, c->emA, c->emAe, c->info + 1, c->st);
+      if (e != cudaSuccess) return e;
     }
+    count((int)(batch * (1 + emul_launches(K))));
+    return cudaSuccess;
   }
-  GettDesc d = base_desc(nrow, ncol, c->ntau, batch);
-  d.am = I1(c->ntau); d.ak = I1(1);
+  GettDesc d = base_desc(nrow, ncol, K, batch);
+  d.am = I1(K); d.ak = I1(1);
   d.bk = I1(ncol); d.bn = I1(1); d.bz = I1(xstride);
   d.cm = I1(ncol); d.cn = I1(1); d.cz = I1(ystride);
   return run_gett(d, T, Ty::C128, X, Ty::C128, Y, Ty::C128, Ty::C128, c);
@@ -332,8 +335,23 @@ static int kidx(const int* m, int a, int b, int cc) {
 
 // ------------------------------------------------------------------ init / destroy
 
+static gw_status init_impl(const gw_config* cfg, const gw_grid* grid, const double* H0, const double* S,
+                           const double* V, gw_ctx** out);
+
 extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const double* S, const double* V,
                              gw_ctx** out) {
+  return init_impl(cfg, nullptr, H0, S, V, out);
+}
+
+extern "C" gw_status gw_init_grid(const gw_config* cfg, const gw_grid* grid, const double* H0, const double* S,
+                                  const double* V, gw_ctx** out) {
+  if (out) *out = nullptr;
+  if (!grid) return fail(nullptr, GW_ERR_ARG, "null grid");
+  return init_impl(cfg, grid, H0, S, V, out);
+}
+
+static gw_status init_impl(const gw_config* cfg, const gw_grid* grid, const double* H0, const double* S,
+                           const double* V, gw_ctx** out) {
   if (!out) return fail(nullptr, GW_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!cfg || !H0 || !S || !V) return fail(nullptr, GW_ERR_ARG, "null config or input pointer");
@@ -341,20 +359,34 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
       cfg->kmesh[2] <= 0)
     return fail(nullptr, GW_ERR_ARG, "sizes must be positive");
   if (cfg->nao > 96) return fail(nullptr, GW_ERR_ARG, "nao > 96 is not supported by the Dyson kernel");
-  if (!(cfg->beta > 0) || !cfg->fermi_n || !cfg->bose_m) return fail(nullptr, GW_ERR_ARG, "bad beta or index sets");
+  if (grid) {
+    if (grid->ntau != cfg->ntau || grid->nwf <= 0 || grid->nwb <= 0)
+      return fail(nullptr, GW_ERR_ARG, "grid: ntau must equal cfg->ntau and nwf, nwb be positive");
+    if (!grid->tau || !grid->fermi_n || !grid->bose_m || !grid->TFf || !grid->TBf || !grid->TFb || !grid->TBb ||
+        !grid->lb)
+      return fail(nullptr, GW_ERR_ARG, "grid: null array");
+  }
+  if (!(cfg->beta > 0) || (!grid && (!cfg->fermi_n || !cfg->bose_m)))
+    return fail(nullptr, GW_ERR_ARG, "bad beta or index sets");
   if (cfg->contract_prec != GW_FP64 && cfg->contract_prec != GW_FP32 && cfg->contract_prec != GW_SPLIT_TF32 &&
       cfg->contract_prec != GW_SPLIT_F16 && cfg->contract_prec != GW_SPLIT_BF16)
     return fail(nullptr, GW_ERR_ARG, "contract_prec not available");
   if ((cfg->flags & GW_BORROW_V) && !(cfg->flags & GW_INPUT_DEVICE))
     return fail(nullptr, GW_ERR_ARG, "GW_BORROW_V needs GW_INPUT_DEVICE");
-  for (int i = 0; i < cfg->ntau; ++i)
-    for (int j = i + 1; j < cfg->ntau; ++j)
-      if (cfg->fermi_n[i] == cfg->fermi_n[j] || cfg->bose_m[i] == cfg->bose_m[j])
-        return fail(nullptr, GW_ERR_ARG, "repeated Matsubara index");
+  const int nwf_ = grid ? grid->nwf : cfg->ntau, nwb_ = grid ? grid->nwb : cfg->ntau;
+  const int32_t* fn_h = grid ? grid->fermi_n : cfg->fermi_n;
+  const int32_t* bm_h = grid ? grid->bose_m : cfg->bose_m;
+  for (int i = 0; i < nwf_; ++i)
+    for (int j = i + 1; j < nwf_; ++j)
+      if (fn_h[i] == fn_h[j]) return fail(nullptr, GW_ERR_ARG, "repeated Matsubara index");
+  for (int i = 0; i < nwb_; ++i)
+    for (int j = i + 1; j < nwb_; ++j)
+      if (bm_h[i] == bm_h[j]) return fail(nullptr, GW_ERR_ARG, "repeated Matsubara index");
   gw_ctx* c = new (std::nothrow) gw_ctx();
   if (!c) return fail(nullptr, GW_ERR_OOM, "host allocation failed");
   c->cfg = *cfg;
-  c->nao = cfg->nao; c->naux = cfg->naux; c->ntau = cfg->ntau; c->nw = cfg->ntau;
+  c->nao = cfg->nao; c->naux = cfg->naux; c->ntau = cfg->ntau;
+  c->nwf = c->nw = nwf_; c->nwb = nwb_;
   c->nk = cfg->kmesh[0] * cfg->kmesh[1] * cfg->kmesh[2];
   c->q0 = 0; c->q1 = c->nk;
   c->n2 = (int64_t)c->nao * c->nao; c->na2 = (int64_t)c->naux * c->naux;
@@ -392,30 +424,34 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   else c->V = (double2*)need(A(vbytes));
   const bool lowp = cfg->contract_prec != GW_FP64;
   if (lowp) c->V32 = (float2*)need(A(vbytes / 2));
+  const int nwf = c->nwf, nwb = c->nwb;
+  const int kmax = ntau > nwf ? (ntau > nwb ? ntau : nwb) : (nwf > nwb ? nwf : nwb);
   c->tau = (double*)need(A(ntau * 8)); c->lb = (double*)need(A(ntau * 8)); c->l0 = (double*)need(A(ntau * 8));
-  c->wn = (double*)need(A(ntau * 8));
-  c->TFf = (double2*)need(A((size_t)ntau * ntau * cb)); c->TBf = (double2*)need(A((size_t)ntau * ntau * cb));
-  c->TFb = (double2*)need(A((size_t)ntau * ntau * cb)); c->TBb = (double2*)need(A((size_t)ntau * ntau * cb));
+  c->wn = (double*)need(A(nwf * 8));
+  // transforms: TFf [nwf][ntau], TBf [ntau][nwf], TFb [nwb][ntau], TBb [ntau][nwb]
+  c->TFf = (double2*)need(A((size_t)nwf * ntau * cb)); c->TBf = (double2*)need(A((size_t)ntau * nwf * cb));
+  c->TFb = (double2*)need(A((size_t)nwb * ntau * cb)); c->TBb = (double2*)need(A((size_t)ntau * nwb * cb));
   c->emul = !(cfg->flags & GW_FP64_NATIVE);
   if (c->emul) {
     const int64_t ncmax = (int64_t)na2 > (int64_t)nk * n2 ? (int64_t)na2 : (int64_t)nk * n2;
-    c->emA_bytes = emul_digit_bytes(ncmax, ntau);
+    c->emA_bytes = emul_digit_bytes(ncmax, kmax);
     c->emA = (float*)need(A(c->emA_bytes));
     c->emAe = (int*)need(A((size_t)ncmax * 4));
+    const int rows[4] = {nwf, ntau, nwb, ntau}, kk[4] = {ntau, nwf, ntau, nwb};
     for (int i = 0; i < 4; ++i) {
-      c->Tdig[i] = (float*)need(A(emul_digit_bytes(2 * (int64_t)ntau, ntau)));
-      c->Texp[i] = (int*)need(A((size_t)ntau * 4));
+      c->Tdig[i] = (float*)need(A(emul_digit_bytes(2 * (int64_t)rows[i], kk[i])));
+      c->Texp[i] = (int*)need(A((size_t)rows[i] * 4));
     }
   }
-  c->r = (double2*)need(A(ntau * cb));
-  c->d_fn = (int*)need(A(ntau * 4)); c->d_bm = (int*)need(A(ntau * 4));
-  const size_t gsz = (size_t)ntau * nk * n2 * cb;
-  c->G_tau = (double2*)need(A(gsz)); c->G_iw = (double2*)need(A(gsz)); c->G_prev = (double2*)need(A(gsz));
-  c->Stau = (double2*)need(A(gsz)); c->Siw = (double2*)need(A(gsz)); c->Siw_new = (double2*)need(A(gsz));
+  c->r = (double2*)need(A(nwf * cb));
+  c->d_fn = (int*)need(A(nwf * 4)); c->d_bm = (int*)need(A(nwb * 4));
+  const size_t gsz = (size_t)ntau * nk * n2 * cb, gszw = (size_t)nwf * nk * n2 * cb;
+  c->G_tau = (double2*)need(A(gsz)); c->G_iw = (double2*)need(A(gszw)); c->G_prev = (double2*)need(A(gsz));
+  c->Stau = (double2*)need(A(gsz)); c->Siw = (double2*)need(A(gszw)); c->Siw_new = (double2*)need(A(gszw));
   c->gamma = (double2*)need(A(nk * n2 * cb)); c->tQ = (double2*)need(A(naux * cb));
   c->Sinf = (double2*)need(A(nk * n2 * cb)); c->Sinf_new = (double2*)need(A(nk * n2 * cb));
-  const size_t psz = (size_t)nk * ntau * na2 * cb;
-  c->P0_tau = (double2*)need(A(psz)); c->P_iw = (double2*)need(A(psz)); c->P_tau = (double2*)need(A(psz));
+  const size_t psz = (size_t)nk * ntau * na2 * cb, pszw = (size_t)nk * nwb * na2 * cb;
+  c->P0_tau = (double2*)need(A(psz)); c->P_iw = (double2*)need(A(pszw)); c->P_tau = (double2*)need(A(psz));
   // chain intermediates: max(ntau * naux * n2, nk * naux * n2) complex of the contraction type
   size_t chn = (size_t)(ntau > nk ? ntau : nk) * naux * n2;
   c->ch_bytes = chn * (lowp ? 8 : 16);
@@ -514,7 +550,7 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
     c->eY3 = (int*)need(A((size_t)ntau * 4));
   }
   // workspace: split-K partials and the screened-solve panels
-  size_t ws = screened_work_bytes(naux, (int64_t)nk * ntau);
+  size_t ws = screened_work_bytes(naux, (int64_t)nk * nwb);
   const size_t ws_cap = (size_t)4 << 30;
   size_t ws_min = screened_work_bytes(naux, 1) * 8;
   if (ws > ws_cap) ws = ws_cap;
@@ -524,11 +560,13 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   if (ws < splitk) ws = splitk;
   if (ws < splitk2) ws = splitk2;
   int ld = 0;
-  size_t gws = grid_ws_bytes(ntau, cfg->fermi_n, cfg->bose_m, &ld);
-  if (ws < gws) ws = gws;
+  if (!grid) {
+    size_t gws = grid_ws_bytes(ntau, cfg->fermi_n, cfg->bose_m, &ld);
+    if (ws < gws) ws = gws;
+  }
   c->ws_bytes = ws;
   c->ws = need(A(ws));
-  c->partial = (double*)need(A((size_t)ntau * nk * 8));
+  c->partial = (double*)need(A((size_t)(ntau > nwf ? ntau : nwf) * nk * 8));
   if (c->trs) {
     c->d_kneg = (int*)need(A((size_t)nk * 4));
     c->d_kneed = (int*)need(A((size_t)nk * 4));
@@ -540,7 +578,7 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   if (ok && c->emul && screened_refine_ok(naux)) {
     // refined screened solve: as many (q, Omega) systems per batch as the budget
     // allows; without room for one system the FP64 Gauss-Jordan solve is used
-    const int64_t cnt = (int64_t)nk * ntau;
+    const int64_t cnt = (int64_t)nk * nwb;
     const size_t per = screened_refine_bytes(naux, 1);
     int64_t chunk = (int64_t)(opt_budget(kRefineBytes) / per);
     if (chunk < 1) chunk = 1;
@@ -567,11 +605,11 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
   chk(cudaMemcpyAsync(c->H0, H0, nk * n2 * cb, kind, st), "H0 copy");
   chk(cudaMemcpyAsync(c->S, S, nk * n2 * cb, kind, st), "S copy");
   if (!(cfg->flags & GW_BORROW_V)) chk(cudaMemcpyAsync(c->V, V, vbytes, kind, st), "V copy");
-  chk(cudaMemcpyAsync(c->d_fn, cfg->fermi_n, ntau * 4, cudaMemcpyHostToDevice, st), "index copy");
-  chk(cudaMemcpyAsync(c->d_bm, cfg->bose_m, ntau * 4, cudaMemcpyHostToDevice, st), "index copy");
+  chk(cudaMemcpyAsync(c->d_fn, fn_h, nwf * 4, cudaMemcpyHostToDevice, st), "index copy");
+  chk(cudaMemcpyAsync(c->d_bm, bm_h, nwb * 4, cudaMemcpyHostToDevice, st), "index copy");
   chk(cudaMemsetAsync(c->info, 0, 64, st), "memset");
   chk(cudaMemsetAsync(c->Sinf, 0, nk * n2 * cb, st), "memset");
-  chk(cudaMemsetAsync(c->Siw, 0, gsz, st), "memset");
+  chk(cudaMemsetAsync(c->Siw, 0, gszw, st), "memset");
   if (c->Zhi && !c->hfmt) {
     chk(cudaMemsetAsync(c->Zhi, 0, c->zbytes, st), "memset");
     chk(cudaMemsetAsync(c->Zlo, 0, c->zbytes, st), "memset");
@@ -585,20 +623,33 @@ extern "C" gw_status gw_init(const gw_config* cfg, const double* H0, const doubl
       chk(cudaMemsetAsync(c->Xs_lo, 0, xs, st), "memset");
     }
   }
-  // grid and transforms
-  chk(grid_build_ws(ntau, cfg->beta, c->d_fn, c->d_bm, ld, c->ws, c->tau, c->TFf, c->TFb, c->lb, c->l0, st), "grid");
-  count(4);
-  chk(cudaMemcpyAsync(c->TBf, c->TFf, (size_t)ntau * ntau * cb, cudaMemcpyDeviceToDevice, st), "copy");
-  chk(cudaMemcpyAsync(c->TBb, c->TFb, (size_t)ntau * ntau * cb, cudaMemcpyDeviceToDevice, st), "copy");
-  chk(invert_small_gj(c->TBf, ntau, c->info, st), "TBf");
-  chk(invert_small_gj(c->TBb, ntau, c->info, st), "TBb");
-  chk(density_weights(ntau, c->lb, c->TBf, c->r, st), "weights");
+  // grid and transforms: the Chebyshev grid built here, or the caller's sampling grid
+  if (!grid) {
+    chk(grid_build_ws(ntau, cfg->beta, c->d_fn, c->d_bm, ld, c->ws, c->tau, c->TFf, c->TFb, c->lb, c->l0, st),
+        "grid");
+    count(4);
+    chk(cudaMemcpyAsync(c->TBf, c->TFf, (size_t)ntau * ntau * cb, cudaMemcpyDeviceToDevice, st), "copy");
+    chk(cudaMemcpyAsync(c->TBb, c->TFb, (size_t)ntau * ntau * cb, cudaMemcpyDeviceToDevice, st), "copy");
+    chk(invert_small_gj(c->TBf, ntau, c->info, st), "TBf");
+    chk(invert_small_gj(c->TBb, ntau, c->info, st), "TBb");
+  } else {
+    chk(cudaMemcpyAsync(c->tau, grid->tau, ntau * 8, cudaMemcpyHostToDevice, st), "grid copy");
+    chk(cudaMemcpyAsync(c->lb, grid->lb, ntau * 8, cudaMemcpyHostToDevice, st), "grid copy");
+    chk(cudaMemsetAsync(c->l0, 0, ntau * 8, st), "memset");
+    chk(cudaMemcpyAsync(c->TFf, grid->TFf, (size_t)nwf * ntau * cb, cudaMemcpyHostToDevice, st), "grid copy");
+    chk(cudaMemcpyAsync(c->TBf, grid->TBf, (size_t)ntau * nwf * cb, cudaMemcpyHostToDevice, st), "grid copy");
+    chk(cudaMemcpyAsync(c->TFb, grid->TFb, (size_t)nwb * ntau * cb, cudaMemcpyHostToDevice, st), "grid copy");
+    chk(cudaMemcpyAsync(c->TBb, grid->TBb, (size_t)ntau * nwb * cb, cudaMemcpyHostToDevice, st), "grid copy");
+  }
+  chk(density_weights(ntau, nwf, c->lb, c->TBf, c->r, st), "weights");
   if (c->emul) {
     chk(cudaMemsetAsync(c->emA, 0, c->emA_bytes, st), "memset");
     const double2* Ts[4] = {c->TFf, c->TBf, c->TFb, c->TBb};
-    for (int i = 0; i < 4; ++i) chk(emul_split_b(Ts[i], ntau, ntau, ntau, c->Tdig[i], c->Texp[i], st), "digits");
+    const int rows[4] = {nwf, ntau, nwb, ntau}, kk[4] = {ntau, nwf, ntau, nwb};
+    for (int i = 0; i < 4; ++i)
+      chk(emul_split_b(Ts[i], rows[i], kk[i], kk[i], c->Tdig[i], c->Texp[i], st), "digits");
   }
-  chk(fermi_freqs(ntau, cfg->beta, c->d_fn, c->wn, st), "freqs");
+  chk(fermi_freqs(nwf, cfg->beta, c->d_fn, c->wn, st), "freqs");
   count(4);
   if (lowp) { chk(to_c64(c->V, c->V32, vbytes / cb, st), "V32"); count(1); }
   if (c->hfmt) {
@@ -691,24 +742,26 @@ extern "C" int64_t gw_kernel_launches(const gw_ctx*) { return (int64_t)g_launche
 static bool qinfo(gw_ctx* c, gw_quantity q, void** p, size_t* bytes, bool* settable) {
   const size_t cb = 16;
   const size_t gsz = (size_t)c->ntau * c->nk * c->n2 * cb, ksz = (size_t)c->nk * c->n2 * cb;
-  const size_t psz = (size_t)c->nk * c->ntau * c->na2 * cb, tsz = (size_t)c->ntau * c->ntau * cb;
+  const size_t gszw = (size_t)c->nwf * c->nk * c->n2 * cb;
+  const size_t psz = (size_t)c->nk * c->ntau * c->na2 * cb, pszw = (size_t)c->nk * c->nwb * c->na2 * cb;
+  const size_t tszf = (size_t)c->ntau * c->nwf * cb, tszb = (size_t)c->ntau * c->nwb * cb;
   *settable = false;
   switch (q) {
     case GW_Q_G_TAU: *p = c->G_tau; *bytes = gsz; *settable = true; return true;
-    case GW_Q_G_IW: *p = c->G_iw; *bytes = gsz; return true;
+    case GW_Q_G_IW: *p = c->G_iw; *bytes = gszw; return true;
     case GW_Q_SIGMA_INF: *p = c->Sinf; *bytes = ksz; *settable = true; return true;
     case GW_Q_SIGMA_INF_NEW: *p = c->Sinf_new; *bytes = ksz; return true;
     case GW_Q_SIGMA_TAU: *p = c->Stau; *bytes = gsz; *settable = true; return true;
-    case GW_Q_SIGMA_IW: *p = c->Siw; *bytes = gsz; *settable = true; return true;
+    case GW_Q_SIGMA_IW: *p = c->Siw; *bytes = gszw; *settable = true; return true;
     case GW_Q_P0_TAU: *p = c->P0_tau; *bytes = psz; *settable = true; return true;
-    case GW_Q_P0_IW: *p = c->P_iw; *bytes = psz; *settable = true; return true;
-    case GW_Q_P_IW: *p = c->P_iw; *bytes = psz; return true;
+    case GW_Q_P0_IW: *p = c->P_iw; *bytes = pszw; *settable = true; return true;
+    case GW_Q_P_IW: *p = c->P_iw; *bytes = pszw; return true;
     case GW_Q_P_TAU: *p = c->P_tau; *bytes = psz; *settable = true; return true;
     case GW_Q_GAMMA: *p = c->gamma; *bytes = ksz; return true;
-    case GW_Q_TFF: *p = c->TFf; *bytes = tsz; return true;
-    case GW_Q_TBF: *p = c->TBf; *bytes = tsz; return true;
-    case GW_Q_TFB: *p = c->TFb; *bytes = tsz; return true;
-    case GW_Q_TBB: *p = c->TBb; *bytes = tsz; return true;
+    case GW_Q_TFF: *p = c->TFf; *bytes = tszf; return true;
+    case GW_Q_TBF: *p = c->TBf; *bytes = tszf; return true;
+    case GW_Q_TFB: *p = c->TFb; *bytes = tszb; return true;
+    case GW_Q_TBB: *p = c->TBb; *bytes = tszb; return true;
     case GW_Q_LB: *p = c->lb; *bytes = (size_t)c->ntau * 8; return true;
     case GW_Q_TAU: *p = c->tau; *bytes = (size_t)c->ntau * 8; return true;
     default: return false;
@@ -758,7 +811,7 @@ extern "C" gw_status gw_reset_sigma(gw_ctx* c) {
   if (!c) return GW_ERR_ARG;
   c->have_sigma = false;
   CK(cudaMemsetAsync(c->Sinf, 0, (size_t)c->nk * c->n2 * 16, c->st));
-  CK(cudaMemsetAsync(c->Siw, 0, (size_t)c->ntau * c->nk * c->n2 * 16, c->st));
+  CK(cudaMemsetAsync(c->Siw, 0, (size_t)c->nwf * c->nk * c->n2 * 16, c->st));
   return GW_OK;
 }
 
@@ -1051,11 +1104,13 @@ static gw_status polar_chain_half(gw_ctx* c, const double2* Gplus, const double2
   return GW_OK;
 }
 
-// The Sigma~ chain of Eq. tilde_sigma2 with 16-bit pieces (steps and layouts of the
-// split-TF32 chain):
+// The Sigma~ chain of Eq. tilde_sigma2 with 16-bit pieces:
 //   X[t][Q'][(i,a)] = sum_Q conj P~^q_Q'Q(t) V^{k,k-q}_ia(Q)         (rows (t, Q'))
-//   Y[t][i][(Q',b)] = sum_a X[t][Q'][i][a] G^{k-q}_ab(t)             (rows (Q', i), batch t)
-//   Sigma~[t][k][i][j] += -(1/Nk) sum_(Q',b) Y[t][i][(Q',b)] V^{k-q,k}_bj(Q')
+//   Y[t][i][(b,Q')] = sum_a X[t][Q'][i][a] G^{k-q}_ab(t)             (rows (i, Q'), batch t)
+//   Sigma~[t][k][i][j] += -(1/Nk) sum_(b,Q') Y[t][i][(b,Q')] V^{k-q,k}_bj(Q')
+// X is written as rows (t, i, Q') and the last step's K runs over (b, Q'), so that the
+// middle step's consecutive rows Q' are adjacent complex entries of its output (the
+// coalesced lane-per-row write-out).
 // X's rows are scaled from P~'s row sums of moduli times max |V|; Y's from max_Q' of X's
 // bounds times the row sums of G(t).
 static gw_status sigma_chain_half(gw_ctx* c, const double2* Gsrc, const double2* Psrc, double2* out, bool accumulate) {
@@ -1096,23 +1151,26 @@ static gw_status sigma_chain_half(gw_ctx* c, const double2* Gsrc, const double2*
         UmmaOperand ob{c->VThi, c->VTlo, 2 * n2, 1, kps, 0, fmt};
         UmmaScale sc{c->ePc, c->eVall, 0, 0, 0, 1, kAll};
         UmmaOut o{fmt, c->ePs, 0, 1, shift};
-        CK(run_umma(c, fl1, oa, ob, ntau * naux, (int)(2 * n2), kps, 1, c->Xs_hi, false, 1.0, false,
-                    (int64_t)nao * ka, 0, 1, 0, 0, 2 * (int64_t)nao, ka, c->Xs_lo, 2 * (int64_t)naux, &sc, &o));
+        // output row (t, Q'), column (i, a re/im) -> X row (t, i, Q'), entry (a re/im)
+        CK(run_umma(c, fl1, oa, ob, ntau * naux, (int)(2 * n2), kps, 1, c->Xs_hi, false, 1.0, false, ka, 0, 1, naux,
+                    (int64_t)nao * naux * ka, 2 * (int64_t)nao, (int64_t)naux * ka, c->Xs_lo, 2 * (int64_t)naux, &sc,
+                    &o));
       }
-      // Y = X G^{k-q}(t): A rows (Q', i) per t, B = Ge[k-q][t]; written as rows (t, i) of
-      // columns (Q', b) for the last step
+      // Y = X G^{k-q}(t): A rows (i, Q') per t (exponent of row Q'), B = Ge[k-q][t]; row (i, Q'),
+      // column (b re/im) lands at row (t, i), K entry (b, Q') of the last step's operand
       {
         UmmaOperand xa{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka, fmt};
         UmmaOperand gb{hofs(c->Ge_hi, (int64_t)kmq * ntau * per), hofs(c->Ge_lo, (int64_t)kmq * ntau * per),
                        2 * (int64_t)nao, ntau, ka, per, fmt};
-        UmmaScale sc{c->ePs, c->eGe + (size_t)kmq * ntau, naux, 1, shift, nao, kAll};
+        UmmaScale sc{c->ePs, c->eGe + (size_t)kmq * ntau, naux, 1, shift, 1, kAll};
+        sc.ea_mod = naux;
         UmmaOut o{fmt, c->eY3, 1, kAll, 0};
-        CK(run_umma(c, fl2, xa, gb, naux * nao, 2 * nao, ka, ntau, c->Y3hi, false, 1.0, false, kp3,
-                    (int64_t)nao * kp3, 1, nao, 2 * (int64_t)nao, 0, 0, c->Y3lo, 2 * (int64_t)nao, &sc, &o));
+        CK(run_umma(c, fl2, xa, gb, naux * nao, 2 * nao, ka, ntau, c->Y3hi, false, 1.0, false, 2,
+                    (int64_t)nao * kp3, 1, naux, kp3, 2, 2 * (int64_t)naux, c->Y3lo, 2 * (int64_t)nao, &sc, &o));
       }
-      // Sigma~ += -(1/Nk) Y V^{k-q,k}: B = V^{k-q,k} transposed, rows j, K = (Q', b)
+      // Sigma~ += -(1/Nk) Y V^{k-q,k}: B = V^{k-q,k} transposed, rows j, K = (b, Q') (source rows (Q', b))
       CK(half_embed_t(c->V + ((size_t)kmq * nk + k) * slab, (int64_t)naux * nao, nao, c->W3hi, c->W3lo, kp3, fmt,
-                      c->h_Evmax - 15, st));
+                      c->h_Evmax - 15, st, nao, naux));
       count(1);
       {
         UmmaOperand ya{c->Y3hi, c->Y3lo, (int64_t)ntau * nao, 1, kp3, 0, fmt};
@@ -1154,8 +1212,8 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
   CK(herm_batched(P0q, naux, (int64_t)nq * ntau, na2, c->st));
   count(1);
   // P~0(i Omega_m) = sum_j TFb[m][j] P~0(tau_j)   (Eq. P0t_to_P0w)
-  CK(transform(c, c->TFb, P0q, c->P_iw + (size_t)c->q0 * c->nw * na2, c->nw, na2, nq, (int64_t)ntau * na2,
-               (int64_t)c->nw * na2));
+  CK(transform(c, c->TFb, P0q, c->P_iw + (size_t)c->q0 * c->nwb * na2, c->nwb, na2, nq, (int64_t)ntau * na2,
+               (int64_t)c->nwb * na2));
   c->have_P0 = true;
   c->have_P = false;
   mark(c, GW_Q_P0_TAU); mark(c, GW_Q_P0_IW); unmark(c, GW_Q_P_IW);
@@ -1168,21 +1226,21 @@ extern "C" gw_status gw_polarization(gw_ctx* c) {
 static gw_status screened_block(gw_ctx* c, int qa, int qb) {
   const int naux = c->naux, ntau = c->ntau, nq = qb - qa;
   const int64_t na2 = c->na2;
-  double2* Pw = c->P_iw + (size_t)qa * c->nw * na2;
+  double2* Pw = c->P_iw + (size_t)qa * c->nwb * na2;
   double2* Pt = c->P_tau + (size_t)qa * ntau * na2;
   if (c->irws) {
     // complex64 inversion refined to FP64 accuracy (P~0 Y on the tensor cores)
     int64_t nl = 0;
-    CK(screened_refine(Pw, naux, (int64_t)nq * c->nw, c->irws, c->irws_bytes, kRefineSteps, c->info + 2,
+    CK(screened_refine(Pw, naux, (int64_t)nq * c->nwb, c->irws, c->irws_bytes, kRefineSteps, c->info + 2,
                        c->info + 1, c->st, &nl));
     count((int)nl);
   } else {
-    CK(screened_inplace(Pw, naux, (int64_t)nq * c->nw, (double2*)c->ws, c->ws_bytes, c->info + 2, c->st));
+    CK(screened_inplace(Pw, naux, (int64_t)nq * c->nwb, (double2*)c->ws, c->ws_bytes, c->info + 2, c->st));
     int64_t nbk = (naux + 63) / 64;
     count((int)(2 + nbk * 7));
   }
   // P~(tau_j) = sum_m TBb[j][m] P~(i Omega_m)   (Eq. Piw_to_Pt), symmetrised
-  CK(transform(c, c->TBb, Pw, Pt, ntau, na2, nq, (int64_t)c->nw * na2, (int64_t)ntau * na2));
+  CK(transform(c, c->TBb, Pw, Pt, ntau, na2, nq, (int64_t)c->nwb * na2, (int64_t)ntau * na2));
   CK(herm_batched(Pt, naux, (int64_t)nq * ntau, na2, c->st));
   count(1);
   return GW_OK;
@@ -1205,7 +1263,7 @@ extern "C" gw_status gw_screened(gw_ctx* c) {
       qa = qb;
     }
     if (s != GW_OK) return s;
-    CK(conj_fill(c->P_iw, 1, c->nk, (int64_t)c->nw * c->na2, c->d_kneg, c->d_kneed, c->st));
+    CK(conj_fill(c->P_iw, 1, c->nk, (int64_t)c->nwb * c->na2, c->d_kneg, c->d_kneed, c->st));
     CK(conj_fill(c->P_tau, 1, c->nk, (int64_t)c->ntau * c->na2, c->d_kneg, c->d_kneed, c->st));
     count(2);
   } else {
@@ -1408,7 +1466,7 @@ extern "C" gw_status gw_selfenergy_finish(gw_ctx* c) {
   if (s != GW_OK) return s;
   s = sigma_iw_new(c);
   if (s != GW_OK) return s;
-  const int64_t ksz = (int64_t)c->nk * c->n2, gsz = (int64_t)c->ntau * ksz;
+  const int64_t ksz = (int64_t)c->nk * c->n2, gsz = (int64_t)c->nwf * ksz;
   CK(cudaMemsetAsync(c->dscr + 8, 0, 8, c->st));
   CK(maxabs_diff(c->Siw_new, c->Siw, gsz, c->dscr + 8, c->st));
   count(1);
@@ -1641,9 +1699,10 @@ static gw_status adj_c64(gw_ctx* c, gwadj::View* v) {
 
 static gw_status adj_view(gw_ctx* c, gwadj::View* v) {
   const int64_t n2 = c->n2;
+  const size_t tw = (size_t)(c->ntau > c->nwf ? (c->ntau > c->nwb ? c->ntau : c->nwb) : (c->nwf > c->nwb ? c->nwf : c->nwb));
   size_t need = (size_t)c->ntau * c->naux * n2;
-  if ((size_t)c->ntau * c->na2 > need) need = (size_t)c->ntau * c->na2;
-  if ((size_t)c->ntau * c->nk * n2 > need) need = (size_t)c->ntau * c->nk * n2;
+  if (tw * c->na2 > need) need = tw * c->na2;
+  if (tw * c->nk * n2 > need) need = tw * c->nk * n2;
   if (!c->adjA) {
     c->adjA = (double2*)dalloc(c, need * 16);
     c->adjB = (double2*)dalloc(c, need * 16);
@@ -1741,7 +1800,7 @@ extern "C" gw_status gw_screened_jvp(gw_ctx* c, const double* dP0_tau, double* d
   gwadj::View v;
   gw_status s = adj_view(c, &v);
   if (s != GW_OK) return s;
-  const int naux = c->naux, ntau = c->ntau, nw = c->nw;
+  const int naux = c->naux, ntau = c->ntau, nw = c->nwb;
   const int64_t na2 = c->na2;
   for (int q = 0; q < c->nk; ++q) {
     const double2* x = (const double2*)dP0_tau + (size_t)q * ntau * na2;
@@ -1786,7 +1845,7 @@ extern "C" gw_status gw_selfenergy_jvp(gw_ctx* c, const double* dG, const double
 static gw_status sc_tangent_buffers(gw_ctx* c) {
   if (c->tGiw) return GW_OK;
   const size_t gsz = (size_t)c->ntau * c->nk * c->n2 * 16, psz = (size_t)c->nk * c->ntau * c->na2 * 16;
-  c->tGiw = (double2*)dalloc(c, gsz);
+  c->tGiw = (double2*)dalloc(c, (size_t)c->nwf * c->nk * c->n2 * 16);
   c->tGtau = (double2*)dalloc(c, gsz);
   c->tS = (double2*)dalloc(c, gsz);
   c->tgam = (double2*)dalloc(c, (size_t)c->nk * c->n2 * 16);
@@ -2228,7 +2287,7 @@ extern "C" gw_status gw_batch_iterate(gw_ctx* const* ctxs, int32_t n, int32_t n_
 namespace {
 struct StateHeader {
   char magic[8];
-  int32_t version, nao, naux, ntau, kmesh[3], flags;
+  int32_t version, nao, naux, ntau, kmesh[3], flags, nwf, nwb;
   double beta, mu, n_at_mu;
 };
 constexpr char kStateMagic[8] = {'G', 'W', 'G', 'B', 'S', 'T', 'A', '1'};
@@ -2242,15 +2301,15 @@ uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
 extern "C" gw_status gw_save_state(gw_ctx* c, const char* path) {
   if (!c || !path) return fail(c, GW_ERR_ARG, "null argument");
   if (!c->have_G) return fail(c, GW_ERR_STATE, "no Green's function to save");
-  const size_t gsz = (size_t)c->ntau * c->nk * c->n2, ksz = (size_t)c->nk * c->n2;
-  std::vector<double2> G(gsz), Si(ksz), Sw(gsz);
+  const size_t gsz = (size_t)c->ntau * c->nk * c->n2, ksz = (size_t)c->nk * c->n2, wsz = (size_t)c->nwf * ksz;
+  std::vector<double2> G(gsz), Si(ksz), Sw(wsz);
   CK(cudaMemcpyAsync(G.data(), c->G_tau, gsz * 16, cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(Si.data(), c->Sinf, ksz * 16, cudaMemcpyDeviceToHost, c->st));
-  CK(cudaMemcpyAsync(Sw.data(), c->Siw, gsz * 16, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(Sw.data(), c->Siw, wsz * 16, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   StateHeader h{};
   memcpy(h.magic, kStateMagic, 8);
-  h.version = 1; h.nao = c->nao; h.naux = c->naux; h.ntau = c->ntau;
+  h.version = 1; h.nao = c->nao; h.naux = c->naux; h.ntau = c->ntau; h.nwf = c->nwf; h.nwb = c->nwb;
   for (int i = 0; i < 3; ++i) h.kmesh[i] = c->cfg.kmesh[i];
   h.flags = (c->have_sigma ? 1 : 0) | (c->have_mu ? 2 : 0);
   h.beta = c->cfg.beta; h.mu = c->mu; h.n_at_mu = c->n_at_mu;
@@ -2274,12 +2333,13 @@ extern "C" gw_status gw_load_state(gw_ctx* c, const char* path) {
   FILE* f = fopen(path, "rb");
   if (!f) return fail(c, GW_ERR_ARG, std::string("cannot open ") + path);
   StateHeader h{};
-  const size_t gsz = (size_t)c->ntau * c->nk * c->n2, ksz = (size_t)c->nk * c->n2;
-  std::vector<double2> G(gsz), Si(ksz), Sw(gsz);
+  const size_t gsz = (size_t)c->ntau * c->nk * c->n2, ksz = (size_t)c->nk * c->n2, wsz = (size_t)c->nwf * ksz;
+  std::vector<double2> G(gsz), Si(ksz), Sw(wsz);
   uint64_t hash = 1469598103934665603ull, stored = 0;
   bool ok = fread(&h, sizeof h, 1, f) == 1;
   const bool same = ok && memcmp(h.magic, kStateMagic, 8) == 0 && h.version == 1 && h.nao == c->nao &&
-                    h.naux == c->naux && h.ntau == c->ntau && h.kmesh[0] == c->cfg.kmesh[0] &&
+                    h.naux == c->naux && h.ntau == c->ntau && h.nwf == c->nwf && h.nwb == c->nwb &&
+                    h.kmesh[0] == c->cfg.kmesh[0] &&
                     h.kmesh[1] == c->cfg.kmesh[1] && h.kmesh[2] == c->cfg.kmesh[2] && h.beta == c->cfg.beta;
   if (!same) { fclose(f); return fail(c, GW_ERR_ARG, "state file does not match this context's sizes"); }
   hash = fnv1a(&h, sizeof h, hash);
@@ -2294,7 +2354,7 @@ extern "C" gw_status gw_load_state(gw_ctx* c, const char* path) {
   if (!ok || stored != hash) return fail(c, GW_ERR_ARG, "state file is truncated or corrupt");
   CK(cudaMemcpyAsync(c->G_tau, G.data(), gsz * 16, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->Sinf, Si.data(), ksz * 16, cudaMemcpyHostToDevice, c->st));
-  CK(cudaMemcpyAsync(c->Siw, Sw.data(), gsz * 16, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->Siw, Sw.data(), wsz * 16, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
   c->have_G = true;
   c->have_sigma = (h.flags & 1) != 0;

@@ -56,8 +56,8 @@ cudaError_t herm_batched(double2* X, int64_t n, int64_t count, int64_t stride, c
 size_t grid_ws_bytes(int ntau, const int* fn_host, const int* bm_host, int* ld_out);
 cudaError_t grid_build_ws(int ntau, double beta, const int* d_fn, const int* d_bm, int ld, void* ws,
                           double* tau, double2* TFf, double2* TFb, double* lb, double* l0, cudaStream_t st);
-cudaError_t density_weights(int ntau, const double* lb, const double2* TBf, double2* r, cudaStream_t st);
-cudaError_t fermi_freqs(int ntau, double beta, const int* fn, double* wn, cudaStream_t st);
+cudaError_t density_weights(int ntau, int nwf, const double* lb, const double2* TBf, double2* r, cudaStream_t st);
+cudaError_t fermi_freqs(int nwf, double beta, const int* fn, double* wn, cudaStream_t st);
 cudaError_t invert_small_gj(double2* A, int n, int* d_info, cudaStream_t st);
 cudaError_t screened_inplace(double2* P, int64_t n, int64_t count, double2* work, size_t work_bytes,
                              int* d_info, cudaStream_t st);
@@ -151,6 +151,7 @@ struct UmmaScale {
   int64_t ea_zs, eb_zs;
   int eshift;
   int64_t ea_div = 1, eb_div = 1;   // row m uses eA[z*ea_zs + m/ea_div], column n eB[z*eb_zs + (n/2)/eb_div]
+  int64_t ea_mod = 0;               // > 0: row m uses eA[z*ea_zs + (m/ea_div) % ea_mod]
 };
 // 16-bit pieces as the output of a GEMM (C: hi, C_lo: lo, fp32-class layout in 16-bit
 // elements): D * 2^-(eO[z*eo_zs + m/eo_div] + eo_shift) in fp16 (half = 1) or bf16 (2)
@@ -206,8 +207,10 @@ cudaError_t half_rows(const double2* src, int64_t rows, int64_t K, int64_t ld, b
                       int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs, cudaStream_t st);
 cudaError_t half_embed_conj(const double2* src, int64_t rows, int64_t K, void* hi, void* lo, int64_t Kpad,
                             int64_t ldo, int fmt, const int* ex, cudaStream_t st);
+// kin > 0: source row k lands at K index (k % kin) * kout + k / kin (a K order permuted from
+// (outer, inner) to (inner, outer))
 cudaError_t half_embed_t(const double2* src, int64_t K, int64_t N, void* hi, void* lo, int64_t Kpad, int fmt, int e,
-                         cudaStream_t st);
+                         cudaStream_t st, int64_t kin = 0, int64_t kout = 0);
 cudaError_t half_embed_mats(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, void* hi,
                             void* lo, int64_t Kpad, int64_t ds, int fmt, bool plain, int* ex, cudaStream_t st);
 cudaError_t v_norms(const double2* V, int64_t nslab, int naux, int nao, float* vmax, float* vrs, cudaStream_t st);

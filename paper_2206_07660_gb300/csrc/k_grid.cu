@@ -164,26 +164,26 @@ cudaError_t invert_small_gj(double2* A, int n, int* d_info, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// r[n] = sum_j lb[j] TBf[j][n]  (weights of the density: gamma = -sum_n r_n G(i w_n))
-__global__ void rweights_kernel(int ntau, const double* lb, const double2* TBf, double2* r) {
+// r[n] = sum_j lb[j] TBf[j][n], TBf [ntau][nwf]  (weights of the density: gamma = -sum_n r_n G(i w_n))
+__global__ void rweights_kernel(int ntau, int nwf, const double* lb, const double2* TBf, double2* r) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= ntau) return;
+  if (n >= nwf) return;
   double re = 0, im = 0;
-  for (int j = 0; j < ntau; ++j) { double2 t = TBf[(int64_t)j * ntau + n]; re += lb[j] * t.x; im += lb[j] * t.y; }
+  for (int j = 0; j < ntau; ++j) { double2 t = TBf[(int64_t)j * nwf + n]; re += lb[j] * t.x; im += lb[j] * t.y; }
   r[n] = make_double2(re, im);
 }
-cudaError_t density_weights(int ntau, const double* lb, const double2* TBf, double2* r, cudaStream_t st) {
-  rweights_kernel<<<(ntau + 63) / 64, 64, 0, st>>>(ntau, lb, TBf, r);
+cudaError_t density_weights(int ntau, int nwf, const double* lb, const double2* TBf, double2* r, cudaStream_t st) {
+  rweights_kernel<<<(nwf + 63) / 64, 64, 0, st>>>(ntau, nwf, lb, TBf, r);
   return cudaGetLastError();
 }
 
 // frequencies w_n = (2n+1) pi / beta
-__global__ void freq_kernel(int ntau, double beta, const int* fn, double* wn) {
+__global__ void freq_kernel(int nwf, double beta, const int* fn, double* wn) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < ntau) wn[n] = (2.0 * fn[n] + 1.0) * M_PI / beta;
+  if (n < nwf) wn[n] = (2.0 * fn[n] + 1.0) * M_PI / beta;
 }
-cudaError_t fermi_freqs(int ntau, double beta, const int* fn, double* wn, cudaStream_t st) {
-  freq_kernel<<<(ntau + 63) / 64, 64, 0, st>>>(ntau, beta, fn, wn);
+cudaError_t fermi_freqs(int nwf, double beta, const int* fn, double* wn, cudaStream_t st) {
+  freq_kernel<<<(nwf + 63) / 64, 64, 0, st>>>(nwf, beta, fn, wn);
   return cudaGetLastError();
 }
 

@@ -22,19 +22,31 @@ namespace gwk {
 __device__ __forceinline__ int bound_exp(double b, int margin) {
   int E = 0;
   if (b > 0.0) frexp(b, &E);
-  return E - 15 + margin;
+  // kept inside [-100, 100] so that 2^-e and every product of scales stays a normal
+  // float (rows below 2^-115 are zero to working accuracy)
+  const int e = E - 15 + margin;
+  return e < -100 ? -100 : (e > 100 ? 100 : e);
 }
 
+// 2^e as a float (e within the normal range; clamped)
+__device__ __forceinline__ float pow2f(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __int_as_float((e + 127) << 23);
+}
+
+// pieces of x 2^-e, x rounded to fp32 first (24 bits, more than the 22 the two
+// pieces keep); the scaling by a power of two is exact; fp32 arithmetic only (the
+// FP64 pipe is a small fraction of the SM's throughput)
 __device__ __forceinline__ void pieces(int fmt, double x, int e, uint16_t& h, uint16_t& l) {
-  const double d = ldexp(x, -e);
+  const float d = (float)x * pow2f(-e);
   if (fmt == 2) {
-    const __nv_bfloat16 hb = __double2bfloat16(d);
-    const __nv_bfloat16 lb = __double2bfloat16(d - (double)__bfloat162float(hb));
+    const __nv_bfloat16 hb = __float2bfloat16_rn(d);
+    const __nv_bfloat16 lb = __float2bfloat16_rn(d - __bfloat162float(hb));
     h = __bfloat16_as_ushort(hb);
     l = __bfloat16_as_ushort(lb);
   } else {
-    const __half hh = __double2half(d);
-    const __half lh = __double2half(d - (double)__half2float(hh));
+    const __half hh = __float2half_rn(d);
+    const __half lh = __float2half_rn(d - __half2float(hh));
     h = __half_as_ushort(hh);
     l = __half_as_ushort(lh);
   }
@@ -64,17 +76,20 @@ __global__ void __launch_bounds__(256) half_rows_kernel(const double2* __restric
   const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= rows) return;
   const double2* x = src + r * ld;
-  double m = 0.0, sm = 0.0;
+  // fp32 is enough for the bounds: a rounded maximum only moves the exponent up, and
+  // the row sum is enlarged by far more than its rounding error
+  float m = 0.f, sm = 0.f;
   for (int64_t k = lane; k < K; k += 32) {
     const double2 v = x[k];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
-    sm += cabs2(v);
+    const float a = (float)v.x, b = (float)v.y;
+    m = fmaxf(m, fmaxf(fabsf(a), fabsf(b)));
+    sm += sqrtf(a * a + b * b);
   }
-  const int e = bound_exp(wmax(m), 0);
-  sm = wsum(sm);
+  const int e = bound_exp((double)wmax((double)m), 0);
+  sm = (float)wsum((double)sm);
   if (lane == 0) {
     ex[r] = e;
-    if (exs) exs[r] = bound_exp(sm, 0);
+    if (exs) exs[r] = bound_exp((double)sm * (1.0 + 1e-4), 0);
   }
   uint32_t* h2 = (uint32_t*)(hi + r * ldo);
   uint32_t* l2 = (uint32_t*)(lo + r * ldo);
@@ -95,20 +110,20 @@ __global__ void __launch_bounds__(256) half_rows_kernel(const double2* __restric
 
 // Doubled operand of C = A conj(B)^T from complex rows n of B (K entries): real rows
 // 2n = (re, im), 2n+1 = (-im, re) of 16-bit pieces at row stride ldo, with the given
-// exponent ex[n] of each complex row.  One warp per complex row.
+// exponent ex[n] of each complex row.  Grid (column blocks of 256 complex entries, rows).
 __global__ void __launch_bounds__(256) half_embed_conj_kernel(const double2* __restrict__ src, int64_t rows,
                                                               int64_t K, uint16_t* hi, uint16_t* lo, int64_t Kpad,
                                                               int64_t ldo, int fmt, const int* ex) {
-  const int lane = threadIdx.x & 31;
-  const int64_t n = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (n >= rows) return;
+  const int64_t n = blockIdx.y;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= rows || 2 * c >= Kpad) return;
   const double2* x = src + n * K;
   const int e = ex[n];
   uint32_t* h0 = (uint32_t*)(hi + 2 * n * ldo);
   uint32_t* l0 = (uint32_t*)(lo + 2 * n * ldo);
   uint32_t* h1 = (uint32_t*)(hi + (2 * n + 1) * ldo);
   uint32_t* l1 = (uint32_t*)(lo + (2 * n + 1) * ldo);
-  for (int64_t c = lane; 2 * c < Kpad; c += 32) {
+  {
     double re = 0.0, im = 0.0;
     if (c < K) {
       const double2 v = x[c];
@@ -130,7 +145,7 @@ __global__ void __launch_bounds__(256) half_embed_conj_kernel(const double2* __r
 // stride N): rows 2n = (re, -im), 2n+1 = (im, re) of 16-bit pieces with one exponent
 // e for the whole operand, transposed through shared memory.  Grid (N/32, K/32).
 __global__ void half_embed_t_kernel(const double2* __restrict__ src, int64_t K, int64_t N, uint16_t* hi, uint16_t* lo,
-                                    int64_t Kpad, int fmt, int e) {
+                                    int64_t Kpad, int fmt, int e, int64_t kin, int64_t kout) {
   __shared__ double2 tile[32][33];
   const int64_t k0 = blockIdx.y * 32, nb = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -143,15 +158,15 @@ __global__ void half_embed_t_kernel(const double2* __restrict__ src, int64_t K, 
     const int64_t n = nb + r, k = k0 + tx;
     if (n >= N || k >= K) continue;
     const double2 v = tile[tx][r];
-    uint16_t a, b, c, d, a2, b2, c2, d2;
+    const int64_t kd = kin > 0 ? (k % kin) * kout + k / kin : k;   // K index in the operand
+    uint16_t a, b, c, a2, b2, c2;
     pieces(fmt, v.x, e, a, a2);
     pieces(fmt, -v.y, e, b, b2);
     pieces(fmt, v.y, e, c, c2);
-    *(uint32_t*)(hi + (2 * n) * Kpad + 2 * k) = (uint32_t)a | ((uint32_t)b << 16);
-    *(uint32_t*)(lo + (2 * n) * Kpad + 2 * k) = (uint32_t)a2 | ((uint32_t)b2 << 16);
-    *(uint32_t*)(hi + (2 * n + 1) * Kpad + 2 * k) = (uint32_t)c | ((uint32_t)a << 16);
-    *(uint32_t*)(lo + (2 * n + 1) * Kpad + 2 * k) = (uint32_t)c2 | ((uint32_t)a2 << 16);
-    (void)d; (void)d2;
+    *(uint32_t*)(hi + (2 * n) * Kpad + 2 * kd) = (uint32_t)a | ((uint32_t)b << 16);
+    *(uint32_t*)(lo + (2 * n) * Kpad + 2 * kd) = (uint32_t)a2 | ((uint32_t)b2 << 16);
+    *(uint32_t*)(hi + (2 * n + 1) * Kpad + 2 * kd) = (uint32_t)c | ((uint32_t)a << 16);
+    *(uint32_t*)(lo + (2 * n + 1) * Kpad + 2 * kd) = (uint32_t)c2 | ((uint32_t)a2 << 16);
   }
   // zero padding columns [2K, Kpad), by the first column of blocks
   if (blockIdx.y == 0) {
@@ -177,9 +192,10 @@ __global__ void __launch_bounds__(256) half_embed_mats_kernel(const double2* __r
   __shared__ double red[8];
   const int64_t z = blockIdx.x;
   const double2* x = src + z * ss;
-  double m = 0.0;
-  for (int64_t i = threadIdx.x; i < rows * K; i += blockDim.x) m = fmax(m, fmax(fabs(x[i].x), fabs(x[i].y)));
-  m = wmax(m);
+  float mf = 0.f;
+  for (int64_t i = threadIdx.x; i < rows * K; i += blockDim.x)
+    mf = fmaxf(mf, fmaxf(fabsf((float)x[i].x), fabsf((float)x[i].y)));
+  double m = wmax((double)mf);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -334,17 +350,19 @@ cudaError_t half_rows(const double2* src, int64_t rows, int64_t K, int64_t ld, b
 
 cudaError_t half_embed_conj(const double2* src, int64_t rows, int64_t K, void* hi, void* lo, int64_t Kpad,
                             int64_t ldo, int fmt, const int* ex, cudaStream_t st) {
-  if (Kpad % 64 || rows <= 0) return cudaErrorInvalidValue;
-  half_embed_conj_kernel<<<nblk(rows, 8), 256, 0, st>>>(src, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad,
-                                                         ldo > 0 ? ldo : Kpad, fmt, ex);
+  if (Kpad % 64 || rows <= 0 || rows > 65535) return cudaErrorInvalidValue;
+  dim3 grid(nblk(Kpad / 2, 256), (unsigned)rows);
+  half_embed_conj_kernel<<<grid, 256, 0, st>>>(src, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad,
+                                               ldo > 0 ? ldo : Kpad, fmt, ex);
   return cudaGetLastError();
 }
 
 cudaError_t half_embed_t(const double2* src, int64_t K, int64_t N, void* hi, void* lo, int64_t Kpad, int fmt, int e,
-                         cudaStream_t st) {
+                         cudaStream_t st, int64_t kin, int64_t kout) {
   if (Kpad % 64 || K <= 0 || N <= 0) return cudaErrorInvalidValue;
+  if (kin > 0 && (K % kin || kout * kin != K)) return cudaErrorInvalidValue;   // a permutation of [0, K)
   dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32), 1);
-  half_embed_t_kernel<<<grid, 256, 0, st>>>(src, K, N, (uint16_t*)hi, (uint16_t*)lo, Kpad, fmt, e);
+  half_embed_t_kernel<<<grid, 256, 0, st>>>(src, K, N, (uint16_t*)hi, (uint16_t*)lo, Kpad, fmt, e, kin, kout);
   return cudaGetLastError();
 }
 

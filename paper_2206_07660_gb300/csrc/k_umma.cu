@@ -76,6 +76,7 @@ struct UmmaArgs {
   const int* eB;
   int64_t ea_zs, eb_zs;
   int64_t ea_div, eb_div;
+  int64_t ea_mod;      // > 0: row m uses eA[z*ea_zs + (m/ea_div) % ea_mod]
   int eshift;
   // o_half != 0: the fp32 output is written as 16-bit hi (C) / lo (C_lo) pieces (1 fp16, 2 bf16)
   // of D * 2^-(eO[z*eo_zs + m/eo_div] + eo_shift): the next GEMM's operand with its row scale
@@ -93,7 +94,10 @@ __device__ __forceinline__ int64_t exp_index(int64_t m, int64_t div) {
 }
 // exponent of the row scale of row m (output or operand side); 0 without scales
 __device__ __forceinline__ int row_exp(const UmmaArgs& a, int z, int64_t m) {
-  return a.eA ? a.eA[(int64_t)z * a.ea_zs + exp_index(m, a.ea_div)] + a.eshift : 0;
+  if (!a.eA) return 0;
+  int64_t i = exp_index(m, a.ea_div);
+  if (a.ea_mod > 0) i = (int64_t)((uint32_t)i % (uint32_t)a.ea_mod);
+  return a.eA[(int64_t)z * a.ea_zs + i] + a.eshift;
 }
 __device__ __forceinline__ int col_exp(const UmmaArgs& a, int z, int64_t n) {
   return a.eB ? a.eB[(int64_t)z * a.eb_zs + exp_index(n >> 1, a.eb_div)] : 0;
@@ -1260,6 +1264,7 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
     a.eA = scale->eA; a.eB = scale->eB; a.ea_zs = scale->ea_zs; a.eb_zs = scale->eb_zs; a.eshift = scale->eshift;
     a.ea_div = scale->ea_div > 0 ? scale->ea_div : 1;
     a.eb_div = scale->eb_div > 0 ? scale->eb_div : 1;
+    a.ea_mod = scale->ea_mod > 0 ? scale->ea_mod : 0;
   }
   int bn = cost_model_bn(N);
   if (g_force_bn) return umma_launch(g_force_bn, A, B, Kpad, nseg, a, batch, st);

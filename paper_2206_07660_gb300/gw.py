@@ -41,6 +41,15 @@ class GwConfig(ctypes.Structure):
     ]
 
 
+class GwGrid(ctypes.Structure):
+    _fields_ = [
+        ("ntau", ctypes.c_int32), ("nwf", ctypes.c_int32), ("nwb", ctypes.c_int32),
+        ("tau", ctypes.c_void_p), ("fermi_n", ctypes.c_void_p), ("bose_m", ctypes.c_void_p),
+        ("TFf", ctypes.c_void_p), ("TBf", ctypes.c_void_p), ("TFb", ctypes.c_void_p), ("TBb", ctypes.c_void_p),
+        ("lb", ctypes.c_void_p),
+    ]
+
+
 class GwIterStats(ctypes.Structure):
     _fields_ = [
         ("mu", ctypes.c_double), ("n_elec", ctypes.c_double), ("mu_steps", ctypes.c_int32),
@@ -64,6 +73,7 @@ def load():
     lib = ctypes.CDLL(LIB_PATH)
     P = ctypes.c_void_p
     lib.gw_init.argtypes = [ctypes.POINTER(GwConfig), P, P, P, ctypes.POINTER(P)]
+    lib.gw_init_grid.argtypes = [ctypes.POINTER(GwConfig), ctypes.POINTER(GwGrid), P, P, P, ctypes.POINTER(P)]
     lib.gw_destroy.argtypes = [P]
     lib.gw_set.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int]
     lib.gw_get.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int]
@@ -95,7 +105,7 @@ def load():
     lib.gw_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.gw_kernel_launches.argtypes = [P]
     lib.gw_kernel_launches.restype = ctypes.c_int64
-    for name in ("gw_init", "gw_destroy", "gw_set", "gw_get", "gw_hf", "gw_polarization", "gw_screened",
+    for name in ("gw_init", "gw_init_grid", "gw_destroy", "gw_set", "gw_get", "gw_hf", "gw_polarization", "gw_screened",
                  "gw_selfenergy", "gw_dyson", "gw_iterate", "gw_reset_sigma", "gw_profile", "gw_profile_read",
                  "gw_polarization_vjp", "gw_selfenergy_vjp", "gw_iterate_graph", "gw_batch_iterate",
                  "gw_polarization_jvp", "gw_screened_jvp", "gw_selfenergy_jvp", "gw_sc_jvp",
@@ -135,20 +145,27 @@ class GW:
 
     H0, S: [nk, nao, nao] complex128; V: [nk, nk, naux, nao, nao] complex128
     (numpy arrays, or CUDA torch tensors with device_inputs=True).
-    fermi_n, bose_m: sampled Matsubara integers (length ntau).
+    fermi_n, bose_m: sampled Matsubara integers (length ntau) of the Chebyshev grid.
+    grid: optional sparse-sampling grid (an object or dict with tau, fermi_n, bose_m,
+    TFf, TBf, TFb, TBb, lb; gw_init_grid) used instead of the Chebyshev grid.
     """
 
-    def __init__(self, H0, S, V, kmesh, ntau, beta, fermi_n, bose_m, n_elec=None, damping=0.5,
+    def __init__(self, H0, S, V, kmesh, ntau, beta, fermi_n=None, bose_m=None, n_elec=None, damping=0.5,
                  mu_tol=1e-9, mu_maxit=400, precision="fp64", spin=2, borrow_V=False,
-                 skip_checks=False, torch_alloc=True, small_steps="auto", fp64_gemm="tensor", trs=False):
+                 skip_checks=False, torch_alloc=True, small_steps="auto", fp64_gemm="tensor", trs=False,
+                 grid=None):
         import torch
         self.lib = load()
         self.torch = torch
         nk, nao = H0.shape[0], H0.shape[1]
         naux = V.shape[2]
         self.nk, self.nao, self.naux, self.ntau = int(nk), int(nao), int(naux), int(ntau)
+        gget = (lambda k: grid[k]) if isinstance(grid, dict) else (lambda k: getattr(grid, k))
+        if grid is not None:
+            fermi_n, bose_m = gget("fermi_n"), gget("bose_m")
         self._fn = np.ascontiguousarray(fermi_n, dtype=np.int32)
         self._bm = np.ascontiguousarray(bose_m, dtype=np.int32)
+        self.nwf, self.nwb = int(self._fn.size), int(self._bm.size)
         cfg = GwConfig()
         cfg.nao, cfg.naux, cfg.ntau = self.nao, self.naux, self.ntau
         for i in range(3):
@@ -194,7 +211,18 @@ class GW:
         cfg.flags = flags
         self._cfg = cfg
         ctx = ctypes.c_void_p()
-        st = self.lib.gw_init(ctypes.byref(cfg), hp, sp, vp, ctypes.byref(ctx))
+        if grid is None:
+            st = self.lib.gw_init(ctypes.byref(cfg), hp, sp, vp, ctypes.byref(ctx))
+        else:
+            keep = {k: np.ascontiguousarray(gget(k), dtype=np.complex128) for k in ("TFf", "TBf", "TFb", "TBb")}
+            keep["tau"] = np.ascontiguousarray(gget("tau"), dtype=np.float64)
+            keep["lb"] = np.ascontiguousarray(np.real(gget("lb")), dtype=np.float64)
+            gr = GwGrid()
+            gr.ntau, gr.nwf, gr.nwb = self.ntau, self.nwf, self.nwb
+            for k, v in keep.items():
+                setattr(gr, k, v.ctypes.data)
+            gr.fermi_n, gr.bose_m = self._fn.ctypes.data, self._bm.ctypes.data
+            st = self.lib.gw_init_grid(ctypes.byref(cfg), ctypes.byref(gr), hp, sp, vp, ctypes.byref(ctx))
         if st != GW_OK:
             raise GWError(st, self.lib.gw_last_error(None).decode())
         self.ctx = ctx
@@ -216,13 +244,13 @@ class GW:
             pass
 
     def shape_of(self, name):
-        nk, nao, naux, nt = self.nk, self.nao, self.naux, self.ntau
+        nk, nao, naux, nt, nf, nb = self.nk, self.nao, self.naux, self.ntau, self.nwf, self.nwb
         return {
-            "G_tau": (nt, nk, nao, nao), "G_iw": (nt, nk, nao, nao), "Sigma_inf": (nk, nao, nao),
-            "Sigma_inf_new": (nk, nao, nao), "Sigma_tau": (nt, nk, nao, nao), "Sigma_iw": (nt, nk, nao, nao),
-            "P0_tau": (nk, nt, naux, naux), "P0_iw": (nk, nt, naux, naux), "P_iw": (nk, nt, naux, naux),
-            "P_tau": (nk, nt, naux, naux), "gamma": (nk, nao, nao), "TFf": (nt, nt), "TBf": (nt, nt),
-            "TFb": (nt, nt), "TBb": (nt, nt),
+            "G_tau": (nt, nk, nao, nao), "G_iw": (nf, nk, nao, nao), "Sigma_inf": (nk, nao, nao),
+            "Sigma_inf_new": (nk, nao, nao), "Sigma_tau": (nt, nk, nao, nao), "Sigma_iw": (nf, nk, nao, nao),
+            "P0_tau": (nk, nt, naux, naux), "P0_iw": (nk, nb, naux, naux), "P_iw": (nk, nb, naux, naux),
+            "P_tau": (nk, nt, naux, naux), "gamma": (nk, nao, nao), "TFf": (nf, nt), "TBf": (nt, nf),
+            "TFb": (nb, nt), "TBb": (nt, nb),
         }[name]
 
     def get(self, name, out=None):
