@@ -198,57 +198,97 @@ def pair_list(nk, n, offset=0):
     return out
 
 
-def cpu_sample(cfg, sysd, n_pairs=2, offset=0, state=None):
+def cpu_state(sysd):
+    """The oracle's state at the non-interacting G0: its own mu search and Dyson
+    step, timed.  Returns (state, seconds)."""
+    from oracle import gw as ogw
+    t0 = time.perf_counter()
+    st = ogw.State(dict(sysd, V=oracle_V(sysd)))
+    st.dyson()
+    return st, time.perf_counter() - t0
+
+
+def tau_subset(ntau, half):
+    """The first and last `half` tau indices: a set closed under tau_j -> tau_{ntau-1-j},
+    so that G(-tau) = -G(beta - tau) of a point in it stays in it."""
+    import numpy as np
+    if 2 * half >= ntau:
+        return np.arange(ntau)
+    return np.r_[0:half, ntau - half:ntau]
+
+
+def cpu_sample(cfg, sysd, state, n_pairs=1, offset=0, tau_half=4):
     """Time the oracle on a bounded slice of one iteration and extrapolate.
 
-    The slice: A2 (P~0) and A6 (Sigma~) on n_pairs (q, k) pairs, the screened
-    solve with its two transforms for one q, the exchange term for one k and
-    one k', and the q-independent rest (Hartree, the Sigma~ transform, mu
-    search and Dyson) in full.  Seconds per iteration = each part x (total
-    units / sampled units).  The oracle's G0 (state) may be passed in.
+    The slice: A2 (P~0) and A6 (Sigma~) on n_pairs (q, k) pairs and 2 tau_half
+    tau points (every tau point is an independent batch of the same products);
+    the screened solve with its two transforms for one q; Hartree for one k and
+    the exchange term for one (k, k') pair; one electron count N(mu) (a Dyson
+    inversion at every (n, k) and a trace), the G(tau) transform and the Sigma~
+    transform.  Seconds per iteration = each part x (total units / sampled
+    units), with the mu search counted as the number of N(mu) evaluations the
+    oracle's bisection made on the state it was given.
     """
     import numpy as np
     from oracle import gw as ogw
     V = oracle_V(sysd)
-    if state is None:
-        state = ogw.State(dict(sysd, V=V))
-        state.dyson()
     st = state
     G, km, grid = st.G_tau, st.km, st.grid
-    nk = km.nk
+    nk, ntau = km.nk, G.shape[0]
+    ts = tau_subset(ntau, tau_half)
+    Gs = np.ascontiguousarray(G[ts])
     pairs = pair_list(nk, n_pairs, offset)
+    for q, k in pairs:                    # draw the V slabs the sample reads before the clock starts
+        for a, b in ((k, km.add(k, q)), (k, km.sub(k, q))):
+            V[a, b], V[b, a]
+    V[0, 0], V[pairs[0][0], pairs[0][1]], V[pairs[0][1], pairs[0][0]]
     t_p = t_s = 0.0
     P = {}
     for q, k in pairs:
         t0 = time.perf_counter()
-        P[q] = ogw.polarization_tau(V, G, km, qs=[q], ks=[k])[q]
+        P[q] = ogw.polarization_tau(V, Gs, km, qs=[q], ks=[k])[q]
         t_p += time.perf_counter() - t0
-    q0 = pairs[0][0]
-    t0 = time.perf_counter()
-    Piw = ogw.to_matsubara(grid.TFb, P[q0], 0)
-    Pt = {q0: ogw.herm(ogw.to_matsubara(grid.TBb, ogw.screened(Piw), 0))}
-    t_w = time.perf_counter() - t0
     for q, k in pairs:
         t0 = time.perf_counter()
-        ogw.selfenergy_tau(V, G, {q: Pt[q0]}, km, qs=[q], ks=[k])
+        ogw.selfenergy_tau(V, Gs, {q: P[q]}, km, qs=[q], ks=[k])
         t_s += time.perf_counter() - t0
+    # the screened solve of one q from a full-length P~0(tau) of that q
+    q0 = pairs[0][0]
+    P0q = np.zeros((ntau,) + P[q0].shape[1:], dtype=np.complex128)
+    P0q[ts] = P[q0]
+    t0 = time.perf_counter()
+    Piw = ogw.to_matsubara(grid.TFb, P0q, 0)
+    ogw.herm(ogw.to_matsubara(grid.TBb, ogw.screened(Piw), 0))
+    t_w = time.perf_counter() - t0
     t0 = time.perf_counter()
     gam = ogw.density_matrix(grid, G)
-    ogw.hartree(V, gam)
     t_j = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ogw.hartree(V, gam[:1])                 # the k = 0 term of the k' sum and row
+    t_j1 = time.perf_counter() - t0
     t0 = time.perf_counter()
     ogw.exchange(V, gam, kps=[pairs[0][1]], ks=[pairs[0][0]])
     t_k = time.perf_counter() - t0
     t0 = time.perf_counter()
+    Giw = ogw.dyson_inverse(grid, st.H0, st.S, st.Sigma_inf, st.Sigma_iw, st.mu)
+    ogw.electron_count(grid, st.S, Giw)
+    t_n = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ogw.green_tau(grid, Giw)
     ogw.to_matsubara(grid.TFf, G, 0)      # the Sigma~ transform (an array of Sigma~'s shape)
-    ogw.State(dict(sysd, V=V), grid=grid).dyson()
-    t_rest = time.perf_counter() - t0
+    t_tr = time.perf_counter() - t0
+    n_eval = st.mu_steps + 4              # bracket ends, first midpoint, bisection steps, final inversion
     npairs = len(pairs)
-    per_iter = (t_p + t_s) * (nk * nk) / npairs + t_w * nk + t_j + t_k * nk * nk + t_rest
+    t_pairs = (t_p + t_s) * (nk * nk) / npairs * (ntau / float(len(ts)))
+    t_hf = t_j + t_j1 * nk + t_k * nk * nk
+    t_rest = t_n * n_eval + t_tr
+    per_iter = t_pairs + t_w * nk + t_hf + t_rest
     cores = len(os.sched_getaffinity(0))
-    what = ("A2+A6 on %d of %d x %d (q, k) pairs, A4 with its transforms on 1 of %d q, exchange on 1 of %d x %d "
-            "(k, k') pairs, full Hartree, Sigma transform, mu search and Dyson" % (npairs, nk, nk, nk, nk, nk))
-    return per_iter, dict(cores=cores, parts_s=dict(pairs=t_p + t_s, screened=t_w, hf=t_j + t_k, rest=t_rest),
+    what = ("A2+A6 on %d of %d x %d (q, k) pairs and %d of %d tau points, A4 with its transforms on 1 of %d q, "
+            "Hartree on 1 of %d k, exchange on 1 of %d x %d (k, k') pairs, one N(mu) evaluation (scaled by the %d "
+            "inversions of the oracle's mu search and Dyson step), the G(tau) and Sigma~ transforms"
+            % (npairs, nk, nk, len(ts), ntau, nk, nk, nk, nk, n_eval))
+    return per_iter, dict(cores=cores, parts_s=dict(pairs=t_pairs, screened=t_w * nk, hf=t_hf, rest=t_rest),
                           sample="oracle (NumPy complex128): " + what + "; each part scaled by total/sampled units")
 
 
@@ -379,24 +419,26 @@ def gemm_timing(args):
 
 def run_reference(args):
     """The oracle (fp64 NumPy on the host cores) on the same workload: every step
-    times a bounded sample (one (q, k) pair of both contractions, one q of the
-    screened solve, one (k, k') pair of the exchange, the full q-independent rest)
-    and extrapolates it to one iteration."""
+    times a bounded sample (one (q, k) pair of both contractions on a tau subset,
+    one q of the screened solve, one k of Hartree, one (k, k') pair of the
+    exchange, one N(mu) evaluation and the transforms) and extrapolates it to one
+    iteration.  The oracle's G0 (its own mu search and Dyson step) is computed
+    once before the steps; its time is reported beside the sampled estimate of
+    the same q-independent rest."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import gw as ogw
     cfg, sysd = make_inputs(args.workload, kmesh=args.kmesh)
-    st = ogw.State(dict(sysd, V=oracle_V(sysd)))
-    st.dyson()
-    vals, walls = [], []
+    st, t_dyson = cpu_state(sysd)
+    vals, walls, rests = [], [], []
     info = None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        v, info = cpu_sample(cfg, sysd, 1, offset=i, state=st)
+        v, info = cpu_sample(cfg, sysd, st, 1, offset=i)
         if i >= args.warmup:
             vals.append(v)
             walls.append(time.perf_counter() - t0)
+            rests.append(info["parts_s"]["rest"])
     value = statistics.median(vals)
     ms_step = statistics.median(walls) * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/iteration",
@@ -406,6 +448,8 @@ def run_reference(args):
             "reference_note": "the CPU oracle (fp64 NumPy) on a bounded sample of the same workload per step; "
                               "value = the sample's time extrapolated to one full iteration (median over steps), "
                               "ms_per_step = the wall time of one sampled step",
+            "mu_search_and_dyson_s": {"full_once": t_dyson, "sampled_median": statistics.median(rests),
+                                      "mu_evaluations": st.mu_steps + 3},
             "cpu_baseline": {"value": value, "unit": "s/iteration", "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
             "e2e": {"value": value, "unit": "s/iteration", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -541,9 +585,9 @@ def run_gw(args):
     # sampled slices against the oracle (rank 0, single GPU): the mixed path's errors in Ha, and the
     # FP64 path's errors and its seconds per iteration extrapolated from one q
     extra = {}
+    st = None
     if rank == 0 and world == 1 and not args.no_slices:
-        st = ogw.State(dict(sysd, V=oracle_V(sysd)))
-        st.dyson()
+        st, _ = cpu_state(sysd)
         sl = slice_inputs(sysd, st)
         r_mixed = run_slices(g, sl, st.G_tau, torch)
         g.close()
@@ -626,7 +670,9 @@ def run_gw(args):
     if g is not None:
         g.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, info = cpu_sample(cfg, sysd, args.cpu_pairs)
+        if st is None:
+            st, _ = cpu_state(sysd)
+        v, info = cpu_sample(cfg, sysd, st, args.cpu_pairs)
         line["cpu_baseline"] = {"value": v, "unit": "s/iteration", "cores": info["cores"], "kind": "oracle",
                                 "sample": info["sample"]}
     if rank == 0:
@@ -699,7 +745,7 @@ def run_batch(args):
     if not args.no_cpu_baseline:
         tot, parts = 0.0, []
         for cfg, sysd in zip(cfgs, systems):
-            v, info = cpu_sample(cfg, sysd, 1)
+            v, info = cpu_sample(cfg, sysd, cpu_state(sysd)[0], 1)
             tot += v
         line["cpu_baseline"] = {"value": tot, "unit": "s/batch-iteration (16 systems)", "cores": info["cores"],
                                 "kind": "oracle", "sample": "per system: " + info["sample"] + "; summed"}
