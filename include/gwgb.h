@@ -404,6 +404,24 @@ gw_status gw_iterate_newton(gw_ctx* ctx, int32_t n_outer, int32_t m, double tol,
  * the final x.  Allocates 2m + 1 vectors of x's size on first use. */
 gw_status gw_iterate_diis(gw_ctx* ctx, int32_t n_iter, int32_t m, double mix, double tol, double* res_out);
 
+/* Dynamical part of the GW Luttinger-Ward functional (Sec. "Thermodynamics",
+ * Eq. tilde_Phi_GW):
+ *   Phi~ = 1/(2 Nk) sum_q (1/beta) sum_n tr{ln[I - P~0^q(i Omega_n)] + P~0^q(i Omega_n)},
+ * from the context's P~0(tau) (gw_polarization or gw_set of GW_Q_P0_TAU; GW_ERR_STATE
+ * otherwise), summed over the context's q range (gw_set_q_range: the ranks' values
+ * add up to Phi~).  The bosonic Matsubara sum is the grid's own: (1/beta) sum_n F =
+ * F(tau = beta^-) of the interpolant fitted at the sampled frequencies, i.e.
+ * sum_m w_m F(i Omega_m) with w = lb TBb (the construction of gamma = -G(beta^-));
+ * the real part is returned in *phi (host double).  P~0(i Omega_m) comes from
+ * P~0(tau) by the FP64 transform; tr ln(I - P~0) is the sum of the logarithms of
+ * the pivots of an FP64 LU factorisation without row exchanges, the continuous
+ * branch when the Hermitian part of I - P~0 is positive definite (a negative
+ * semidefinite polarization).  GW_ERR_SINGULAR for a zero pivot or one with
+ * non-positive real part.  naux <= 800 (GW_ERR_ARG otherwise).  Synchronises the
+ * context's stream; allocates a workspace of up to nq nwb naux^2 complex doubles
+ * for the duration of the call (GW_ERR_OOM when even one q does not fit). */
+gw_status gw_grand_potential(gw_ctx* ctx, double* phi);
+
 /* Allocation-free screened solve: P = [I - P0]^{-1} P0 for `count` complex
  * n x n matrices (interleaved (re, im) doubles, row-major, contiguous), the
  * operation of gw_screened without a context.  The paper has no counterpart;

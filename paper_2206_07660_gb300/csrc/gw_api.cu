@@ -2369,6 +2369,75 @@ extern "C" gw_status gw_load_state(gw_ctx* c, const char* path) {
   return GW_OK;
 }
 
+// ------------------------------------------------------------------ F4: Phi~ (Eq. tilde_Phi_GW)
+
+extern "C" gw_status gw_grand_potential(gw_ctx* c, double* phi) {
+  if (!c || !phi) return fail(c, GW_ERR_ARG, "null argument");
+  if (c->deferred) return fail(c, GW_ERR_STATE, "not available inside a captured iteration");
+  if (!(c->valid & qbit(GW_Q_P0_TAU))) return fail(c, GW_ERR_STATE, "no polarization P~0(tau) yet");
+  const int ntau = c->ntau, nwb = c->nwb, naux = c->naux;
+  const int64_t na2 = c->na2;
+  if (tracelog_panel(naux) == 0) return fail(c, GW_ERR_ARG, "naux too large for the trace-log kernel");
+  cudaStream_t st = c->st;
+  // Matsubara-sum weights w_m = sum_j lb_j TBb[j][m]
+  std::vector<double> lb((size_t)ntau);
+  std::vector<double2> TB((size_t)ntau * nwb);
+  CK(cudaMemcpyAsync(lb.data(), c->lb, (size_t)ntau * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(TB.data(), c->TBb, TB.size() * 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<double2> w((size_t)nwb, make_double2(0, 0));
+  for (int j = 0; j < ntau; ++j)
+    for (int m = 0; m < nwb; ++m) {
+      w[(size_t)m].x += lb[(size_t)j] * TB[(size_t)j * nwb + m].x;
+      w[(size_t)m].y += lb[(size_t)j] * TB[(size_t)j * nwb + m].y;
+    }
+  // P~0(i Omega) of a block of q per pass, factored in place
+  const int nq = c->q1 - c->q0;
+  const size_t per_q = (size_t)nwb * na2 * 16;
+  int64_t qb = (int64_t)(opt_budget((size_t)4 << 30) / per_q);
+  if (qb > nq) qb = nq;
+  if (qb < 1) qb = 1;
+  double2* ws = nullptr;
+  while (!(ws = (double2*)dalloc(c, (size_t)qb * per_q)) && qb > 1) qb /= 2;
+  double2* f = (double2*)dalloc(c, (size_t)nq * nwb * 16 + 16);
+  if (!ws || !f) {
+    dfree(c, ws); dfree(c, f);
+    return fail(c, GW_ERR_OOM, "no room for the trace-log workspace");
+  }
+  int* flag = (int*)(f + (size_t)nq * nwb);
+  gw_status s = GW_OK;
+  cudaError_t e = cudaMemsetAsync(flag, 0, 4, st);
+  for (int qa = c->q0; qa < c->q1 && e == cudaSuccess; qa += (int)qb) {
+    const int64_t nb = std::min<int64_t>(qb, c->q1 - qa);
+    e = transform(c, c->TFb, c->P0_tau + (size_t)qa * ntau * na2, ws, nwb, na2, nb, (int64_t)ntau * na2,
+                  (int64_t)nwb * na2);
+    if (e == cudaSuccess) {
+      e = lu_tracelog(ws, naux, nb * nwb, na2, f + (size_t)(qa - c->q0) * nwb, flag, st);
+      count(1);
+    }
+  }
+  std::vector<double2> fh((size_t)nq * nwb);
+  int hflag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(fh.data(), f, fh.size() * 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_scr, flag, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) memcpy(&hflag, c->h_scr, 4);
+  dfree(c, ws);
+  dfree(c, f);
+  if (e != cudaSuccess) return fail(c, GW_ERR_CUDA, cudaGetErrorString(e));
+  if (hflag & 1) return fail(c, GW_ERR_SINGULAR, "zero pivot in the trace-log of I - P~0");
+  if (hflag & 2)
+    return fail(c, GW_ERR_SINGULAR, "pivot with non-positive real part: I - P~0 is not positive definite");
+  double re = 0.0;
+  for (int q = 0; q < nq; ++q)
+    for (int m = 0; m < nwb; ++m) {
+      const double2 v = fh[(size_t)q * nwb + m], ww = w[(size_t)m];
+      re += ww.x * v.x - ww.y * v.y;
+    }
+  *phi = re / (2.0 * c->nk);
+  return s;
+}
+
 // Caps the number of k-points whose last P~0 step runs as one GEMM in contexts created
 // afterwards (0: no cap); returns the old cap.
 extern "C" int gwdbg_set_pgroup_cap(int cap) {

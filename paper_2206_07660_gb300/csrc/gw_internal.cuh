@@ -53,6 +53,11 @@ inline Idx2 I2(int64_t inner, int64_t s1, int64_t s0) { return Idx2{inner, s1, s
 
 // ------------------------------------------------------------------ other kernels
 cudaError_t herm_batched(double2* X, int64_t n, int64_t count, int64_t stride, cudaStream_t st);
+// out[m] = tr ln(I - A_m) + tr A_m for `count` n x n matrices A_m spaced `stride` apart
+// (overwritten), by FP64 LU without row exchanges; flag |= 1 (zero pivot), 2 (pivot with
+// non-positive real part).  tracelog_panel(n) == 0: n too large for the shared-memory panel.
+int tracelog_panel(int n);
+cudaError_t lu_tracelog(double2* A, int n, int64_t count, int64_t stride, double2* out, int* flag, cudaStream_t st);
 size_t grid_ws_bytes(int ntau, const int* fn_host, const int* bm_host, int* ld_out);
 cudaError_t grid_build_ws(int ntau, double beta, const int* d_fn, const int* d_bm, int ld, void* ws,
                           double* tau, double2* TFf, double2* TFb, double* lb, double* l0, cudaStream_t st);

@@ -84,6 +84,7 @@ def load():
     lib.gw_save_state.argtypes = [P, ctypes.c_char_p]
     lib.gw_load_state.argtypes = [P, ctypes.c_char_p]
     lib.gw_dyson.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.gw_grand_potential.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.gw_iterate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(GwIterStats)]
     lib.gw_last_error.argtypes = [P]
     lib.gw_last_error.restype = ctypes.c_char_p
@@ -316,6 +317,12 @@ class GW:
         mu = ctypes.c_double()
         self._check(self.lib.gw_dyson(self.ctx, ctypes.byref(mu)))
         return mu.value
+
+    def grand_potential(self):
+        """Phi~ of Eq. tilde_Phi_GW from the current P~0(tau), summed over the context's q range."""
+        phi = ctypes.c_double()
+        self._check(self.lib.gw_grand_potential(self.ctx, ctypes.byref(phi)))
+        return phi.value
 
     def reset_sigma(self):
         self._check(self.lib.gw_reset_sigma(self.ctx))
