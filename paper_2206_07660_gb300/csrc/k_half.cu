@@ -69,9 +69,29 @@ __device__ __forceinline__ double cabs2(double2 v) { return sqrt(v.x * v.x + v.y
 // row's max |re|, |im| (ex[r]); exs (optional) receives the exponent of the row's
 // sum of moduli (a bound of any product of the row with a vector of modulus <= 1).
 // One warp per row.
+// Kernels launched as programmatic dependents of the stream's previous kernel start
+// while it finishes and wait here for it to complete before touching memory.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, (KArgs)args...);
+}
+
 __global__ void __launch_bounds__(256) half_rows_kernel(const double2* __restrict__ src, int64_t rows, int64_t K,
                                                         int64_t ld, int conj, uint16_t* hi, uint16_t* lo,
                                                         int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs) {
+  dep_wait();
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= rows) return;
@@ -114,6 +134,7 @@ __global__ void __launch_bounds__(256) half_rows_kernel(const double2* __restric
 __global__ void __launch_bounds__(256) half_embed_conj_kernel(const double2* __restrict__ src, int64_t rows,
                                                               int64_t K, uint16_t* hi, uint16_t* lo, int64_t Kpad,
                                                               int64_t ldo, int fmt, const int* ex) {
+  dep_wait();
   const int64_t n = blockIdx.y;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= rows || 2 * c >= Kpad) return;
@@ -146,6 +167,7 @@ __global__ void __launch_bounds__(256) half_embed_conj_kernel(const double2* __r
 // e for the whole operand, transposed through shared memory.  Grid (N/32, K/32).
 __global__ void half_embed_t_kernel(const double2* __restrict__ src, int64_t K, int64_t N, uint16_t* hi, uint16_t* lo,
                                     int64_t Kpad, int fmt, int e, int64_t kin, int64_t kout) {
+  dep_wait();
   __shared__ double2 tile[32][33];
   const int64_t k0 = blockIdx.y * 32, nb = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -189,6 +211,7 @@ __global__ void half_embed_t_kernel(const double2* __restrict__ src, int64_t K, 
 __global__ void __launch_bounds__(256) half_embed_mats_kernel(const double2* __restrict__ src, int64_t ss, int64_t rows,
                                                               int64_t K, uint16_t* hi, uint16_t* lo, int64_t Kpad,
                                                               int64_t ds, int fmt, int plain, int* ex) {
+  dep_wait();
   __shared__ double red[8];
   const int64_t z = blockIdx.x;
   const double2* x = src + z * ss;
@@ -343,18 +366,16 @@ static inline unsigned nblk(int64_t rows, int per) {
 cudaError_t half_rows(const double2* src, int64_t rows, int64_t K, int64_t ld, bool conj, void* hi, void* lo,
                       int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs, cudaStream_t st) {
   if (Kpad % 64 || rows <= 0) return cudaErrorInvalidValue;
-  half_rows_kernel<<<nblk(rows, 8), 256, 0, st>>>(src, rows, K, ld, conj ? 1 : 0, (uint16_t*)hi, (uint16_t*)lo, Kpad,
-                                                   ldo > 0 ? ldo : Kpad, fmt, ex, exs);
-  return cudaGetLastError();
+  return launch_dep(half_rows_kernel, dim3(nblk(rows, 8)), dim3(256), st, src, rows, K, ld, conj ? 1 : 0, (uint16_t*)hi,
+                    (uint16_t*)lo, Kpad, ldo > 0 ? ldo : Kpad, fmt, ex, exs);
 }
 
 cudaError_t half_embed_conj(const double2* src, int64_t rows, int64_t K, void* hi, void* lo, int64_t Kpad,
                             int64_t ldo, int fmt, const int* ex, cudaStream_t st) {
   if (Kpad % 64 || rows <= 0 || rows > 65535) return cudaErrorInvalidValue;
   dim3 grid(nblk(Kpad / 2, 256), (unsigned)rows);
-  half_embed_conj_kernel<<<grid, 256, 0, st>>>(src, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad,
-                                               ldo > 0 ? ldo : Kpad, fmt, ex);
-  return cudaGetLastError();
+  return launch_dep(half_embed_conj_kernel, grid, dim3(256), st, src, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad,
+                    ldo > 0 ? ldo : Kpad, fmt, ex);
 }
 
 cudaError_t half_embed_t(const double2* src, int64_t K, int64_t N, void* hi, void* lo, int64_t Kpad, int fmt, int e,
@@ -362,16 +383,15 @@ cudaError_t half_embed_t(const double2* src, int64_t K, int64_t N, void* hi, voi
   if (Kpad % 64 || K <= 0 || N <= 0) return cudaErrorInvalidValue;
   if (kin > 0 && (K % kin || kout * kin != K)) return cudaErrorInvalidValue;   // a permutation of [0, K)
   dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32), 1);
-  half_embed_t_kernel<<<grid, 256, 0, st>>>(src, K, N, (uint16_t*)hi, (uint16_t*)lo, Kpad, fmt, e, kin, kout);
-  return cudaGetLastError();
+  return launch_dep(half_embed_t_kernel, grid, dim3(256), st, src, K, N, (uint16_t*)hi, (uint16_t*)lo, Kpad, fmt, e,
+                    kin, kout);
 }
 
 cudaError_t half_embed_mats(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, void* hi,
                             void* lo, int64_t Kpad, int64_t ds, int fmt, bool plain, int* ex, cudaStream_t st) {
   if (Kpad % 64 || count <= 0 || count > INT32_MAX) return cudaErrorInvalidValue;
-  half_embed_mats_kernel<<<(unsigned)count, 256, 0, st>>>(src, ss, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad, ds,
-                                                          fmt, plain ? 1 : 0, ex);
-  return cudaGetLastError();
+  return launch_dep(half_embed_mats_kernel, dim3((unsigned)count), dim3(256), st, src, ss, rows, K, (uint16_t*)hi,
+                    (uint16_t*)lo, Kpad, ds, fmt, plain ? 1 : 0, ex);
 }
 
 cudaError_t v_norms(const double2* V, int64_t nslab, int naux, int nao, float* vmax, float* vrs, cudaStream_t st) {

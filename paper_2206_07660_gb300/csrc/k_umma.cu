@@ -430,6 +430,9 @@ static int g_prefetch = 0;   // L2 prefetch distance in stages (0: off)
 static uint32_t g_spin = UM_SPIN_LIMIT;   // pipeline wait limit (test hook lowers it)
 static int g_wide = 1;       // autotuner may pick 160..256-column tiles (split 8-warp epilogue)
 static int g_force_bn = 0;   // test hook: nonzero forces this N tile (no tuning)
+// 1: the persistent kernel is launched as a programmatic dependent of the stream's previous
+// kernel (its setup overlaps that kernel's last blocks; it waits before touching memory)
+static int g_pdl = 1;
 
 // Writes one 32 x 32 block of a finished tile: lane l holds the row sums of
 // output row r0 + l in stg[l * 33 + j] (j = column - c0).  Rows are written
@@ -639,6 +642,10 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // launched as a programmatic dependent of the previous kernel on the stream, the block
+  // got here (barriers set up, TMEM held) while that kernel was still finishing; no
+  // global memory is touched before it has completed
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   // tile t -> (n tile, m tile, batch entry z, k range)
   auto decode = [&](int t, int& n0, int& m0, int& z, int& kb0, int& nkb) {
@@ -1100,7 +1107,18 @@ static cudaError_t launch_bn(const CUtensorMap* m, const UmmaArgs& a, int batch,
     const int64_t ntiles = (int64_t)ntn * ntm * batch * a.ksplit;
     if (ntiles > INT32_MAX) return cudaErrorInvalidValue;
     const int grid = (int)(ntiles < g_num_sms ? ntiles : g_num_sms);
-    umma_pkernel<BN, SPLIT><<<grid, UP_THREADS, sm, st>>>(m[0], m[1], m[2], m[3], a, ntn, ntm, (int)ntiles);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(UP_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, umma_pkernel<BN, SPLIT>, m[0], m[1], m[2], m[3], a, ntn, ntm, (int)ntiles);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   if constexpr (BN <= 128) {
