@@ -86,6 +86,11 @@ struct gw_ctx {
   // nao-sized steps on tensor cores: V slab split, doubled G(tau) per k, X hi/lo
   float *Vs_hi = nullptr, *Vs_lo = nullptr, *Ge_hi = nullptr, *Ge_lo = nullptr, *Xs_hi = nullptr, *Xs_lo = nullptr;
   float *Gp_hi = nullptr, *Gp_lo = nullptr;
+  // k-points per launch of the 16-bit chains (their per-k operands side by side) and the
+  // G blocks of k+q (or k-q) gathered in k order for such a launch
+  int pbatch = 1;
+  float *Gq_hi = nullptr, *Gq_lo = nullptr;
+  int* eGq = nullptr;
   int64_t kpadA = 0;
   size_t zbytes = 0;
   // 16-bit pieces (GW_SPLIT_F16 / GW_SPLIT_BF16): format (1 fp16, 2 bf16; 0 none), norms of V per Q
@@ -141,6 +146,7 @@ static constexpr bool kTensorSmallSteps = true;   // GW_SMALL_TENSOR / GW_SMALL_
 static constexpr int kRefineSteps = 2;
 static constexpr size_t kZGroupBytes = (size_t)8 << 30;
 static int g_pgroup_cap = 0;   // test hook: upper bound on the k-points per group (0: none)
+static int g_pbatch_cap = 0;   // test hook: upper bound on the k-points per chain launch (0: none)
 static constexpr size_t kRefineBytes = (size_t)6 << 30;
 
 #define CK(x)                                                                        \
@@ -235,7 +241,8 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
                             int64_t Kpad, int batch, void* C, bool c_fp64, double alpha, bool accumulate, int64_t c_ld,
                             int64_t c_zs, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
                             int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr,
-                            int64_t kvalid = 0, const UmmaScale* scale = nullptr, const UmmaOut* out = nullptr) {
+                            int64_t kvalid = 0, const UmmaScale* scale = nullptr, const UmmaOut* out = nullptr,
+                            const UmmaZ* zz = nullptr) {
   count(1);
   if (c->prof) {
     while (c->uev.size() < c->uused + 2) {
@@ -250,7 +257,7 @@ static cudaError_t run_umma(gw_ctx* c, double flops, const UmmaOperand& A, const
   // profiler can select exactly these launches
   nvtxRangePushA("contraction");
   cudaError_t r = umma_gemm(A, B, M, N, Kpad, batch, C, c_fp64, alpha, accumulate, c_ld, c_zs, 3, c->info + 1, c->st,
-                            ksplit, row_inner, row_s1, col_inner, col_s1, C_lo, scale, kvalid, out);
+                            ksplit, row_inner, row_s1, col_inner, col_s1, C_lo, scale, kvalid, out, zz);
   nvtxRangePop();
   if (c->prof) {
     cudaEventRecord(c->uev[c->uused + 1], c->st);
@@ -528,22 +535,39 @@ static gw_status init_impl(const gw_config* cfg, const gw_grid* grid, const doub
     }
     need(c->Zhi); need(c->Zlo); need(c->Vhi); need(c->Vlo);
     c->zbytes = zb;
+    // k-points per launch of the chains: enough output tiles for ~16 rounds of the SMs in the
+    // nao-sized steps (small systems put several (k, k+q) pairs into each GEMM); the per-k
+    // operand buffers below hold that many blocks
+    {
+      const int64_t tiles1 = ((int64_t)naux * nao + 127) / 128 * ntau;
+      int64_t kb = (16 * 152 + tiles1 - 1) / tiles1;
+      if (kb > kSrcListMax) kb = kSrcListMax;
+      if (kb > nk) kb = nk;
+      if (g_pbatch_cap > 0 && kb > g_pbatch_cap) kb = g_pbatch_cap;
+      c->pbatch = kb < 1 ? 1 : (int)kb;
+    }
+    const size_t kb = (size_t)c->pbatch;
     const size_t pb = (size_t)ntau * naux * c->kpadS * 2, tb = (size_t)2 * n2 * c->kpadS * 2;
     c->Pchi = (float*)need(A(pb)); c->Pclo = (float*)need(A(pb));
-    c->VThi = (float*)need(A(tb)); c->VTlo = (float*)need(A(tb));
+    c->VThi = (float*)need(A(kb * tb)); c->VTlo = (float*)need(A(kb * tb));
     const size_t vs = (size_t)naux * nao * c->kpadA * 2, ge = (size_t)nk * ntau * 2 * nao * c->kpadA * 2;
     const size_t xs = (size_t)ntau * naux * nao * c->kpadA * 2;
-    c->Vs_hi = (float*)need(A(vs)); c->Vs_lo = (float*)need(A(vs));
+    c->Vs_hi = (float*)need(A(kb * vs)); c->Vs_lo = (float*)need(A(kb * vs));
     c->Ge_hi = (float*)need(A(ge)); c->Ge_lo = (float*)need(A(ge));
     c->Gp_hi = (float*)need(A(ge)); c->Gp_lo = (float*)need(A(ge));
-    c->Xs_hi = (float*)need(A(xs)); c->Xs_lo = (float*)need(A(xs));
+    if (kb > 1) {
+      const size_t gq = kb * ntau * 2 * nao * c->kpadA * 2;
+      c->Gq_hi = (float*)need(A(gq)); c->Gq_lo = (float*)need(A(gq));
+      c->eGq = (int*)need(A(kb * ntau * 4));
+    }
+    c->Xs_hi = (float*)need(A(kb * xs)); c->Xs_lo = (float*)need(A(kb * xs));
     c->y3bytes = (size_t)ntau * nao * c->kpad3 * 2;
-    c->Y3hi = (float*)need(A(c->y3bytes)); c->Y3lo = (float*)need(A(c->y3bytes));
-    c->W3hi = (float*)need(A((size_t)2 * nao * c->kpad3 * 2)); c->W3lo = (float*)need(A((size_t)2 * nao * c->kpad3 * 2));
+    c->Y3hi = (float*)need(A(kb * c->y3bytes)); c->Y3lo = (float*)need(A(kb * c->y3bytes));
+    c->W3hi = (float*)need(A(kb * 2 * nao * c->kpad3 * 2)); c->W3lo = (float*)need(A(kb * 2 * nao * c->kpad3 * 2));
     c->vQmax = (float*)need(A((size_t)naux * 4)); c->vQrs = (float*)need(A((size_t)naux * 4));
     c->gn = (float*)need(A((size_t)4 * ntau * 4));
     c->eVQ = (int*)need(A((size_t)naux * 4)); c->eVall = (int*)need(A(16));
-    c->eV1 = (int*)need(A((size_t)naux * nao * 4));
+    c->eV1 = (int*)need(A(kb * naux * nao * 4));
     c->eY = (int*)need(A((size_t)ntau * naux * 4)); c->eZ = (int*)need(A((size_t)ntau * naux * 4));
     c->eGe = (int*)need(A((size_t)nk * ntau * 4)); c->eGp = (int*)need(A((size_t)nk * ntau * 4));
     c->ePc = (int*)need(A((size_t)ntau * naux * 4)); c->ePs = (int*)need(A((size_t)ntau * naux * 4));
@@ -661,9 +685,10 @@ static gw_status init_impl(const gw_config* cfg, const gw_grid* grid, const doub
     count(3);
     chk(cudaMemsetAsync(c->Zhi, 0, c->zbytes, st), "memset");
     chk(cudaMemsetAsync(c->Zlo, 0, c->zbytes, st), "memset");
-    chk(cudaMemsetAsync(c->Y3hi, 0, c->y3bytes, st), "memset");
-    chk(cudaMemsetAsync(c->Y3lo, 0, c->y3bytes, st), "memset");
-    const size_t xs = (size_t)ntau * naux * nao * c->kpadA * 2;
+    // the padding columns of the chain intermediates stay zero (every k block)
+    chk(cudaMemsetAsync(c->Y3hi, 0, (size_t)c->pbatch * c->y3bytes, st), "memset");
+    chk(cudaMemsetAsync(c->Y3lo, 0, (size_t)c->pbatch * c->y3bytes, st), "memset");
+    const size_t xs = (size_t)c->pbatch * ntau * naux * nao * c->kpadA * 2;
     chk(cudaMemsetAsync(c->Xs_hi, 0, xs, st), "memset");
     chk(cudaMemsetAsync(c->Xs_lo, 0, xs, st), "memset");
   }
@@ -1056,49 +1081,71 @@ static gw_status polar_chain_half(gw_ctx* c, const double2* Gplus, const double2
   }
   count(2 * nk);
   const double fl12 = 8.0 * ntau * naux * (double)nao * n2;
+  // k-points per launch: several (k, k+q) pairs of small systems share each GEMM
+  // (batch entry z = (k, t)), whole groups of the last step at most
+  const int KB = c->pbatch < G ? c->pbatch : G;
+  const int64_t vs_blk = (int64_t)naux * nao * ka, xs_blk = (int64_t)ntau * naux * nao * ka;
   for (int q = c->q0; q < c->q1; ++q) {
     if (c->reduce && c->kneg[(size_t)q] < q) continue;   // the conjugate of P~0^{-q}
     double2* Pq = out + (size_t)q * ntau * c->na2;
-    for (int k = 0; k < nk; ++k) {
-      const int kq = c->kplus[(size_t)q * nk + k];
-      const int j = k % G;
-      const double2* Vkq = c->V + ((size_t)k * nk + kq) * slab;
-      // Y: A = V^{k,k+q} rows (Q, d) with exact row exponents, B = Ge[k+q][t]
-      CK(half_rows(Vkq, (int64_t)naux * nao, nao, nao, false, c->Vs_hi, c->Vs_lo, ka, ka, fmt, c->eV1, nullptr, st));
-      count(1);
-      {
-        UmmaOperand oa{c->Vs_hi, c->Vs_lo, (int64_t)naux * nao, 1, ka, 0, fmt};
-        UmmaOperand ob{hofs(c->Ge_hi, (int64_t)kq * ntau * per), hofs(c->Ge_lo, (int64_t)kq * ntau * per),
-                       2 * (int64_t)nao, ntau, ka, per, fmt};
-        UmmaScale sc{c->eV1, c->eGe + (size_t)kq * ntau, 0, 1, 0, 1, kAll};
-        UmmaOut o{fmt, c->eY, naux, nao, 0};
-        CK(run_umma(c, fl12, oa, ob, naux * nao, 2 * nao, ka, ntau, c->Xs_hi, false, 1.0, false, 2,
-                    (int64_t)naux * nao * ka, 1, nao, (int64_t)nao * ka, 2, ka, c->Xs_lo, 2 * (int64_t)nao, &sc, &o));
+    for (int g0 = 0; g0 < nk; g0 += G) {
+      const int gn = nk - g0 < G ? nk - g0 : G;
+      for (int b0 = 0; b0 < gn; b0 += KB) {
+        const int kn = gn - b0 < KB ? gn - b0 : KB, k0 = g0 + b0;
+        int64_t voff[kSrcListMax];
+        int kq[kSrcListMax];
+        for (int l = 0; l < kn; ++l) {
+          kq[l] = c->kplus[(size_t)q * nk + k0 + l];
+          voff[l] = ((int64_t)(k0 + l) * nk + kq[l]) * slab;
+        }
+        // Y: A = V^{k,k+q} rows (Q, d) with exact row exponents, B = Ge[k+q][t]
+        CK(half_rows_multi(c->V, voff, kn, (int64_t)naux * nao, nao, nao, false, c->Vs_hi, c->Vs_lo, ka, ka, vs_blk,
+                           fmt, c->eV1, nullptr, (int64_t)naux * nao, st));
+        count(1);
+        const void *gbh = hofs(c->Ge_hi, (int64_t)kq[0] * ntau * per), *gbl = hofs(c->Ge_lo, (int64_t)kq[0] * ntau * per);
+        const int* gbe = c->eGe + (size_t)kq[0] * ntau;
+        if (kn > 1) {   // the blocks of G^{k+q} in k order
+          CK(gather_blocks(c->Ge_hi, c->Ge_lo, c->eGe, c->Gq_hi, c->Gq_lo, c->eGq, (int64_t)ntau * per * 2, ntau, kq, kn,
+                           st));
+          count(1);
+          gbh = c->Gq_hi; gbl = c->Gq_lo; gbe = c->eGq;
+        }
+        {
+          UmmaOperand oa{c->Vs_hi, c->Vs_lo, (int64_t)naux * nao, kn, ka, vs_blk, fmt};
+          UmmaOperand ob{(const float*)gbh, (const float*)gbl, 2 * (int64_t)nao, (int64_t)kn * ntau, ka, per, fmt};
+          UmmaScale sc{c->eV1, gbe, 0, 1, 0, 1, kAll};
+          UmmaOut o{fmt, c->eY, naux, nao, 0};
+          // z = (k, t): A and the row exponents per k, B and its exponents per (k, t), Y blocks per (k, t)
+          UmmaZ zz{ntau, 1, 0, ntau, 1, (int64_t)naux * nao, ntau, 0, xs_blk};
+          CK(run_umma(c, fl12 * kn, oa, ob, naux * nao, 2 * nao, ka, kn * ntau, c->Xs_hi, false, 1.0, false, 2,
+                      (int64_t)naux * nao * ka, 1, nao, (int64_t)nao * ka, 2, ka, c->Xs_lo, 2 * (int64_t)nao, &sc, &o,
+                      kn > 1 ? &zz : nullptr));
+        }
+        // Z: A = Y^T rows (Q, b) per (k, t) (exponent per (t, Q)), B = Gp[k][t]; written into
+        // the (c, b) columns of blocks b0.. of the grouped last step's A operand
+        {
+          UmmaOperand ya{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, (int64_t)kn * ntau, ka, (int64_t)naux * nao * ka, fmt};
+          UmmaOperand gb{hofs(c->Gp_hi, (int64_t)k0 * ntau * per), hofs(c->Gp_lo, (int64_t)k0 * ntau * per),
+                         2 * (int64_t)nao, (int64_t)kn * ntau, ka, per, fmt};
+          UmmaScale sc{c->eY, c->eGp + (size_t)k0 * ntau, naux, 1, 0, nao, kAll};
+          UmmaOut o{fmt, c->eZ, naux, nao, 0};
+          UmmaZ zz{ntau, ntau, 1, ntau, 1, 0, ntau, 0, kp};
+          CK(run_umma(c, fl12 * kn, ya, gb, naux * nao, 2 * nao, ka, kn * ntau, hofs(c->Zhi, b0 * kp), false, -1.0, false,
+                      2, (int64_t)naux * zld, 1, nao, zld, 2, 2 * (int64_t)nao, hofs(c->Zlo, b0 * kp),
+                      2 * (int64_t)nao, &sc, &o, kn > 1 ? &zz : nullptr));
+        }
+        // embedded conj V^{k,k+q}(Q') rows with the per-Q exponents shared by the group
+        CK(half_embed_conj_multi(c->V, voff, kn, naux, n2, hofs(c->Vhi, b0 * kp), hofs(c->Vlo, b0 * kp), kp, zld, kp,
+                                 fmt, c->eVQ, st));
+        count(1);
       }
-      // Z: A = Y^T rows (Q, b) per t (exponent per (t, Q)), B = Gp[k][t]; written into the
-      // (c, b) columns of block j of the grouped last step's A operand
-      {
-        UmmaOperand ya{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka, fmt};
-        UmmaOperand gb{hofs(c->Gp_hi, (int64_t)k * ntau * per), hofs(c->Gp_lo, (int64_t)k * ntau * per),
-                       2 * (int64_t)nao, ntau, ka, per, fmt};
-        UmmaScale sc{c->eY, c->eGp + (size_t)k * ntau, naux, 1, 0, nao, kAll};
-        UmmaOut o{fmt, c->eZ, naux, nao, 0};
-        CK(run_umma(c, fl12, ya, gb, naux * nao, 2 * nao, ka, ntau, hofs(c->Zhi, j * kp), false, -1.0, false, 2,
-                    (int64_t)naux * zld, 1, nao, zld, 2, 2 * (int64_t)nao, hofs(c->Zlo, j * kp), 2 * (int64_t)nao, &sc,
-                    &o));
-      }
-      // embedded conj V^{k,k+q}(Q') rows with the per-Q exponents shared by the group
-      CK(half_embed_conj(Vkq, naux, n2, hofs(c->Vhi, j * kp), hofs(c->Vlo, j * kp), kp, zld, fmt, c->eVQ, st));
-      count(1);
-      if (j == G - 1 || k == nk - 1) {
-        const int g = j + 1, k0 = k - j;
-        UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, zld, 0, fmt};
-        UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, zld, 0, fmt};
-        UmmaScale sc{c->eZ, c->eVQ, 0, 0, 0, 1, 1};
-        CK(run_umma(c, 8.0 * g * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, g * kp, 1, Pq, true,
-                    c->spin / nk, accumulate || k0 > 0, 2 * (int64_t)naux, 0, 1, 0, 0, 0, 0, nullptr,
-                    (g - 1) * kp + 2 * n2, &sc, nullptr));
-      }
+      const int g = gn;
+      UmmaOperand oa{c->Zhi, c->Zlo, (int64_t)ntau * naux, 1, zld, 0, fmt};
+      UmmaOperand ob{c->Vhi, c->Vlo, 2 * (int64_t)naux, 1, zld, 0, fmt};
+      UmmaScale sc{c->eZ, c->eVQ, 0, 0, 0, 1, 1};
+      CK(run_umma(c, 8.0 * g * ntau * naux * (double)naux * n2, oa, ob, ntau * naux, 2 * naux, g * kp, 1, Pq, true,
+                  c->spin / nk, accumulate || g0 > 0, 2 * (int64_t)naux, 0, 1, 0, 0, 0, 0, nullptr,
+                  (g - 1) * kp + 2 * n2, &sc, nullptr));
     }
   }
   return GW_OK;
@@ -1130,9 +1177,11 @@ static gw_status sigma_chain_half(gw_ctx* c, const double2* Gsrc, const double2*
   count(nk);
   const double fl1 = 8.0 * ntau * naux * (double)naux * n2, fl2 = 8.0 * ntau * naux * (double)nao * n2;
   const int64_t mt = ((int64_t)ntau * nao + 127) / 128, nt = (2 * (int64_t)nao + 159) / 160;
-  int64_t ks = (304 + mt * nt - 1) / (mt * nt);
-  if (ks > kp3 / 64) ks = kp3 / 64;
-  if (ks < 1) ks = 1;
+  const int KB = c->pbatch;
+  const int64_t xs_blk = (int64_t)ntau * naux * nao * ka, y3_blk = (int64_t)ntau * nao * kp3;
+  const int64_t vt_blk = 2 * n2 * kps, w3_blk = 2 * (int64_t)nao * kp3;
+  std::vector<int> act;
+  act.reserve((size_t)nk);
   for (int q = c->q0; q < c->q1; ++q) {
     // A operand of the first step: conj P~^q(t) rows (t, Q') with exact row exponents and
     // the exponents of their sums of moduli; then Y's exponent per t
@@ -1140,45 +1189,70 @@ static gw_status sigma_chain_half(gw_ctx* c, const double2* Gsrc, const double2*
                  c->ePc, c->ePs, st));
     CK(sigma_exps(c->ePs, shift, c->gn + ntau, ntau, naux, c->eY3, st));
     count(2);
-    for (int k = 0; k < nk; ++k) {
-      if (c->reduce && c->kneg[(size_t)k] < k) continue;   // the conjugate of Sigma~^{-k}
-      const int kmq = c->kminus[(size_t)q * nk + k];
+    act.clear();
+    for (int k = 0; k < nk; ++k)
+      if (!(c->reduce && c->kneg[(size_t)k] < k)) act.push_back(k);   // else the conjugate of Sigma~^{-k}
+    for (size_t b0 = 0; b0 < act.size();) {
+      // a run of consecutive k (their Sigma~^k blocks are equally spaced), KB at most
+      int kn = 1;
+      while (kn < KB && b0 + kn < act.size() && act[b0 + kn] == act[b0] + kn) ++kn;
+      const int k0 = act[b0];
+      b0 += kn;
+      int64_t voffX[kSrcListMax], voffW[kSrcListMax];
+      int kmq[kSrcListMax];
+      for (int l = 0; l < kn; ++l) {
+        kmq[l] = c->kminus[(size_t)q * nk + k0 + l];
+        voffX[l] = ((int64_t)(k0 + l) * nk + kmq[l]) * slab;
+        voffW[l] = ((int64_t)kmq[l] * nk + k0 + l) * slab;
+      }
       // X = conj(P~) V: B = V^{k,k-q} transposed, rows (i, a), K = Q, one exponent
-      CK(half_embed_t(c->V + ((size_t)k * nk + kmq) * slab, naux, n2, c->VThi, c->VTlo, kps, fmt, c->h_Evmax - 15, st));
+      CK(half_embed_t_multi(c->V, voffX, kn, naux, n2, c->VThi, c->VTlo, kps, vt_blk, fmt, c->h_Evmax - 15, st));
       count(1);
       {
         UmmaOperand oa{c->Pchi, c->Pclo, (int64_t)ntau * naux, 1, kps, 0, fmt};
-        UmmaOperand ob{c->VThi, c->VTlo, 2 * n2, 1, kps, 0, fmt};
+        UmmaOperand ob{c->VThi, c->VTlo, 2 * n2, kn, kps, vt_blk, fmt};
         UmmaScale sc{c->ePc, c->eVall, 0, 0, 0, 1, kAll};
         UmmaOut o{fmt, c->ePs, 0, 1, shift};
-        // output row (t, Q'), column (i, a re/im) -> X row (t, i, Q'), entry (a re/im)
-        CK(run_umma(c, fl1, oa, ob, ntau * naux, (int)(2 * n2), kps, 1, c->Xs_hi, false, 1.0, false, ka, 0, 1, naux,
-                    (int64_t)nao * naux * ka, 2 * (int64_t)nao, (int64_t)naux * ka, c->Xs_lo, 2 * (int64_t)naux, &sc,
-                    &o));
+        // output row (t, Q'), column (i, a re/im) -> X row (t, i, Q'), entry (a re/im); one X block per k
+        CK(run_umma(c, fl1 * kn, oa, ob, ntau * naux, (int)(2 * n2), kps, kn, c->Xs_hi, false, 1.0, false, ka,
+                    kn > 1 ? xs_blk : 0, 1, naux, (int64_t)nao * naux * ka, 2 * (int64_t)nao, (int64_t)naux * ka,
+                    c->Xs_lo, 2 * (int64_t)naux, &sc, &o));
       }
-      // Y = X G^{k-q}(t): A rows (i, Q') per t (exponent of row Q'), B = Ge[k-q][t]; row (i, Q'),
+      // Y = X G^{k-q}(t): A rows (i, Q') per (k, t) (exponent of row Q'), B = Ge[k-q][t]; row (i, Q'),
       // column (b re/im) lands at row (t, i), K entry (b, Q') of the last step's operand
       {
-        UmmaOperand xa{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, ntau, ka, (int64_t)naux * nao * ka, fmt};
-        UmmaOperand gb{hofs(c->Ge_hi, (int64_t)kmq * ntau * per), hofs(c->Ge_lo, (int64_t)kmq * ntau * per),
-                       2 * (int64_t)nao, ntau, ka, per, fmt};
-        UmmaScale sc{c->ePs, c->eGe + (size_t)kmq * ntau, naux, 1, shift, 1, kAll};
+        const void *gbh = hofs(c->Ge_hi, (int64_t)kmq[0] * ntau * per), *gbl = hofs(c->Ge_lo, (int64_t)kmq[0] * ntau * per);
+        const int* gbe = c->eGe + (size_t)kmq[0] * ntau;
+        if (kn > 1) {
+          CK(gather_blocks(c->Ge_hi, c->Ge_lo, c->eGe, c->Gq_hi, c->Gq_lo, c->eGq, (int64_t)ntau * per * 2, ntau, kmq,
+                           kn, st));
+          count(1);
+          gbh = c->Gq_hi; gbl = c->Gq_lo; gbe = c->eGq;
+        }
+        UmmaOperand xa{c->Xs_hi, c->Xs_lo, (int64_t)naux * nao, (int64_t)kn * ntau, ka, (int64_t)naux * nao * ka, fmt};
+        UmmaOperand gb{(const float*)gbh, (const float*)gbl, 2 * (int64_t)nao, (int64_t)kn * ntau, ka, per, fmt};
+        UmmaScale sc{c->ePs, gbe, naux, 1, shift, 1, kAll};
         sc.ea_mod = naux;
         UmmaOut o{fmt, c->eY3, 1, kAll, 0};
-        CK(run_umma(c, fl2, xa, gb, naux * nao, 2 * nao, ka, ntau, c->Y3hi, false, 1.0, false, 2,
-                    (int64_t)nao * kp3, 1, naux, kp3, 2, 2 * (int64_t)naux, c->Y3lo, 2 * (int64_t)nao, &sc, &o));
+        UmmaZ zz{ntau, ntau, 1, ntau, 1, 0, ntau, 0, y3_blk};
+        CK(run_umma(c, fl2 * kn, xa, gb, naux * nao, 2 * nao, ka, kn * ntau, c->Y3hi, false, 1.0, false, 2,
+                    (int64_t)nao * kp3, 1, naux, kp3, 2, 2 * (int64_t)naux, c->Y3lo, 2 * (int64_t)nao, &sc, &o,
+                    kn > 1 ? &zz : nullptr));
       }
       // Sigma~ += -(1/Nk) Y V^{k-q,k}: B = V^{k-q,k} transposed, rows j, K = (b, Q') (source rows (Q', b))
-      CK(half_embed_t(c->V + ((size_t)kmq * nk + k) * slab, (int64_t)naux * nao, nao, c->W3hi, c->W3lo, kp3, fmt,
-                      c->h_Evmax - 15, st, nao, naux));
+      CK(half_embed_t_multi(c->V, voffW, kn, (int64_t)naux * nao, nao, c->W3hi, c->W3lo, kp3, w3_blk, fmt,
+                            c->h_Evmax - 15, st, nao, naux));
       count(1);
       {
-        UmmaOperand ya{c->Y3hi, c->Y3lo, (int64_t)ntau * nao, 1, kp3, 0, fmt};
-        UmmaOperand wb{c->W3hi, c->W3lo, 2 * (int64_t)nao, 1, kp3, 0, fmt};
+        int64_t ks = (304 + mt * nt * kn - 1) / (mt * nt * kn);
+        if (ks > kp3 / 64) ks = kp3 / 64;
+        if (ks < 1) ks = 1;
+        UmmaOperand ya{c->Y3hi, c->Y3lo, (int64_t)ntau * nao, kn, kp3, y3_blk, fmt};
+        UmmaOperand wb{c->W3hi, c->W3lo, 2 * (int64_t)nao, kn, kp3, w3_blk, fmt};
         UmmaScale sc{c->eY3, c->eVall, 0, 0, 0, nao, kAll};
-        CK(run_umma(c, fl2, ya, wb, ntau * nao, 2 * nao, kp3, 1, (double*)(out + (size_t)k * n2), true, -1.0 / nk, true,
-                    2 * (int64_t)nao, 0, (int)ks, nao, 2 * gstep, 0, 0, nullptr, 2 * (int64_t)naux * nao, &sc,
-                    nullptr));
+        CK(run_umma(c, fl2 * kn, ya, wb, ntau * nao, 2 * nao, kp3, kn, (double*)(out + (size_t)k0 * n2), true,
+                    -1.0 / nk, true, 2 * (int64_t)nao, 2 * n2, (int)ks, nao, 2 * gstep, 0, 0, nullptr,
+                    2 * (int64_t)naux * nao, &sc, nullptr));
       }
     }
   }
@@ -2436,6 +2510,14 @@ extern "C" gw_status gw_grand_potential(gw_ctx* c, double* phi) {
     }
   *phi = re / (2.0 * c->nk);
   return s;
+}
+
+// Caps the number of k-points per launch of the 16-bit chains in contexts created
+// afterwards (0: no cap); returns the old cap.
+extern "C" int gwdbg_set_pbatch_cap(int cap) {
+  const int old = g_pbatch_cap;
+  g_pbatch_cap = cap < 0 ? 0 : cap;
+  return old;
 }
 
 // Caps the number of k-points whose last P~0 step runs as one GEMM in contexts created

@@ -132,6 +132,26 @@ struct BsmDesc {
 cudaError_t bsm(const BsmDesc& d, cudaStream_t st);
 
 // ------------------------------------------------------------------ tensor-core split-TF32 GEMM
+// Source matrices of one batched operand-preparation launch: entry i reads at src + off[i]
+// (complex elements) and writes its output block i (up to kSrcListMax entries).
+constexpr int kSrcListMax = 32;
+struct SrcList {
+  int n;
+  int64_t off[kSrcListMax];
+};
+// copies n blocks (block_bytes of hi and of lo pieces, ecount exponents each) from block
+// indices idx[i] of the sources into consecutive blocks of the destinations
+cudaError_t gather_blocks(const void* shi, const void* slo, const int* se, void* dhi, void* dlo, int* de,
+                          int64_t block_bytes, int64_t ecount, const int* idx, int n, cudaStream_t st);
+cudaError_t half_rows_multi(const double2* src, const int64_t* offs, int n, int64_t rows, int64_t K, int64_t ld,
+                            bool conj, void* hi, void* lo, int64_t Kpad, int64_t ldo, int64_t dstride, int fmt,
+                            int* ex, int* exs, int64_t estride, cudaStream_t st);
+cudaError_t half_embed_conj_multi(const double2* src, const int64_t* offs, int n, int64_t rows, int64_t K, void* hi,
+                                  void* lo, int64_t Kpad, int64_t ldo, int64_t dstride, int fmt, const int* ex,
+                                  cudaStream_t st);
+cudaError_t half_embed_t_multi(const double2* src, const int64_t* offs, int n, int64_t K, int64_t N, void* hi,
+                               void* lo, int64_t Kpad, int64_t dstride, int fmt, int e, cudaStream_t st,
+                               int64_t kin = 0, int64_t kout = 0);
 struct UmmaOperand {
   const float* hi;
   const float* lo;
@@ -166,11 +186,21 @@ struct UmmaOut {
   int64_t eo_zs, eo_div;
   int eo_shift;
 };
+// Two-level batches (several k-points of a chain step in one launch): batch entry
+// z = zo * zin + zi; the TMA batch coordinate of A is zo * za_o + zi * za_i (B likewise),
+// and the exponent and output strides of the other arguments (ea_zs, eb_zs, eo_zs, c_zs)
+// apply to zi while ea_zso, eb_zso, eo_zso, c_zso apply to zo.
+struct UmmaZ {
+  int zin;
+  int za_o, za_i, zb_o, zb_i;
+  int64_t ea_zso, eb_zso, eo_zso, c_zso;
+};
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit = 1, int64_t row_inner = 0, int64_t row_s1 = 0,
                       int64_t col_inner = 0, int64_t col_s1 = 0, float* C_lo = nullptr,
-                      const UmmaScale* scale = nullptr, int64_t kvalid = 0, const UmmaOut* out = nullptr);
+                      const UmmaScale* scale = nullptr, int64_t kvalid = 0, const UmmaOut* out = nullptr,
+                      const UmmaZ* zz = nullptr);
 // FP64 complex products on tensor cores by exact digit splitting (k_emul.cu)
 int64_t emul_kpad(int64_t K);
 size_t emul_digit_bytes(int64_t rows, int64_t K);

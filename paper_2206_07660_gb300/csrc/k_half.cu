@@ -90,8 +90,15 @@ static cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, c
 
 __global__ void __launch_bounds__(256) half_rows_kernel(const double2* __restrict__ src, int64_t rows, int64_t K,
                                                         int64_t ld, int conj, uint16_t* hi, uint16_t* lo,
-                                                        int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs) {
+                                                        int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs,
+                                                        const __grid_constant__ SrcList list, int64_t dstride, int64_t estride) {
   dep_wait();
+  // matrix blockIdx.y of the list: its source offset, its output and exponent blocks
+  src += list.off[blockIdx.y];
+  hi += blockIdx.y * dstride;
+  lo += blockIdx.y * dstride;
+  ex += blockIdx.y * estride;
+  if (exs) exs += blockIdx.y * estride;
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= rows) return;
@@ -133,8 +140,12 @@ __global__ void __launch_bounds__(256) half_rows_kernel(const double2* __restric
 // exponent ex[n] of each complex row.  Grid (column blocks of 256 complex entries, rows).
 __global__ void __launch_bounds__(256) half_embed_conj_kernel(const double2* __restrict__ src, int64_t rows,
                                                               int64_t K, uint16_t* hi, uint16_t* lo, int64_t Kpad,
-                                                              int64_t ldo, int fmt, const int* ex) {
+                                                              int64_t ldo, int fmt, const int* ex,
+                                                              const __grid_constant__ SrcList list, int64_t dstride) {
   dep_wait();
+  src += list.off[blockIdx.z];
+  hi += blockIdx.z * dstride;
+  lo += blockIdx.z * dstride;
   const int64_t n = blockIdx.y;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= rows || 2 * c >= Kpad) return;
@@ -166,8 +177,12 @@ __global__ void __launch_bounds__(256) half_embed_conj_kernel(const double2* __r
 // stride N): rows 2n = (re, -im), 2n+1 = (im, re) of 16-bit pieces with one exponent
 // e for the whole operand, transposed through shared memory.  Grid (N/32, K/32).
 __global__ void half_embed_t_kernel(const double2* __restrict__ src, int64_t K, int64_t N, uint16_t* hi, uint16_t* lo,
-                                    int64_t Kpad, int fmt, int e, int64_t kin, int64_t kout) {
+                                    int64_t Kpad, int fmt, int e, int64_t kin, int64_t kout, const __grid_constant__ SrcList list,
+                                    int64_t dstride) {
   dep_wait();
+  src += list.off[blockIdx.z];
+  hi += blockIdx.z * dstride;
+  lo += blockIdx.z * dstride;
   __shared__ double2 tile[32][33];
   const int64_t k0 = blockIdx.y * 32, nb = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -361,13 +376,58 @@ static inline unsigned nblk(int64_t rows, int per) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
+// Gathers n blocks of 16-bit pieces (hi and lo planes, `words` 16-byte words each) and
+// their exponents (ecount each) from block indices list.off[i] into consecutive blocks.
+__global__ void __launch_bounds__(256) gather_blocks_kernel(const uint4* __restrict__ shi, const uint4* __restrict__ slo,
+                                                            const int* __restrict__ se, uint4* dhi, uint4* dlo, int* de,
+                                                            int64_t words, int64_t ecount, const __grid_constant__ SrcList list) {
+  dep_wait();
+  const int64_t i = blockIdx.y, src = list.off[i];
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
+    dhi[i * words + w] = shi[src * words + w];
+    dlo[i * words + w] = slo[src * words + w];
+  }
+  if (blockIdx.x == 0)
+    for (int64_t e = threadIdx.x; e < ecount; e += blockDim.x) de[i * ecount + e] = se[src * ecount + e];
+}
+
 // ------------------------------------------------------------------ launch wrappers
+
+static SrcList one_src() {
+  SrcList l{};
+  l.n = 1;
+  return l;
+}
+
+cudaError_t half_rows_multi(const double2* src, const int64_t* offs, int n, int64_t rows, int64_t K, int64_t ld,
+                            bool conj, void* hi, void* lo, int64_t Kpad, int64_t ldo, int64_t dstride, int fmt,
+                            int* ex, int* exs, int64_t estride, cudaStream_t st) {
+  if (Kpad % 64 || rows <= 0 || n < 1 || n > kSrcListMax) return cudaErrorInvalidValue;
+  SrcList l{};
+  l.n = n;
+  for (int i = 0; i < n; ++i) l.off[i] = offs ? offs[i] : 0;
+  return launch_dep(half_rows_kernel, dim3(nblk(rows, 8), (unsigned)n), dim3(256), st, src, rows, K, ld,
+                    conj ? 1 : 0, (uint16_t*)hi, (uint16_t*)lo, Kpad, ldo > 0 ? ldo : Kpad, fmt, ex, exs, l, dstride,
+                    estride);
+}
 
 cudaError_t half_rows(const double2* src, int64_t rows, int64_t K, int64_t ld, bool conj, void* hi, void* lo,
                       int64_t Kpad, int64_t ldo, int fmt, int* ex, int* exs, cudaStream_t st) {
   if (Kpad % 64 || rows <= 0) return cudaErrorInvalidValue;
   return launch_dep(half_rows_kernel, dim3(nblk(rows, 8)), dim3(256), st, src, rows, K, ld, conj ? 1 : 0, (uint16_t*)hi,
-                    (uint16_t*)lo, Kpad, ldo > 0 ? ldo : Kpad, fmt, ex, exs);
+                    (uint16_t*)lo, Kpad, ldo > 0 ? ldo : Kpad, fmt, ex, exs, one_src(), (int64_t)0, (int64_t)0);
+}
+
+cudaError_t half_embed_conj_multi(const double2* src, const int64_t* offs, int n, int64_t rows, int64_t K, void* hi,
+                                  void* lo, int64_t Kpad, int64_t ldo, int64_t dstride, int fmt, const int* ex,
+                                  cudaStream_t st) {
+  if (Kpad % 64 || rows <= 0 || rows > 65535 || n < 1 || n > kSrcListMax) return cudaErrorInvalidValue;
+  SrcList l{};
+  l.n = n;
+  for (int i = 0; i < n; ++i) l.off[i] = offs ? offs[i] : 0;
+  dim3 grid(nblk(Kpad / 2, 256), (unsigned)rows, (unsigned)n);
+  return launch_dep(half_embed_conj_kernel, grid, dim3(256), st, src, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad,
+                    ldo > 0 ? ldo : Kpad, fmt, ex, l, dstride);
 }
 
 cudaError_t half_embed_conj(const double2* src, int64_t rows, int64_t K, void* hi, void* lo, int64_t Kpad,
@@ -375,7 +435,20 @@ cudaError_t half_embed_conj(const double2* src, int64_t rows, int64_t K, void* h
   if (Kpad % 64 || rows <= 0 || rows > 65535) return cudaErrorInvalidValue;
   dim3 grid(nblk(Kpad / 2, 256), (unsigned)rows);
   return launch_dep(half_embed_conj_kernel, grid, dim3(256), st, src, rows, K, (uint16_t*)hi, (uint16_t*)lo, Kpad,
-                    ldo > 0 ? ldo : Kpad, fmt, ex);
+                    ldo > 0 ? ldo : Kpad, fmt, ex, one_src(), (int64_t)0);
+}
+
+cudaError_t half_embed_t_multi(const double2* src, const int64_t* offs, int n, int64_t K, int64_t N, void* hi,
+                               void* lo, int64_t Kpad, int64_t dstride, int fmt, int e, cudaStream_t st, int64_t kin,
+                               int64_t kout) {
+  if (Kpad % 64 || K <= 0 || N <= 0 || n < 1 || n > kSrcListMax) return cudaErrorInvalidValue;
+  if (kin > 0 && (K % kin || kout * kin != K)) return cudaErrorInvalidValue;   // a permutation of [0, K)
+  SrcList l{};
+  l.n = n;
+  for (int i = 0; i < n; ++i) l.off[i] = offs ? offs[i] : 0;
+  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)n);
+  return launch_dep(half_embed_t_kernel, grid, dim3(256), st, src, K, N, (uint16_t*)hi, (uint16_t*)lo, Kpad, fmt, e,
+                    kin, kout, l, dstride);
 }
 
 cudaError_t half_embed_t(const double2* src, int64_t K, int64_t N, void* hi, void* lo, int64_t Kpad, int fmt, int e,
@@ -384,7 +457,7 @@ cudaError_t half_embed_t(const double2* src, int64_t K, int64_t N, void* hi, voi
   if (kin > 0 && (K % kin || kout * kin != K)) return cudaErrorInvalidValue;   // a permutation of [0, K)
   dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32), 1);
   return launch_dep(half_embed_t_kernel, grid, dim3(256), st, src, K, N, (uint16_t*)hi, (uint16_t*)lo, Kpad, fmt, e,
-                    kin, kout);
+                    kin, kout, one_src(), (int64_t)0);
 }
 
 cudaError_t half_embed_mats(const double2* src, int64_t count, int64_t ss, int64_t rows, int64_t K, void* hi,
@@ -433,4 +506,18 @@ cudaError_t row_exps(const float* v, int n, int* out, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+}  // namespace gwk
+
+namespace gwk {
+cudaError_t gather_blocks(const void* shi, const void* slo, const int* se, void* dhi, void* dlo, int* de,
+                          int64_t block_bytes, int64_t ecount, const int* idx, int n, cudaStream_t st) {
+  if (block_bytes % 16 || n < 1 || n > kSrcListMax) return cudaErrorInvalidValue;
+  SrcList l{};
+  l.n = n;
+  for (int i = 0; i < n; ++i) l.off[i] = idx[i];
+  const int64_t words = block_bytes / 16;
+  const unsigned gx = (unsigned)std::min<int64_t>((words + 255) / 256, 152);
+  return launch_dep(gather_blocks_kernel, dim3(gx, (unsigned)n), dim3(256), st, (const uint4*)shi, (const uint4*)slo,
+                    se, (uint4*)dhi, (uint4*)dlo, de, words, ecount, l);
+}
 }  // namespace gwk

@@ -85,6 +85,12 @@ struct UmmaArgs {
   int64_t eo_zs, eo_div;
   int eo_shift;
   int* err;
+  // two-level batches: zin > 0 splits batch entry z into zo = z / zin and zi = z % zin, and
+  // every z stride s above is applied as zo * s_o + zi * s (the s_o below; 0 by default).
+  // The TMA batch coordinates are zo * za_o + zi * za_i (A) and zo * zb_o + zi * zb_i (B).
+  int zin;
+  int za_o, za_i, zb_o, zb_i;
+  int64_t ea_zso, eb_zso, eo_zso, c_zso;
 };
 
 // index m / div of an exponent array (rows and columns fit in 32 bits; div >= 2^30
@@ -92,18 +98,24 @@ struct UmmaArgs {
 __device__ __forceinline__ int64_t exp_index(int64_t m, int64_t div) {
   return div >= ((int64_t)1 << 30) ? 0 : (int64_t)((uint32_t)m / (uint32_t)div);
 }
+// offset of batch entry z for inner stride s and outer stride so (two-level batches)
+__device__ __forceinline__ int64_t zlin(const UmmaArgs& a, int z, int64_t s, int64_t so) {
+  if (a.zin <= 0) return (int64_t)z * s;
+  const int zo = (int)((uint32_t)z / (uint32_t)a.zin);
+  return (int64_t)zo * so + (int64_t)(z - zo * a.zin) * s;
+}
 // exponent of the row scale of row m (output or operand side); 0 without scales
 __device__ __forceinline__ int row_exp(const UmmaArgs& a, int z, int64_t m) {
   if (!a.eA) return 0;
   int64_t i = exp_index(m, a.ea_div);
   if (a.ea_mod > 0) i = (int64_t)((uint32_t)i % (uint32_t)a.ea_mod);
-  return a.eA[(int64_t)z * a.ea_zs + i] + a.eshift;
+  return a.eA[zlin(a, z, a.ea_zs, a.ea_zso) + i] + a.eshift;
 }
 __device__ __forceinline__ int col_exp(const UmmaArgs& a, int z, int64_t n) {
-  return a.eB ? a.eB[(int64_t)z * a.eb_zs + exp_index(n >> 1, a.eb_div)] : 0;
+  return a.eB ? a.eB[zlin(a, z, a.eb_zs, a.eb_zso) + exp_index(n >> 1, a.eb_div)] : 0;
 }
 __device__ __forceinline__ int out_exp(const UmmaArgs& a, int z, int64_t m) {
-  return a.eO ? a.eO[(int64_t)z * a.eo_zs + exp_index(m, a.eo_div)] + a.eo_shift : 0;
+  return a.eO ? a.eO[zlin(a, z, a.eo_zs, a.eo_zso) + exp_index(m, a.eo_div)] + a.eo_shift : 0;
 }
 // exact powers of two built from their bit patterns (the scales stay far inside the
 // normal range; clamped for safety): multiplying by them equals ldexp
@@ -255,7 +267,8 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
 
   if (warp == 0) {
     if (lane == 0) {
-      const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
+      const int za = a.a_batched ? (int)zlin(a, z, a.za_i, a.za_o) : 0;
+      const int zb = a.b_batched ? (int)zlin(a, z, a.zb_i, a.zb_o) : 0;
       int it = 0;
       for (; it < total; ++it) {
         const int s = it % UM_STAGES;
@@ -350,7 +363,7 @@ __global__ void __launch_bounds__(UM_THREADS, 2)
         const int row = m0 + rr;
         if (row >= a.M) break;
         const int64_t ro = row / a.row_inner, ri = row - ro * a.row_inner;
-        const int64_t base = (int64_t)z * a.c_zs + ro * a.row_s1 + ri * a.c_ld;
+        const int64_t base = zlin(a, z, a.c_zs, a.c_zso) + ro * a.row_s1 + ri * a.c_ld;
         const float* trow = tile + rr * LDT;
         if (a.c_fp64) {
           double* C = (double*)a.C + base;
@@ -446,7 +459,7 @@ __device__ __forceinline__ void umma_write_block(const UmmaArgs& a, int z, int r
   {
     const int row = r0 + lane;
     const int64_t ro = row / a.row_inner, ri = row - ro * a.row_inner;
-    myoff = (int64_t)z * a.c_zs + ro * a.row_s1 + ri * a.c_ld;
+    myoff = zlin(a, z, a.c_zs, a.c_zso) + ro * a.row_s1 + ri * a.c_ld;
   }
   const int n = n0 + lane;
   const bool colok = lane < ncol && n < a.N;
@@ -665,7 +678,8 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         if (*(volatile int*)&s_fail) break;
         int n0, m0, z, kb0, nkb;
         decode(t, n0, m0, z, kb0, nkb);
-        const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
+        const int za = a.a_batched ? (int)zlin(a, z, a.za_i, a.za_o) : 0;
+        const int zb = a.b_batched ? (int)zlin(a, z, a.zb_i, a.zb_o) : 0;
         const bool three = a.nseg == 3;
         // three products: one k-block per stage (hi and lo planes); one product: two k-blocks
         const int nst = three ? nkb : (nkb + 1) / 2;
@@ -878,12 +892,20 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
         // float2 stores cover 256 contiguous bytes
         int64_t myoff = 0;
         {
-          const int64_t ro = row / a.row_inner, ri = row - ro * a.row_inner;
-          myoff = (int64_t)z * a.c_zs + ro * a.row_s1 + ri * a.c_ld;
+          const int64_t ro = a.row_inner >= ((int64_t)1 << 31) ? 0 : (int64_t)((uint32_t)row / (uint32_t)a.row_inner);
+          const int64_t ri = row - ro * a.row_inner;
+          myoff = zlin(a, z, a.c_zs, a.c_zso) + ro * a.row_s1 + ri * a.c_ld;
         }
         const bool rok = row < a.M;
         float* C = (float*)a.C;
         const float al = (float)a.alpha;
+        // the row's scale exponents and the base of its column exponents, once per tile
+        const int rexp_r = (rok && a.eA) ? row_exp(a, z, row) : 0;
+        const int oexp_r = (rok && a.o_half) ? out_exp(a, z, row) : 0;
+        const int64_t ebase = a.eB ? zlin(a, z, a.eb_zs, a.eb_zso) : 0;
+        const bool bconst = a.eb_div >= ((int64_t)1 << 30) || !a.eB;
+        const int cconst = (a.eB && bconst) ? a.eB[ebase] : 0;
+        auto colexp = [&](int n) { return a.eB ? a.eB[ebase + exp_index(n >> 1, a.eb_div)] : 0; };
         for (int cb = 0; cb < BW; cb += 32) {
           uint32_t v[32];
           asm volatile(
@@ -902,13 +924,13 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           if (rok && a.c_fp64) {
             double* Cd = (double*)a.C;
-            const int rexp = row_exp(a, z, row);
+            const int rexp = rexp_r;
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const double sc = a.alpha * p2d(rexp + col_exp(a, z, n));
+                const double sc = a.alpha * p2d(rexp + colexp(n));
                 const double sre = sc * (double)__uint_as_float(v[j]);
                 const double sim = sc * (double)__uint_as_float(v[j + 1]);
                 double2* p2 = (double2*)(Cd + off);
@@ -923,10 +945,8 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
           } else if (rok && a.o_half) {
             // 16-bit hi / lo pieces of D 2^(eA + eB - eO): each (re, im) pair converted as one
             // fp16x2 / bf16x2 value and stored with one 32-bit store per plane
-            const int rexp = row_exp(a, z, row) - out_exp(a, z, row);
-            // one column exponent for the whole tile when B has one per batch entry
-            const bool bconst = a.eb_div >= ((int64_t)1 << 30) || !a.eB;
-            const int cconst = (a.eB && bconst) ? a.eB[(int64_t)z * a.eb_zs] : 0;
+            const int rexp = rexp_r - oexp_r;
+            // one column exponent for the whole tile when B has one per batch entry (cconst)
             const float rsc = al * p2f(rexp + cconst);
             const int nb = n0 + cbase + cb;   // first column of this 32-column block
             int nv = a.N - nb;
@@ -938,7 +958,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
 #pragma unroll
               for (int j = 0; j < 32; j += 2) {
                 if (j < nv) {
-                  const float sc = bconst ? rsc : al * p2f(rexp + col_exp(a, z, nb + j));
+                  const float sc = bconst ? rsc : al * p2f(rexp + colexp(nb + j));
                   const float2 x = make_float2(sc * __uint_as_float(v[j]), sc * __uint_as_float(v[j + 1]));
                   const __nv_bfloat162 h2 = __float22bfloat162_rn(x);
                   const float2 hx = __bfloat1622float2(h2);
@@ -950,7 +970,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
 #pragma unroll
               for (int j = 0; j < 32; j += 2) {
                 if (j < nv) {
-                  const float sc = bconst ? rsc : al * p2f(rexp + col_exp(a, z, nb + j));
+                  const float sc = bconst ? rsc : al * p2f(rexp + colexp(nb + j));
                   const float2 x = make_float2(sc * __uint_as_float(v[j]), sc * __uint_as_float(v[j + 1]));
                   const __half2 h2 = __float22half2_rn(x);
                   const float2 hx = __half22float2(h2);
@@ -961,13 +981,13 @@ __global__ void __launch_bounds__(UP_THREADS, 1)
             }
           } else if (rok && a.eA) {
             // scaled operands: 2^(eA[row] + eB[column pair] + eshift), exact powers of two
-            const float rsc = al * p2f(row_exp(a, z, row));
+            const float rsc = al * p2f(rexp_r);
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const int n = n0 + cbase + cb + j;
               if (cb + j < BW && n < a.N) {
                 const int64_t off = myoff + (int64_t)(n >> 1) * a.col_s1;
-                const float sc = rsc * p2f(col_exp(a, z, n));
+                const float sc = rsc * p2f(colexp(n));
                 const float re = sc * __uint_as_float(v[j]), im = sc * __uint_as_float(v[j + 1]);
                 if (a.C_lo) {
                   const float hr = tf32_rna_dev(re), hi_ = tf32_rna_dev(im);
@@ -1230,7 +1250,8 @@ static int tune_bn(const UmmaOperand& A, const UmmaOperand& B, int64_t Kpad, int
 cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, int64_t Kpad, int batch, void* C,
                       bool c_fp64, double alpha, bool accumulate, int64_t c_ld, int64_t c_zs, int nseg, int* err,
                       cudaStream_t st, int ksplit, int64_t row_inner, int64_t row_s1, int64_t col_inner,
-                      int64_t col_s1, float* C_lo, const UmmaScale* scale, int64_t kvalid, const UmmaOut* out) {
+                      int64_t col_s1, float* C_lo, const UmmaScale* scale, int64_t kvalid, const UmmaOut* out,
+                      const UmmaZ* zz) {
   const bool f16 = A.f16 != 0;
   const int bke = f16 ? 64 : UM_BK;   // elements per 128-byte k-block
   if (B.f16 != A.f16) return cudaErrorInvalidValue;   // one MMA kind: both operands fp16 or both tf32
@@ -1244,6 +1265,13 @@ cudaError_t umma_gemm(const UmmaOperand& A, const UmmaOperand& B, int M, int N, 
   a.f16 = A.f16;
   a.bke = bke;
   a.a_batched = A.batch > 1; a.b_batched = B.batch > 1;
+  a.za_i = a.zb_i = 1;
+  if (zz && zz->zin > 0) {
+    if (!g_persistent) return cudaErrorInvalidValue;
+    a.zin = zz->zin;
+    a.za_o = zz->za_o; a.za_i = zz->za_i; a.zb_o = zz->zb_o; a.zb_i = zz->zb_i;
+    a.ea_zso = zz->ea_zso; a.eb_zso = zz->eb_zso; a.eo_zso = zz->eo_zso; a.c_zso = zz->c_zso;
+  }
   a.C = C; a.c_fp64 = c_fp64; a.accumulate = accumulate; a.alpha = alpha; a.c_ld = c_ld; a.c_zs = c_zs;
   a.ksplit = ksplit;
   a.row_inner = row_inner > 0 ? row_inner : (int64_t)1 << 40;
