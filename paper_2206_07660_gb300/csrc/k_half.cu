@@ -13,6 +13,10 @@
 // Exponent rule: for a bound b = f 2^E (f in [0.5, 1)), e = E - 15 when b is the
 // exact row maximum, E - 14 (one bit of margin) when it bounds a sum computed in
 // fp32 by the tensor cores.
+//
+// The per-pair operand kernels take a list of source slabs (one output block each), so
+// that one launch prepares the operands of several k-points, and they are launched as
+// programmatic dependents of the previous kernel on the stream.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include "gw_internal.cuh"
