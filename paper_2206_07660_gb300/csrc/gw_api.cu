@@ -147,6 +147,18 @@ static constexpr int kRefineSteps = 2;
 static constexpr size_t kZGroupBytes = (size_t)8 << 30;
 static int g_pgroup_cap = 0;   // test hook: upper bound on the k-points per group (0: none)
 static int g_pbatch_cap = 0;   // test hook: upper bound on the k-points per chain launch (0: none)
+
+// k-points per launch of the 16-bit chains: enough output tiles of a nao-sized step
+// (naux nao rows in 128-row tiles, one per tau) for ~16 rounds of the 152 SMs, at most
+// the operand lists' length and nk
+static int chain_pbatch(int nao, int naux, int nk, int ntau) {
+  const int64_t tiles1 = ((int64_t)naux * nao + 127) / 128 * ntau;
+  int64_t kb = tiles1 > 0 ? (16 * 152 + tiles1 - 1) / tiles1 : 1;
+  if (kb > kSrcListMax) kb = kSrcListMax;
+  if (kb > nk) kb = nk;
+  if (g_pbatch_cap > 0 && kb > g_pbatch_cap) kb = g_pbatch_cap;
+  return kb < 1 ? 1 : (int)kb;
+}
 static constexpr size_t kRefineBytes = (size_t)6 << 30;
 
 #define CK(x)                                                                        \
@@ -538,14 +550,7 @@ static gw_status init_impl(const gw_config* cfg, const gw_grid* grid, const doub
     // k-points per launch of the chains: enough output tiles for ~16 rounds of the SMs in the
     // nao-sized steps (small systems put several (k, k+q) pairs into each GEMM); the per-k
     // operand buffers below hold that many blocks
-    {
-      const int64_t tiles1 = ((int64_t)naux * nao + 127) / 128 * ntau;
-      int64_t kb = (16 * 152 + tiles1 - 1) / tiles1;
-      if (kb > kSrcListMax) kb = kSrcListMax;
-      if (kb > nk) kb = nk;
-      if (g_pbatch_cap > 0 && kb > g_pbatch_cap) kb = g_pbatch_cap;
-      c->pbatch = kb < 1 ? 1 : (int)kb;
-    }
+    c->pbatch = chain_pbatch(nao, naux, nk, ntau);
     const size_t kb = (size_t)c->pbatch;
     const size_t pb = (size_t)ntau * naux * c->kpadS * 2, tb = (size_t)2 * n2 * c->kpadS * 2;
     c->Pchi = (float*)need(A(pb)); c->Pclo = (float*)need(A(pb));
@@ -2510,6 +2515,11 @@ extern "C" gw_status gw_grand_potential(gw_ctx* c, double* phi) {
     }
   *phi = re / (2.0 * c->nk);
   return s;
+}
+
+// The k-points per launch that a 16-bit context of these sizes uses (host only).
+extern "C" int gwdbg_chain_pbatch(int nao, int naux, int nk, int ntau) {
+  return chain_pbatch(nao, naux, nk, ntau);
 }
 
 // Caps the number of k-points per launch of the 16-bit chains in contexts created

@@ -53,3 +53,13 @@ def sharded_iteration(g, device="cuda", group=None, reduce=sum_over_ranks):
     g.set("Sigma_tau", S)
     g.selfenergy_finish()
     return g.dyson()
+
+
+def sharded_grand_potential(g, group=None, reduce=sum_over_ranks):
+    """Phi~ (Eq. tilde_Phi_GW) of a q-sharded problem: each rank's context sums its
+    own q block (gw_grand_potential) and one all-reduce adds the blocks.  Call it
+    after the rank's polarization step."""
+    import torch
+    x = torch.tensor([g.grand_potential()], dtype=torch.float64)
+    reduce(x, group)
+    return float(x[0])

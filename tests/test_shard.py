@@ -14,7 +14,8 @@ import numpy as np
 import pytest
 
 from oracle import gw as ogw
-from paper_2206_07660_gb300.shard import q_block, sharded_iteration
+from oracle import thermo
+from paper_2206_07660_gb300.shard import q_block, sharded_grand_potential, sharded_iteration
 from gpu_helpers import system
 
 
@@ -67,6 +68,11 @@ class OracleContext:
     def dyson(self):
         return self.st.dyson()
 
+    def grand_potential(self):
+        # the rank's share of Eq. tilde_Phi_GW: its q block, normalised by the full nk
+        qs = list(range(self.q0, self.q1))
+        return thermo.phi_tilde(self.st.grid, self.P0[qs]) * len(qs) / self.nk
+
 
 def test_q_blocks_cover_every_q_once():
     for nq in range(1, 70):
@@ -100,7 +106,8 @@ def _rank_main(rank, world, port, out):
         g = OracleContext(_sysd())
         blk = attach(g, rank, world)
         mu = sharded_iteration(g, device="cpu")
-        out[rank] = (blk, mu, g.Stau, g.st.G_tau)
+        phi = sharded_grand_potential(g)
+        out[rank] = (blk, mu, g.Stau, g.st.G_tau, phi)
     finally:
         dist.destroy_process_group()
 
@@ -113,9 +120,12 @@ def test_two_rank_q_sharded_iteration_matches_unsharded():
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
     ref = ogw.State(_sysd())
+    ref.dyson()
+    phi_ref = thermo.phi_tilde(ref.grid, ogw.polarization_tau(ref.V, ref.G_tau, ref.km))
     ref.iterate()
     assert res[0][0] == (0, 2) and res[1][0] == (2, 4)
     for r in range(world):
         assert np.abs(res[r][2] - ref.Sigma_tau).max() < 1e-13     # summed partials = full Sigma~(tau)
         assert np.abs(res[r][3] - ref.G_tau).max() < 1e-12        # replicated Dyson step
         assert abs(res[r][1] - ref.mu) < 1e-12
+        assert abs(res[r][4] - phi_ref) <= 1e-12 * abs(phi_ref)   # summed q blocks = full Phi~
