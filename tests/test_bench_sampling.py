@@ -52,3 +52,25 @@ def test_sample_at_c1(c1):
     assert np.isfinite(v) and v > 0
     assert abs(v - sum(parts.values())) <= 1e-9 * v
     assert info["cores"] >= 1 and "8 of 32 tau points" in info["sample"]
+
+
+def test_traffic_record_is_keyed_to_the_kernel_source(tmp_path, monkeypatch):
+    # the committed record carries the source hash of the contraction kernel it was taken
+    # on; the bench reports its bytes only while that hash matches the current source
+    import re
+    txt0 = open(os.path.join(ROOT, "profiles", "contraction_C3_split_f16.md")).read()
+    keyed = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt0).group(1) == bench.source_sha("split_f16")
+    v = bench.traffic_from_profiles("C3", "split_f16")
+    assert (v is not None) == keyed
+    if v is not None:
+        assert 1e8 < v < 1e11
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    txt = open(os.path.join(ROOT, "profiles", "contraction_C3_split_f16.md")).read()
+    (prof / "contraction_C3_split_f16.md").write_text(txt.replace(bench.source_sha("split_f16"), "0" * 16))
+    src = tmp_path / "paper_2206_07660_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "k_umma.cu").write_bytes(open(os.path.join(ROOT, "paper_2206_07660_gb300", "csrc", "k_umma.cu"), "rb").read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("C3", "split_f16") is None
+    assert bench.traffic_from_profiles("C9", "split_f16") is None
