@@ -498,6 +498,24 @@ def run_gw(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # one system; with N > 1 ranks every rank owns a block of q-points (strong scaling)
+    cfg, sysd = make_inputs(args.workload, kmesh=args.kmesh)
+    # the oracle's state (the error slices below use it too) and the CPU baseline, timed
+    # first, in a process that has not touched the GPU yet (as the reference arm does)
+    st = None
+    cpu_line = None
+    if rank == 0 and world == 1 and not (args.no_slices and args.no_cpu_baseline):
+        st, _ = cpu_state(sysd)
+    if st is not None and not args.no_cpu_baseline:
+        # the reference arm's per-step sample (one (q, k) pair), median over a few pairs
+        vs = []
+        for i in range(args.cpu_samples):
+            v, info = cpu_sample(cfg, sysd, st, 1, offset=i)
+            vs.append(v)
+        cpu_line = {"value": statistics.median(vs), "unit": "s/iteration", "cores": info["cores"], "kind": "oracle",
+                    "sample": "median over %d samples of: %s" % (len(vs), info["sample"])}
+
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
@@ -506,8 +524,6 @@ def run_gw(args):
         if world > 1:
             dist.barrier()
 
-    # one system; with N > 1 ranks every rank owns a block of q-points (strong scaling)
-    cfg, sysd = make_inputs(args.workload, kmesh=args.kmesh)
     fl = flops(cfg)
     Vd = device_V(sysd) if sysd.get("V") is None else None
     g = make_context(sysd, Vd, args.precision, args)
@@ -602,9 +618,7 @@ def run_gw(args):
     # sampled slices against the oracle (rank 0, single GPU): the mixed path's errors in Ha, and the
     # FP64 path's errors and its seconds per iteration extrapolated from one q
     extra = {}
-    st = None
     if rank == 0 and world == 1 and not args.no_slices:
-        st, _ = cpu_state(sysd)
         sl = slice_inputs(sysd, st)
         r_mixed = run_slices(g, sl, st.G_tau, torch)
         g.close()
@@ -690,17 +704,8 @@ def run_gw(args):
         line["grand_potential"] = phi
     if g is not None:
         g.close()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if st is None:
-            st, _ = cpu_state(sysd)
-        # the reference arm's per-step sample (one (q, k) pair), median over a few pairs
-        vs = []
-        for i in range(args.cpu_samples):
-            v, info = cpu_sample(cfg, sysd, st, 1, offset=i)
-            vs.append(v)
-        line["cpu_baseline"] = {"value": statistics.median(vs), "unit": "s/iteration", "cores": info["cores"],
-                                "kind": "oracle",
-                                "sample": "median over %d samples of: %s" % (len(vs), info["sample"])}
+    if cpu_line is not None:
+        line["cpu_baseline"] = cpu_line
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
