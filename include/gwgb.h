@@ -417,7 +417,7 @@ gw_status gw_iterate_diis(gw_ctx* ctx, int32_t n_iter, int32_t m, double mix, do
  * the pivots of an FP64 LU factorisation without row exchanges, the continuous
  * branch when the Hermitian part of I - P~0 is positive definite (a negative
  * semidefinite polarization).  GW_ERR_SINGULAR for a zero pivot or one with
- * non-positive real part.  naux <= 800 (GW_ERR_ARG otherwise).  Synchronises the
+ * non-positive real part.  naux <= 6400 (GW_ERR_ARG otherwise).  Synchronises the
  * context's stream; allocates a workspace of up to nq nwb naux^2 complex doubles
  * for the duration of the call (GW_ERR_OOM when even one q does not fit). */
 gw_status gw_grand_potential(gw_ctx* ctx, double* phi);
