@@ -187,11 +187,12 @@ typedef struct {
   const double* lb;        /* [ntau] real                                           */
 } gw_grid;
 
-/* Create a context: validates sizes, copies H0, S (Eq. scalar_S) and V (Eq.
- * U_decompose), builds the tau grid, the transform matrices and the density
- * weights on the device.  Unless GW_SKIP_CHECKS, rejects with GW_ERR_ARG
- * inputs where H0 or S is not Hermitian or V^{k'k}(Q) != V^{kk'}(Q)^H beyond
- * 1e-10 relative.  Synchronises cfg->stream.  *out is NULL on failure. */
+/* Create a context: validates sizes (nao <= 96, the Dyson kernel's bound; GW_ERR_ARG
+ * otherwise), copies H0, S (Eq. scalar_S) and V (Eq. U_decompose), builds the tau
+ * grid, the transform matrices and the density weights on the device.  Unless
+ * GW_SKIP_CHECKS, rejects with GW_ERR_ARG inputs where H0 or S is not Hermitian or
+ * V^{k'k}(Q) != V^{kk'}(Q)^H beyond 1e-10 relative.  Synchronises cfg->stream.
+ * *out is NULL on failure. */
 gw_status gw_init(const gw_config* cfg, const double* H0, const double* S, const double* V,
                   gw_ctx** out);
 
