@@ -86,3 +86,26 @@ def test_zero_and_trace_terms():
     a, w0 = 0.4, 0.9
     F = thermo.matsubara_sum_weights(grid) @ (grid.TFb @ pole_tau(grid.tau, beta, a, w0))
     assert abs(F - (-a / np.tanh(beta * w0 / 2))) < 1e-12
+
+
+def test_symmetric_frequency_set_gives_a_real_sum():
+    # with an odd ntau the sampled bosonic set is closed under m -> -m; a Hermitian
+    # P~0(tau) without any other symmetry has P~0(-i Omega) = P~0(i Omega)^H, so the
+    # terms at +-m are complex conjugates and the sampled Matsubara sum is real
+    beta, ntau = 10.0, 33
+    fn, bm = matsubara_indices(ntau)
+    assert set((-bm).tolist()) == set(bm.tolist())
+    grid = Grid(beta, ntau, fn, bm)
+    rng = np.random.default_rng(19)
+    n = 6
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    a, w0 = rng.uniform(0.1, 0.6, n), rng.uniform(0.4, 1.2, n)
+    # two poles per channel with unequal weights at +-w0: complex p(i Omega), Hermitian P~0(tau)
+    t = grid.tau[:, None]
+    d = -(a * np.exp(-w0 * t) + 0.3 * a * np.exp(-w0 * (beta - t))) / (1 - np.exp(-beta * w0))
+    P = np.einsum("ab,tb,cb->tac", U, d, U.conj())[None]
+    assert np.abs(P - np.conj(np.swapaxes(P, -1, -2))).max() < 1e-15
+    Piw = grid.TFb @ P[0].reshape(ntau, -1)
+    assert np.abs(Piw.imag).max() > 1e-3                     # P~0(i Omega) is not real
+    phi, im = thermo.phi_tilde(grid, P, return_imag=True)
+    assert abs(im) <= 1e-12 * abs(phi)
