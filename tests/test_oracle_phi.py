@@ -109,3 +109,34 @@ def test_symmetric_frequency_set_gives_a_real_sum():
     assert np.abs(Piw.imag).max() > 1e-3                     # P~0(i Omega) is not real
     phi, im = thermo.phi_tilde(grid, P, return_imag=True)
     assert abs(im) <= 1e-12 * abs(phi)
+
+
+def _closed_form_case():
+    beta, ntau = 10.0, 32
+    grid = Grid(beta, ntau, *matsubara_indices(ntau))
+    rng = np.random.default_rng(23)
+    params = [(rng.uniform(0.05, 0.9, 4), rng.uniform(0.3, 1.5, 4)) for _ in range(2)]
+    P0 = rotated_poles(grid, params, 29)
+    ref = sum(np.sum(pole_sum(beta, a, w0)) for a, w0 in params) / (2 * len(params))
+    return grid, P0, ref
+
+
+@pytest.mark.parametrize("slip", ["no_trace_term", "weights_x2", "backward_transform"])
+def test_planted_slips_fail_the_closed_form(monkeypatch, slip):
+    # each plausible mistake, planted in the oracle, moves Phi~ far from the closed form
+    grid, P0, ref = _closed_form_case()
+    assert abs(thermo.phi_tilde(grid, P0) - ref) <= 1e-11 * abs(ref)
+    if slip == "no_trace_term":
+        monkeypatch.setattr(thermo, "trace_log_plus",
+                            lambda A: np.sum(np.log(np.linalg.eigvals(np.eye(A.shape[0]) - A))))
+    elif slip == "weights_x2":
+        monkeypatch.setattr(thermo, "matsubara_sum_weights", lambda g: 2.0 * (g.lb @ g.TBb))
+    elif slip == "backward_transform":
+        class Swapped:
+            pass
+        sw = Swapped()
+        sw.__dict__.update(grid.__dict__)
+        sw.TFb = grid.TBb.T.copy()
+        grid = sw
+    bad = thermo.phi_tilde(grid, P0)
+    assert abs(bad - ref) > 1e-4 * abs(ref)
